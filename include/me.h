@@ -1,0 +1,178 @@
+/*
+ * libme -- batched tree-level squared matrix elements on GB300 (sm_103a).
+ *
+ * C ABI of the data-parallel hot path of arXiv:2507.21039: for a batch of
+ * phase-space points, the per-event |M|^2 summed over helicities and colours
+ * (Sec. 3.1 "Parallel scattering amplitudes"), evaluated by a helicity-amplitude
+ * chain and a colour contraction J^+ C J (Sec. 4.1), plus the seeded RAMBO
+ * sampler of the standalone application (Sec. 4).  It plays the role of the
+ * paper's Bridge / fBridge (Sec. 3.2): create, execute, destroy.
+ *
+ * Processes (particle order: initial state first):
+ *   "ee_mumu"   e-(in) e+(in)  -> mu-  mu+        photon only, massless
+ *   "gg_ttx"    g(in)  g(in)   -> t t~            3 diagrams,    2 colour flows
+ *   "gg_ttxg"   g g -> t t~ g                     16 diagrams,   6 colour flows
+ *   "gg_ttxgg"  g g -> t t~ g g                   123 diagrams,  24 colour flows
+ *   "gg_ttxggg" g g -> t t~ g g g                 1240 diagrams, 120 colour flows
+ *
+ * Returned |M|^2: summed over all helicities and colours, averaged over the
+ * initial-state spins (x 1/4) and colours (x 1/64 for gg), divided by n! for n
+ * identical final-state gluons.  Couplings are fixed (no running).
+ *
+ * Conventions for every call:
+ *   - momenta are FP64 [nevt][npar][4] row-major, components (E, px, py, pz),
+ *     all particles with physical (positive-energy) momenta.  The same bytes as
+ *     the paper's Fortran P(0:3, npar, nevt).
+ *   - pointers may be host or device memory (detected with
+ *     cudaPointerGetAttributes).  With device pointers a call is asynchronous
+ *     on `cuda_stream` (a cudaStream_t; NULL = legacy default stream); with any
+ *     host pointer the call stages through device memory and returns after the
+ *     results are in the caller's buffer.
+ *   - the caller owns every buffer it passes; the library never keeps a
+ *     pointer to it after the call.  The handle owns its device state.
+ *   - every call returns 0 on success or a negative ME_E* code; nothing
+ *     throws across the ABI.  nevt == 0 is a no-op returning 0.
+ *   - handles are independent; one handle must not be used from two host
+ *     threads at the same time.  There is no global mutable state.
+ */
+#ifndef LIBME_ME_H
+#define LIBME_ME_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define ME_OK 0
+#define ME_EINVAL (-1)        /* null pointer, nevt < 0, unknown process, bad masses/couplings/precision */
+#define ME_ENOMEM (-2)        /* a device or host allocation failed */
+#define ME_ECUDA (-3)         /* a CUDA runtime call or kernel launch failed */
+#define ME_ENOTFILTERED (-4)  /* me_sigmakin before me_filter_helicities with ME_OPT_REQUIRE_FILTER set */
+#define ME_ENONFINITE (-5)    /* non-finite momenta found (ME_OPT_CHECK_FINITE) */
+#define ME_ETIMEOUT (-6)      /* a bounded wait expired (serving layer) */
+#define ME_ESAMPLER (-7)      /* RAMBO: an event needed more than 1000 attempts or Newton failed */
+
+/* precision modes (Sec. 4.1, Table 1: FP64, FP32, mixed) */
+#define ME_PREC_FP64 0   /* chain, colour sum and helicity sum in FP64 */
+#define ME_PREC_FP32 1   /* chain and colour sum in FP32; momenta, p^2-m^2 and helicity sum in FP64 */
+#define ME_PREC_MIXED 2  /* FP32 chain (FP64 momenta, p^2-m^2), colour sum on BF16 tensor cores
+                            with hi/lo split operands and FP32 accumulation (24 and 120 flows;
+                            FP32 scalar below), FP64 helicity sum */
+
+typedef struct me_handle me_handle;
+
+/*
+ * me_init -- create a handle for one process and precision (the Bridge
+ * constructor of Sec. 3.2).
+ *   process:   one of the names above.
+ *   masses:    nmass == npar external masses in particle order.  gg_ttx*:
+ *              gluons 0, t and t~ equal (the top mass, e.g. 173.0).  ee_mumu:
+ *              all 0.  NULL with nmass == 0 selects m_t = 173.0.
+ *   couplings: {alpha} -- alpha_s for gg_ttx*, alpha_em for ee_mumu; NULL with
+ *              ncoup == 0 selects 0.118 / (1/132.5).
+ *   precision: ME_PREC_*.
+ * The handle starts with all helicities enabled and unfiltered.
+ * Errors: ME_EINVAL, ME_ENOMEM, ME_ECUDA.  *h is NULL on error.
+ */
+int me_init(me_handle** h, const char* process, const double* masses, int nmass, const double* couplings,
+            int ncoup, int precision);
+
+/*
+ * me_filter_helicities -- find the helicity configurations that contribute
+ * ("non-vanishing", Sec. 3.1).  h is kept iff max over the probe events of
+ * |M_h|^2 / |M|^2 > 1e-14, computed in FP64 on the first min(nevt, 16384)
+ * events of `momenta`.  Synchronous.  Stores the mask in the handle; writes
+ * the number of kept helicities to *ngood_out (may be NULL).
+ * Errors: ME_EINVAL (null handle/momenta, nevt <= 0), ME_ENOMEM, ME_ECUDA.
+ */
+int me_filter_helicities(me_handle* h, const double* momenta, int64_t nevt, int* ngood_out);
+
+/*
+ * me_sigmakin -- |M|^2 for nevt events: momenta [nevt][npar][4] -> me2[nevt]
+ * (Sec. 3.1 chain + Sec. 4.1 colour algebra + helicity sum).  If the handle has
+ * not been filtered it filters on this batch first (synchronously), unless
+ * ME_OPT_REQUIRE_FILTER is set, which makes this ME_ENOTFILTERED.  Per-event
+ * results do not depend on the batch they are computed in.
+ * Errors: ME_EINVAL, ME_ENOTFILTERED, ME_ENONFINITE, ME_ENOMEM, ME_ECUDA.
+ */
+int me_sigmakin(me_handle* h, const double* momenta, int64_t nevt, double* me2, void* cuda_stream);
+
+/*
+ * me_sigmakin_hel -- diagnostic variant: also writes each kept helicity's
+ * contribution, hel_out[nevt][ngood] in the order of me_good_helicities, so
+ * that sum over the row == me2.  Device pointers only (ME_EINVAL otherwise).
+ */
+int me_sigmakin_hel(me_handle* h, const double* momenta, int64_t nevt, double* me2, double* hel_out,
+                    void* cuda_stream);
+
+/*
+ * me_info -- process sizes.  Any output pointer may be NULL.
+ *   good_mask_words: 2 words; bit h of word h/64 set iff helicity h is kept
+ *   (all set before filtering).  nhel <= 128.
+ */
+int me_info(const me_handle* h, int* npar, int* nhel, int* ncol, int* ndiag, uint64_t* good_mask_words);
+
+/* me_good_helicities -- kept helicity indices (host array of capacity cap);
+ * *n receives their number.  Helicity index h: particle i has helicity +1 iff
+ * bit (npar-1-i) of h is set. */
+int me_good_helicities(const me_handle* h, int* out, int cap, int* n);
+
+/* me_flops_per_event -- algorithmic work per event of the current mask, as
+ * counted by the process generator: chain flops (FP32/FP64 pipe) and colour
+ * quadratic-form flops, each = kept helicities x per-helicity count. */
+int me_flops_per_event(const me_handle* h, double* chain_flops, double* colour_flops);
+
+/* options */
+#define ME_OPT_REQUIRE_FILTER 1  /* value 1: me_sigmakin refuses to filter lazily */
+#define ME_OPT_CHECK_FINITE 2    /* value 1: reject non-finite momenta (one extra pass, synchronous) */
+#define ME_OPT_GAUGE_CHECK 3     /* value = external gluon index: its polarisation is replaced by its
+                                    momentum (Ward identity diagnostic); -1 restores normal running */
+int me_set_option(me_handle* h, int option, int value);
+
+/* me_free -- destroy a handle (NULL is a no-op).  Synchronises its work. */
+void me_free(me_handle* h);
+
+/* Cuts of the seeded sampler: final-state particle j is subject to the cuts
+ * iff bit j of final_mask is set (j counts final-state particles from 0).
+ * Each such particle needs pT > ptmin, each such pair Delta R > drmin with
+ * Delta R = sqrt(Delta eta^2 + Delta phi^2), eta the pseudorapidity. */
+typedef struct me_cuts {
+    double ptmin;
+    double drmin;
+    uint32_t final_mask;
+} me_cuts;
+
+/*
+ * rambo_sample -- seeded flat phase space (RAMBO, Kleiss-Stirling-Ellis 1986,
+ * as in the standalone application of Sec. 4) for events ev0 .. ev0+nevt-1.
+ *   masses: npar masses; the two incoming particles are massless and move
+ *           along +z and -z with E = sqrt_s / 2.
+ *   Random numbers: Philox4x64-10, key (seed, 0), counter (event, attempt,
+ *   final particle, 0); one block gives the four uniforms of one final-state
+ *   particle, u = ((x >> 11) + 0.5) 2^-53.  Massive particles: Newton solve of
+ *   the RAMBO rescaling (|f| <= 1e-14 sqrt_s, at most 50 iterations).  With
+ *   cuts, attempt k = 0, 1, ... of the same event until it passes (at most 1000).
+ *   momenta_out: [nevt][npar][4]; weights_out (nullable): [nevt] phase-space
+ *   weight with (2 pi)^(4-3n) normalisation, -1 for an event that failed.
+ *   nfail_out (nullable, host): if given, the call synchronises and stores the
+ *   number of failed events; the return is then ME_ESAMPLER if it is > 0.
+ * Event i's momenta depend only on (seed, i): any range can be regenerated.
+ * Errors: ME_EINVAL (npar < 3 or > 8, masses NULL, sqrt_s <= sum of masses),
+ *         ME_ESAMPLER, ME_ENOMEM, ME_ECUDA.
+ */
+int rambo_sample(uint64_t seed, int64_t ev0, int64_t nevt, double sqrt_s, const double* masses, int npar,
+                 const me_cuts* cuts, double* momenta_out, double* weights_out, int64_t* nfail_out,
+                 void* cuda_stream);
+
+/* me_strerror -- static description of a status code. */
+const char* me_strerror(int status);
+
+/* me_version -- library version string. */
+const char* me_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LIBME_ME_H */

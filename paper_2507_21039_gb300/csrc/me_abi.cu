@@ -1,0 +1,380 @@
+// C ABI of libme (declared in include/me.h): handles, pointer-kind detection,
+// host staging, helicity filtering (arXiv:2507.21039 Sec. 3.1 "non-vanishing
+// helicities"), dispatch to the generated per-process kernels.
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+
+#include "me.h"
+#include "me_proc.h"
+
+using me::LaunchArgs;
+using me::ProcDesc;
+
+struct me_handle {
+    const ProcDesc* proc;
+    int precision;
+    int device;
+    double mt;
+    double alpha;
+    double norm;          // (4 pi alpha)^power / (iden * cden)
+    int nhel;
+    int ngood;
+    short good[128];      // host copy of the kept helicities
+    short* d_hel;         // device copy
+    int filtered;
+    int require_filter;
+    int check_finite;
+    int gauge_ext;
+};
+
+namespace {
+
+constexpr int kMaxProbe = 16384;
+constexpr double kFilterThreshold = 1e-14;
+
+bool is_device_ptr(const void* p)
+{
+    cudaPointerAttributes at;
+    cudaError_t e = cudaPointerGetAttributes(&at, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+int slots_for(int nlist)
+{
+    int s = 1;
+    while (s < nlist && s < 32) s <<= 1;
+    return s;
+}
+
+// per-helicity maximum of |M_h|^2 / |M|^2 over the probe events
+__global__ void filter_reduce(const double* __restrict__ hel_out, const double* __restrict__ me2, int nprobe,
+                              int nhel, double* __restrict__ ratio)
+{
+    const int h = blockIdx.x;
+    double m = 0.0;
+    for (int e = threadIdx.x; e < nprobe; e += blockDim.x) {
+        const double tot = me2[e];
+        if (tot > 0.0 && isfinite(tot)) {
+            const double r = hel_out[(long long)e * nhel + h] / tot;
+            m = fmax(m, r);
+        }
+    }
+    __shared__ double red[256];
+    red[threadIdx.x] = m;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + s]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) ratio[h] = red[0];
+}
+
+__global__ void count_nonfinite(const double* __restrict__ p, long long n, unsigned long long* bad)
+{
+    unsigned long long local = 0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        if (!isfinite(p[i])) ++local;
+    if (local) atomicAdd(bad, local);
+}
+
+int launch_me(me_handle* h, int precision, const double* d_mom, int64_t nevt, double* d_me2, double* d_hel_out,
+              const short* d_list, int nlist, cudaStream_t st)
+{
+    LaunchArgs a;
+    a.mom = d_mom;
+    a.nevt = nevt;
+    a.me2 = d_me2;
+    a.hel_out = d_hel_out;
+    a.hel_list = d_list;
+    a.nlist = nlist;
+    a.slots = slots_for(nlist);
+    a.norm = h->norm;
+    a.mt = h->mt;
+    a.gauge_ext = h->gauge_ext;
+    a.stream = st;
+    cudaError_t e = h->proc->launch(precision, a);
+    return e == cudaSuccess ? ME_OK : ME_ECUDA;
+}
+
+int set_good(me_handle* h, const short* list, int n)
+{
+    memcpy(h->good, list, sizeof(short) * n);
+    h->ngood = n;
+    if (cudaMemcpy(h->d_hel, h->good, sizeof(short) * n, cudaMemcpyHostToDevice) != cudaSuccess) return ME_ECUDA;
+    return ME_OK;
+}
+
+// FP64 per-helicity evaluation of the probe events and the filter decision
+int filter_device(me_handle* h, const double* d_mom, int64_t nevt)
+{
+    const int nprobe = (int)(nevt < kMaxProbe ? nevt : kMaxProbe);
+    const int nhel = h->nhel;
+    short all[128];
+    for (int i = 0; i < nhel; ++i) all[i] = (short)i;
+    double *d_hel_out = nullptr, *d_me2 = nullptr, *d_ratio = nullptr;
+    short* d_all = nullptr;
+    int rc = ME_OK;
+    if (cudaMalloc(&d_hel_out, sizeof(double) * (size_t)nprobe * nhel) != cudaSuccess ||
+        cudaMalloc(&d_me2, sizeof(double) * nprobe) != cudaSuccess ||
+        cudaMalloc(&d_ratio, sizeof(double) * nhel) != cudaSuccess ||
+        cudaMalloc(&d_all, sizeof(short) * nhel) != cudaSuccess) {
+        rc = ME_ENOMEM;
+    }
+    double ratio[128];
+    if (rc == ME_OK && cudaMemcpy(d_all, all, sizeof(short) * nhel, cudaMemcpyHostToDevice) != cudaSuccess)
+        rc = ME_ECUDA;
+    if (rc == ME_OK) rc = launch_me(h, me::PREC_FP64, d_mom, nprobe, d_me2, d_hel_out, d_all, nhel, 0);
+    if (rc == ME_OK) {
+        filter_reduce<<<nhel, 256>>>(d_hel_out, d_me2, nprobe, nhel, d_ratio);
+        if (cudaGetLastError() != cudaSuccess) rc = ME_ECUDA;
+    }
+    if (rc == ME_OK && cudaMemcpy(ratio, d_ratio, sizeof(double) * nhel, cudaMemcpyDeviceToHost) != cudaSuccess)
+        rc = ME_ECUDA;
+    cudaFree(d_hel_out);
+    cudaFree(d_me2);
+    cudaFree(d_ratio);
+    cudaFree(d_all);
+    if (rc != ME_OK) return rc;
+    short good[128];
+    int n = 0;
+    for (int i = 0; i < nhel; ++i)
+        if (ratio[i] > kFilterThreshold) good[n++] = (short)i;
+    if (n == 0) {  // degenerate probe (all zero): keep everything
+        for (int i = 0; i < nhel; ++i) good[i] = (short)i;
+        n = nhel;
+    }
+    rc = set_good(h, good, n);
+    if (rc == ME_OK) h->filtered = 1;
+    return rc;
+}
+
+int check_finite(const double* d_mom, int64_t n, cudaStream_t st)
+{
+    unsigned long long* d_bad = nullptr;
+    unsigned long long bad = 0;
+    if (cudaMallocAsync(&d_bad, sizeof(unsigned long long), st) != cudaSuccess) return ME_ENOMEM;
+    int rc = ME_OK;
+    if (cudaMemsetAsync(d_bad, 0, sizeof(unsigned long long), st) != cudaSuccess) rc = ME_ECUDA;
+    if (rc == ME_OK) {
+        count_nonfinite<<<152 * 4, 256, 0, st>>>(d_mom, n, d_bad);
+        if (cudaGetLastError() != cudaSuccess) rc = ME_ECUDA;
+    }
+    if (rc == ME_OK && cudaMemcpyAsync(&bad, d_bad, sizeof(bad), cudaMemcpyDeviceToHost, st) != cudaSuccess) rc = ME_ECUDA;
+    cudaFreeAsync(d_bad, st);
+    if (cudaStreamSynchronize(st) != cudaSuccess) rc = ME_ECUDA;
+    if (rc == ME_OK && bad) rc = ME_ENONFINITE;
+    return rc;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* me_version(void) { return "libme 0.1 (sm_103a)"; }
+
+const char* me_strerror(int status)
+{
+    switch (status) {
+    case ME_OK: return "success";
+    case ME_EINVAL: return "invalid argument";
+    case ME_ENOMEM: return "out of memory";
+    case ME_ECUDA: return "CUDA error";
+    case ME_ENOTFILTERED: return "helicities not filtered";
+    case ME_ENONFINITE: return "non-finite momenta";
+    case ME_ETIMEOUT: return "timeout";
+    case ME_ESAMPLER: return "phase-space sampler failed";
+    default: return "unknown status";
+    }
+}
+
+int me_init(me_handle** hp, const char* process, const double* masses, int nmass, const double* couplings, int ncoup,
+            int precision)
+{
+    if (!hp) return ME_EINVAL;
+    *hp = nullptr;
+    const ProcDesc* pd = me::find_process(process);
+    if (!pd) return ME_EINVAL;
+    if (precision < ME_PREC_FP64 || precision > ME_PREC_MIXED) return ME_EINVAL;
+    const bool qcd = pd->ngluon > 0;
+    double mt = qcd ? 173.0 : 0.0;
+    if (nmass != 0 || masses) {
+        if (!masses || nmass != pd->npar) return ME_EINVAL;
+        for (int i = 0; i < nmass; ++i)
+            if (!(masses[i] >= 0.0) || !std::isfinite(masses[i])) return ME_EINVAL;
+        if (qcd) {
+            if (masses[2] != masses[3]) return ME_EINVAL;
+            for (int i = 0; i < nmass; ++i)
+                if (i != 2 && i != 3 && masses[i] != 0.0) return ME_EINVAL;
+            mt = masses[2];
+        } else {
+            for (int i = 0; i < nmass; ++i)
+                if (masses[i] != 0.0) return ME_EINVAL;
+        }
+    }
+    double alpha = qcd ? 0.118 : 1.0 / 132.5;
+    if (ncoup != 0 || couplings) {
+        if (!couplings || ncoup != 1 || !(couplings[0] > 0.0) || !std::isfinite(couplings[0])) return ME_EINVAL;
+        alpha = couplings[0];
+    }
+    me_handle* h = new (std::nothrow) me_handle();
+    if (!h) return ME_ENOMEM;
+    h->proc = pd;
+    h->precision = precision;
+    cudaGetDevice(&h->device);
+    h->mt = mt;
+    h->alpha = alpha;
+    h->norm = std::pow(4.0 * M_PI * alpha, pd->coupling_power) / (pd->iden * pd->cden);
+    h->nhel = pd->nhel;
+    h->gauge_ext = -1;
+    if (cudaMalloc(&h->d_hel, sizeof(short) * 128) != cudaSuccess) {
+        delete h;
+        return ME_ENOMEM;
+    }
+    short all[128];
+    for (int i = 0; i < pd->nhel; ++i) all[i] = (short)i;
+    if (set_good(h, all, pd->nhel) != ME_OK) {
+        cudaFree(h->d_hel);
+        delete h;
+        return ME_ECUDA;
+    }
+    *hp = h;
+    return ME_OK;
+}
+
+void me_free(me_handle* h)
+{
+    if (!h) return;
+    cudaDeviceSynchronize();
+    cudaFree(h->d_hel);
+    delete h;
+}
+
+int me_set_option(me_handle* h, int option, int value)
+{
+    if (!h) return ME_EINVAL;
+    switch (option) {
+    case ME_OPT_REQUIRE_FILTER: h->require_filter = value != 0; return ME_OK;
+    case ME_OPT_CHECK_FINITE: h->check_finite = value != 0; return ME_OK;
+    case ME_OPT_GAUGE_CHECK:
+        if (value < -1 || value >= h->proc->npar) return ME_EINVAL;
+        if (value >= 0 && h->proc->ngluon == 0) return ME_EINVAL;
+        if (value >= 0 && (value == 2 || value == 3)) return ME_EINVAL;  // not a gluon
+        h->gauge_ext = value;
+        return ME_OK;
+    default: return ME_EINVAL;
+    }
+}
+
+int me_info(const me_handle* h, int* npar, int* nhel, int* ncol, int* ndiag, uint64_t* good_mask_words)
+{
+    if (!h) return ME_EINVAL;
+    if (npar) *npar = h->proc->npar;
+    if (nhel) *nhel = h->nhel;
+    if (ncol) *ncol = h->proc->ncol;
+    if (ndiag) *ndiag = h->proc->ndiag;
+    if (good_mask_words) {
+        good_mask_words[0] = good_mask_words[1] = 0;
+        for (int i = 0; i < h->ngood; ++i) good_mask_words[h->good[i] >> 6] |= 1ULL << (h->good[i] & 63);
+    }
+    return ME_OK;
+}
+
+int me_good_helicities(const me_handle* h, int* out, int cap, int* n)
+{
+    if (!h || (!out && cap > 0)) return ME_EINVAL;
+    for (int i = 0; i < h->ngood && i < cap; ++i) out[i] = h->good[i];
+    if (n) *n = h->ngood;
+    return ME_OK;
+}
+
+int me_flops_per_event(const me_handle* h, double* chain_flops, double* colour_flops)
+{
+    if (!h) return ME_EINVAL;
+    if (chain_flops) *chain_flops = (double)h->ngood * (double)h->proc->flops_hel;
+    if (colour_flops) *colour_flops = (double)h->ngood * (double)h->proc->colour_flops_hel;
+    return ME_OK;
+}
+
+int me_filter_helicities(me_handle* h, const double* momenta, int64_t nevt, int* ngood_out)
+{
+    if (!h || !momenta || nevt <= 0) return ME_EINVAL;
+    const int64_t nprobe = nevt < kMaxProbe ? nevt : kMaxProbe;
+    int rc;
+    if (is_device_ptr(momenta)) {
+        if (cudaDeviceSynchronize() != cudaSuccess) return ME_ECUDA;
+        rc = filter_device(h, momenta, nprobe);
+    } else {
+        const size_t bytes = sizeof(double) * 4 * h->proc->npar * (size_t)nprobe;
+        double* d = nullptr;
+        if (cudaMalloc(&d, bytes) != cudaSuccess) return ME_ENOMEM;
+        rc = cudaMemcpy(d, momenta, bytes, cudaMemcpyHostToDevice) == cudaSuccess ? ME_OK : ME_ECUDA;
+        if (rc == ME_OK) rc = filter_device(h, d, nprobe);
+        cudaFree(d);
+    }
+    if (rc == ME_OK && ngood_out) *ngood_out = h->ngood;
+    return rc;
+}
+
+static int sigmakin_impl(me_handle* h, const double* momenta, int64_t nevt, double* me2, double* hel_out,
+                         cudaStream_t st)
+{
+    if (!h || nevt < 0) return ME_EINVAL;
+    if (nevt == 0) return ME_OK;
+    if (!momenta || !me2) return ME_EINVAL;
+    const bool dm = is_device_ptr(momenta), dr = is_device_ptr(me2);
+    if (hel_out && !(dm && dr && is_device_ptr(hel_out))) return ME_EINVAL;
+    if (!h->filtered) {
+        if (h->require_filter) return ME_ENOTFILTERED;
+        if (dm && cudaStreamSynchronize(st) != cudaSuccess) return ME_ECUDA;
+        int rc = me_filter_helicities(h, momenta, nevt, nullptr);
+        if (rc != ME_OK) return rc;
+    }
+    const size_t mbytes = sizeof(double) * 4 * h->proc->npar * (size_t)nevt;
+    if (dm && dr) {
+        if (h->check_finite) {
+            int rc = check_finite(momenta, (int64_t)(mbytes / sizeof(double)), st);
+            if (rc != ME_OK) return rc;
+        }
+        return launch_me(h, h->precision, momenta, nevt, me2, hel_out, h->d_hel, h->ngood, st);
+    }
+    // host buffers: stage through stream-ordered device memory, then wait
+    double *d_mom = nullptr, *d_me2 = nullptr;
+    int rc = ME_OK;
+    if (!dm) {
+        if (cudaMallocAsync(&d_mom, mbytes, st) != cudaSuccess) return ME_ENOMEM;
+        if (cudaMemcpyAsync(d_mom, momenta, mbytes, cudaMemcpyHostToDevice, st) != cudaSuccess) rc = ME_ECUDA;
+    }
+    if (rc == ME_OK && !dr && cudaMallocAsync(&d_me2, sizeof(double) * nevt, st) != cudaSuccess) rc = ME_ENOMEM;
+    const double* mom_use = dm ? momenta : d_mom;
+    double* me2_use = dr ? me2 : d_me2;
+    if (rc == ME_OK && h->check_finite) rc = check_finite(mom_use, (int64_t)(mbytes / sizeof(double)), st);
+    if (rc == ME_OK) rc = launch_me(h, h->precision, mom_use, nevt, me2_use, nullptr, h->d_hel, h->ngood, st);
+    if (rc == ME_OK && !dr &&
+        cudaMemcpyAsync(me2, d_me2, sizeof(double) * nevt, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+        rc = ME_ECUDA;
+    if (d_mom) cudaFreeAsync(d_mom, st);
+    if (d_me2) cudaFreeAsync(d_me2, st);
+    if (cudaStreamSynchronize(st) != cudaSuccess && rc == ME_OK) rc = ME_ECUDA;
+    return rc;
+}
+
+int me_sigmakin(me_handle* h, const double* momenta, int64_t nevt, double* me2, void* cuda_stream)
+{
+    return sigmakin_impl(h, momenta, nevt, me2, nullptr, (cudaStream_t)cuda_stream);
+}
+
+int me_sigmakin_hel(me_handle* h, const double* momenta, int64_t nevt, double* me2, double* hel_out,
+                    void* cuda_stream)
+{
+    if (!hel_out) return ME_EINVAL;
+    return sigmakin_impl(h, momenta, nevt, me2, hel_out, (cudaStream_t)cuda_stream);
+}
+
+}  // extern "C"

@@ -1,0 +1,10 @@
+// Mixed-precision launcher (FP32 chain + colour sum).  Placeholder: scalar FP32
+// colour contraction for every basis size.
+#pragma once
+#include "me_kernel.cuh"
+
+namespace me {
+
+template <class P> cudaError_t launch_mixed(const LaunchArgs& a) { return launch_scalar<P, float>(a); }
+
+}  // namespace me

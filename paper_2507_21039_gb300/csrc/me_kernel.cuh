@@ -1,0 +1,181 @@
+// Batched |M|^2 kernel template (arXiv:2507.21039 Sec. 3.1: per event, the
+// helicity-amplitude chain for every good helicity, the colour sum J^+ C J and
+// the helicity sum).
+//
+// Work layout (GB300-first, not the paper's event-per-thread layout):
+//   * a CTA owns E = THREADS / S consecutive events; S lanes (a power of two,
+//     <= 32) share one event and split its good helicities between them, so the
+//     helicity sum is a warp-shuffle reduction inside an S-lane segment;
+//   * the CTA loads its events' momenta ([nevt][npar][4] FP64, contiguous) with
+//     16-byte coalesced loads into shared memory;
+//   * everything that does not depend on the helicity -- the external
+//     wavefunctions for both helicities of every particle, every line's
+//     momentum and propagator denominator p^2 - m^2 -- is computed once per
+//     event in FP64 by the CTA's threads and kept in shared memory (rounded to
+//     the amplitude precision T); FP64 work per (event, helicity) is zero;
+//   * each lane runs the generated straight-line chain with its wavefunctions
+//     and the colour-flow vector J in registers (or J in shared memory for the
+//     120-flow basis), then the colour quadratic form, accumulating |M_h|^2 in
+//     FP64.
+#pragma once
+#include "helas.cuh"
+#include "me_proc.h"
+
+namespace me {
+
+enum ExtKind : unsigned char { VIN = 0, VOUT = 1, FO_U = 2, FO_V = 3, FI_U = 4, FI_V = 5 };
+enum LineKind : unsigned char { L_EXT = 0, L_MASSLESS = 1, L_MASSIVE = 2 };
+
+// shared-memory bytes for E events of process P at precision T (+ J storage)
+template <class P, class T> __host__ __device__ constexpr size_t setup_bytes(int E)
+{
+    return (size_t)E * P::NPAR * 4 * sizeof(double) + (size_t)E * P::NPAR * 2 * sizeof(Wf<T>) +
+           (size_t)E * P::NLINES * sizeof(Ln<T>);
+}
+
+// Strided shared-memory accumulator for a per-thread J (column-major over the CTA)
+template <class T, int STRIDE> struct JSmem {
+    cx<T>* base;
+    __device__ __forceinline__ cx<T>& operator[](int c) const { return base[c * STRIDE]; }
+};
+
+template <class P, class T>
+__device__ __forceinline__ void event_setup(const double* __restrict__ p, int item, double mt, int gauge_ext,
+                                            Wf<T>* __restrict__ ext, Ln<T>* __restrict__ ln)
+{
+    if (item < 2 * P::NPAR) {
+        const int e = item >> 1, b = item & 1, lam = b ? 1 : -1;
+        const double* pe = p + 4 * e;
+        const double m = P::ext_massive(e) ? mt : 0.0;
+        cx<double> w[4];
+        if (e == gauge_ext) {  // diagnostic: gluon polarisation replaced by its momentum
+            for (int mu = 0; mu < 4; ++mu) w[mu] = {pe[mu], 0.0};
+        } else {
+            switch (P::ext_kind(e)) {
+            case VIN: vxxxxx(pe, lam, -1, w); break;
+            case VOUT: vxxxxx(pe, lam, +1, w); break;
+            case FO_U: oxxxxx(pe, m, lam, +1, w); break;
+            case FO_V: oxxxxx(pe, m, lam, -1, w); break;
+            case FI_U: ixxxxx(pe, m, lam, +1, w); break;
+            default: ixxxxx(pe, m, lam, -1, w); break;
+            }
+        }
+        Wf<T>& o = ext[item];
+#pragma unroll
+        for (int mu = 0; mu < 4; ++mu) o.c[mu] = {(T)w[mu].re, (T)w[mu].im};
+    } else {
+        const int l = item - 2 * P::NPAR;
+        const unsigned plus = P::line_plus(l), minus = P::line_minus(l);
+        double q[4] = {0.0, 0.0, 0.0, 0.0};
+        for (int e = 0; e < P::NPAR; ++e) {
+            const double s = ((plus >> e) & 1) ? 1.0 : (((minus >> e) & 1) ? -1.0 : 0.0);
+            if (s != 0.0)
+                for (int mu = 0; mu < 4; ++mu) q[mu] += s * p[4 * e + mu];
+        }
+        const unsigned kind = P::line_kind(l);
+        double inv = 0.0;
+        if (kind != L_EXT) {
+            // the denominator p^2 - m^2 in FP64: its cancellation near collinear
+            // and soft limits is what FP32 cannot resolve
+            const double m2 = kind == L_MASSIVE ? mt * mt : 0.0;
+            const double d = q[0] * q[0] - q[1] * q[1] - q[2] * q[2] - q[3] * q[3] - m2;
+            inv = 1.0 / d;
+        }
+        Ln<T>& o = ln[l];
+#pragma unroll
+        for (int mu = 0; mu < 4; ++mu) o.p[mu] = (T)q[mu];
+        o.inv = (T)inv;
+    }
+}
+
+// Scalar colour contraction and helicity sum.  T: chain/colour precision.
+template <class P, class T>
+__global__ void __launch_bounds__(P::THREADS) me_kernel_scalar(LaunchArgs a)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    constexpr int NPAR = P::NPAR, NL = P::NLINES, TH = P::THREADS;
+    const int S = a.slots;
+    const int E = TH / S;
+    const long long e0 = (long long)blockIdx.x * E;
+    const int ne = (int)min((long long)E, a.nevt - e0);
+
+    double* smom = reinterpret_cast<double*>(smem);
+    Wf<T>* sext = reinterpret_cast<Wf<T>*>(smom + E * NPAR * 4);
+    Ln<T>* sln = reinterpret_cast<Ln<T>*>(sext + E * NPAR * 2);
+
+    // (a1) coalesced load of this CTA's momenta
+    const double* g = a.mom + e0 * NPAR * 4;
+    if ((reinterpret_cast<uintptr_t>(g) & 15) == 0) {
+        const double2* g2 = reinterpret_cast<const double2*>(g);
+        double2* s2 = reinterpret_cast<double2*>(smom);
+        for (int i = threadIdx.x; i < ne * NPAR * 2; i += TH) s2[i] = __ldg(g2 + i);
+    } else {
+        for (int i = threadIdx.x; i < ne * NPAR * 4; i += TH) smom[i] = __ldg(g + i);
+    }
+    __syncthreads();
+
+    // (a2, a3 denominators) helicity-independent per-event data, FP64
+    constexpr int PER = 2 * NPAR + NL;
+    for (int it = threadIdx.x; it < ne * PER; it += TH) {
+        const int ev = it / PER, j = it - ev * PER;
+        event_setup<P, T>(smom + ev * NPAR * 4, j, a.mt, a.gauge_ext, sext + ev * NPAR * 2, sln + ev * NL);
+    }
+    __syncthreads();
+
+    // (a3-a6) chain, colour sum, helicity accumulation
+    const int ev = threadIdx.x / S, slot = threadIdx.x - ev * S;
+    double acc = 0.0;
+    if (ev < ne) {
+        const Wf<T>* ext = sext + ev * NPAR * 2;
+        const Ln<T>* ln = sln + ev * NL;
+        for (int i = slot; i < a.nlist; i += S) {
+            const int hel = a.hel_list[i];
+            T v;
+            if constexpr (P::J_SMEM) {
+                cx<T>* jb = reinterpret_cast<cx<T>*>(smem + setup_bytes<P, T>(E)) + threadIdx.x;
+                JSmem<T, TH> J{jb};
+                for (int c = 0; c < P::NCOL; ++c) J[c] = {T(0), T(0)};
+                P::template chain<T>(ext, hel, ln, (T)a.mt, J);
+                v = P::template colour<T>(J);
+            } else {
+                cx<T> J[P::NCOL];
+#pragma unroll
+                for (int c = 0; c < P::NCOL; ++c) J[c] = {T(0), T(0)};
+                P::template chain<T>(ext, hel, ln, (T)a.mt, J);
+                v = P::template colour<T>(J);
+            }
+            acc += (double)v;
+            if (a.hel_out) a.hel_out[(e0 + ev) * a.nlist + i] = (double)v * a.norm;
+        }
+    }
+    // (a6) helicity sum: reduce over the S lanes of each event
+    for (int off = S >> 1; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+    // (a7) normalisation g^{2k} / (IDEN * colour denominator)
+    if (ev < ne && slot == 0) a.me2[e0 + ev] = acc * a.norm;
+}
+
+template <class P, class T> size_t scalar_smem_bytes(int E)
+{
+    size_t b = setup_bytes<P, T>(E);
+    if constexpr (P::J_SMEM) b += (size_t)P::THREADS * P::NCOL * sizeof(cx<T>);
+    return b;
+}
+
+template <class P, class T> cudaError_t launch_scalar(const LaunchArgs& a)
+{
+    const int E = P::THREADS / a.slots;
+    const long long grid = (a.nevt + E - 1) / E;
+    const size_t smem = scalar_smem_bytes<P, T>(E);
+    static bool attr_set = false;  // per instantiation; benign race (idempotent)
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(me_kernel_scalar<P, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)scalar_smem_bytes<P, T>(P::THREADS));
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    if (grid > 0x7fffffffLL) return cudaErrorInvalidValue;
+    me_kernel_scalar<P, T><<<(unsigned)grid, P::THREADS, smem, a.stream>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace me

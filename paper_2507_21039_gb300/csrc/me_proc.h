@@ -1,0 +1,39 @@
+// Internal (non-ABI) description of a generated process and its launchers.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace me {
+
+// Arguments of one |M|^2 launch.  All pointers are device pointers.
+struct LaunchArgs {
+    const double* mom;      // [nevt][npar][4] FP64
+    long long nevt;
+    double* me2;            // [nevt]
+    double* hel_out;        // optional [nevt][nlist]: per-helicity contribution to me2
+    const short* hel_list;  // helicity indices to sum (device)
+    int nlist;
+    int slots;              // lanes per event: power of two, <= 32
+    double norm;            // g^{2k} / (IDEN * colour denominator)
+    double mt;              // top mass (0 for massless fermions)
+    int gauge_ext;          // -1, or external gluon whose polarisation is replaced by its momentum
+    cudaStream_t stream;
+};
+
+enum Precision : int { PREC_FP64 = 0, PREC_FP32 = 1, PREC_MIXED = 2 };
+
+struct ProcDesc {
+    const char* name;
+    int npar, nhel, ncol, ndiag, namp, ngluon, nlines, threads;
+    double iden;               // initial spin x colour average x final identical-particle factor
+    int cden;                  // colour-matrix denominator (C = num / cden)
+    const int* cnum;           // colour numerators [ncol][ncol] (host)
+    long long flops_hel;       // chain flops per helicity (generator count)
+    long long colour_flops_hel;
+    int coupling_power;        // |M|^2 proportional to (4 pi alpha)^coupling_power
+    cudaError_t (*launch)(int precision, const LaunchArgs&);
+};
+
+const ProcDesc* find_process(const char* name);
+
+}  // namespace me

@@ -1,0 +1,269 @@
+// Seeded flat phase-space sampler on the device (arXiv:2507.21039 Sec. 4: the
+// standalone application draws RAMBO points; RAMBO is Kleiss, Stirling, Ellis
+// 1986).  One thread per event; the event depends only on (seed, index), so any
+// range can be regenerated and sharded without communication.
+//
+// Random numbers: Philox4x64-10 (Salmon, Moraes, Dror, Shaw, SC'11), key
+// (seed, 0), counter (event, attempt, final-particle index, 0); one block
+// yields the four uniforms of one final-state particle, u = ((x >> 11) + 1/2) 2^-53.
+#include <cmath>
+#include <cstdint>
+
+#include "me.h"
+
+namespace {
+
+constexpr int kMaxFinal = 6;
+constexpr int kMaxAttempts = 1000;
+
+struct U4 { uint64_t x[4]; };
+
+__device__ __forceinline__ U4 philox4x64_10(uint64_t c0, uint64_t c1, uint64_t c2, uint64_t c3, uint64_t k0,
+                                            uint64_t k1)
+{
+    const uint64_t M0 = 0xD2E7470EE14C6C93ULL, M1 = 0xCA5A826395121157ULL;
+    const uint64_t W0 = 0x9E3779B97F4A7C15ULL, W1 = 0xBB67AE8584CAA73BULL;
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r > 0) {
+            k0 += W0;
+            k1 += W1;
+        }
+        const uint64_t hi0 = __umul64hi(M0, c0), lo0 = M0 * c0;
+        const uint64_t hi1 = __umul64hi(M1, c2), lo1 = M1 * c2;
+        const uint64_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+        c0 = n0;
+        c1 = lo1;
+        c2 = n2;
+        c3 = lo0;
+    }
+    return {{c0, c1, c2, c3}};
+}
+
+__device__ __forceinline__ double u01(uint64_t x) { return ((double)(x >> 11) + 0.5) * 0x1p-53; }
+
+struct Params {
+    uint64_t seed;
+    long long ev0, nevt;
+    double sqrt_s;
+    double m[kMaxFinal];
+    int nfin;
+    bool massive;
+    double msum;
+    double w0;  // massless weight (pi/2)^{n-1} s^{n-2} / ((n-1)!(n-2)!) (2 pi)^{4-3n}
+    double ptmin, drmin;
+    uint32_t cutmask;
+    double* mom;
+    double* wt;
+    unsigned long long* nfail;
+};
+
+__device__ double eta_of(const double* p)
+{
+    const double P = sqrt(p[1] * p[1] + p[2] * p[2] + p[3] * p[3]);
+    return 0.5 * log((P + p[3]) / (P - p[3]));
+}
+
+__device__ bool passes(const double (*k)[4], int n, const Params& a)
+{
+    if (!a.cutmask) return true;
+    for (int i = 0; i < n; ++i) {
+        if (!((a.cutmask >> i) & 1)) continue;
+        if (!(sqrt(k[i][1] * k[i][1] + k[i][2] * k[i][2]) > a.ptmin)) return false;
+    }
+    for (int i = 0; i < n; ++i) {
+        if (!((a.cutmask >> i) & 1)) continue;
+        for (int j = i + 1; j < n; ++j) {
+            if (!((a.cutmask >> j) & 1)) continue;
+            const double de = eta_of(k[i]) - eta_of(k[j]);
+            double dphi = atan2(k[i][2], k[i][1]) - atan2(k[j][2], k[j][1]);
+            while (dphi > M_PI) dphi -= 2.0 * M_PI;
+            while (dphi < -M_PI) dphi += 2.0 * M_PI;
+            if (!(sqrt(de * de + dphi * dphi) > a.drmin)) return false;
+        }
+    }
+    return true;
+}
+
+// one RAMBO point; returns false when the Newton solve does not converge
+__device__ bool rambo_point(const Params& a, long long ev, int attempt, double (*k)[4], double& w)
+{
+    const int n = a.nfin;
+    double q[kMaxFinal][4];
+    double Q0 = 0, Q1 = 0, Q2 = 0, Q3 = 0;
+    for (int j = 0; j < n; ++j) {
+        const U4 r = philox4x64_10((uint64_t)ev, (uint64_t)attempt, (uint64_t)j, 0, a.seed, 0);
+        const double c = 2.0 * u01(r.x[0]) - 1.0;
+        const double s = sqrt(1.0 - c * c);
+        const double f = 2.0 * M_PI * u01(r.x[1]);
+        const double q0 = -log(u01(r.x[2]) * u01(r.x[3]));
+        q[j][0] = q0;
+        q[j][1] = q0 * s * cos(f);
+        q[j][2] = q0 * s * sin(f);
+        q[j][3] = q0 * c;
+        Q0 += q[j][0];
+        Q1 += q[j][1];
+        Q2 += q[j][2];
+        Q3 += q[j][3];
+    }
+    const double M = sqrt(Q0 * Q0 - Q1 * Q1 - Q2 * Q2 - Q3 * Q3);
+    const double b1 = -Q1 / M, b2 = -Q2 / M, b3 = -Q3 / M;
+    const double x = a.sqrt_s / M, gam = Q0 / M, aa = 1.0 / (1.0 + gam);
+    for (int j = 0; j < n; ++j) {
+        const double bq = b1 * q[j][1] + b2 * q[j][2] + b3 * q[j][3];
+        k[j][0] = x * (gam * q[j][0] + bq);
+        k[j][1] = x * (q[j][1] + b1 * q[j][0] + aa * bq * b1);
+        k[j][2] = x * (q[j][2] + b2 * q[j][0] + aa * bq * b2);
+        k[j][3] = x * (q[j][3] + b3 * q[j][0] + aa * bq * b3);
+    }
+    w = a.w0;
+    if (!a.massive) return true;
+    double P2[kMaxFinal];
+    for (int j = 0; j < n; ++j) P2[j] = k[j][0] * k[j][0];
+    const double r = a.msum / a.sqrt_s;
+    double xi = sqrt(1.0 - r * r);
+    bool ok = false;
+    for (int it = 0; it < 50; ++it) {
+        double f = -a.sqrt_s, fp = 0.0;
+        for (int j = 0; j < n; ++j) {
+            const double e = sqrt(a.m[j] * a.m[j] + xi * xi * P2[j]);
+            f += e;
+            fp += xi * P2[j] / e;
+        }
+        if (fabs(f) <= 1e-14 * a.sqrt_s) {
+            ok = true;
+            break;
+        }
+        xi -= f / fp;
+    }
+    if (!ok) return false;
+    double wt2 = 1.0, wt3 = 0.0;
+    for (int j = 0; j < n; ++j) {
+        const double k0 = sqrt(a.m[j] * a.m[j] + xi * xi * P2[j]);
+        k[j][1] *= xi;
+        k[j][2] *= xi;
+        k[j][3] *= xi;
+        k[j][0] = k0;
+        const double kk = xi * sqrt(P2[j]);
+        wt2 *= kk / k0;
+        wt3 += kk * kk / k0;
+    }
+    w *= pow(xi, 2 * n - 3) * wt2 * a.sqrt_s / wt3;
+    return true;
+}
+
+__global__ void rambo_kernel(Params a)
+{
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= a.nevt) return;
+    const long long ev = a.ev0 + i;
+    double k[kMaxFinal][4];
+    double w = 0.0;
+    bool done = false, newton_fail = false;
+    for (int att = 0; att < kMaxAttempts; ++att) {
+        if (!rambo_point(a, ev, att, k, w)) {
+            newton_fail = true;
+            break;
+        }
+        if (passes(k, a.nfin, a)) {
+            done = true;
+            break;
+        }
+    }
+    const int npar = a.nfin + 2;
+    double* o = a.mom + i * npar * 4;
+    const double h = 0.5 * a.sqrt_s;
+    o[0] = h; o[1] = 0.0; o[2] = 0.0; o[3] = h;
+    o[4] = h; o[5] = 0.0; o[6] = 0.0; o[7] = -h;
+    for (int j = 0; j < a.nfin; ++j)
+        for (int mu = 0; mu < 4; ++mu) o[8 + 4 * j + mu] = k[j][mu];
+    if (!done || newton_fail) {
+        w = -1.0;
+        if (a.nfail) atomicAdd(a.nfail, 1ULL);
+    }
+    if (a.wt) a.wt[i] = w;
+}
+
+bool is_dev(const void* p)
+{
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace
+
+extern "C" int rambo_sample(uint64_t seed, int64_t ev0, int64_t nevt, double sqrt_s, const double* masses, int npar,
+                            const me_cuts* cuts, double* momenta_out, double* weights_out, int64_t* nfail_out,
+                            void* cuda_stream)
+{
+    if (nevt < 0 || ev0 < 0 || npar < 3 || npar > kMaxFinal + 2 || !masses) return ME_EINVAL;
+    if (nevt == 0) return ME_OK;
+    if (!momenta_out || !(sqrt_s > 0.0) || masses[0] != 0.0 || masses[1] != 0.0) return ME_EINVAL;
+    Params a{};
+    a.seed = seed;
+    a.ev0 = ev0;
+    a.nevt = nevt;
+    a.sqrt_s = sqrt_s;
+    a.nfin = npar - 2;
+    double msum = 0.0;
+    for (int j = 0; j < a.nfin; ++j) {
+        const double m = masses[2 + j];
+        if (!(m >= 0.0)) return ME_EINVAL;
+        a.m[j] = m;
+        msum += m;
+        if (m > 0.0) a.massive = true;
+    }
+    if (!(msum < sqrt_s)) return ME_EINVAL;
+    a.msum = msum;
+    const int n = a.nfin;
+    double fact1 = 1.0, fact2 = 1.0;
+    for (int i = 2; i <= n - 1; ++i) fact1 *= i;
+    for (int i = 2; i <= n - 2; ++i) fact2 *= i;
+    a.w0 = std::pow(M_PI / 2.0, n - 1) * std::pow(sqrt_s * sqrt_s, n - 2) / (fact1 * fact2) *
+           std::pow(2.0 * M_PI, 4 - 3 * n);
+    if (cuts) {
+        a.ptmin = cuts->ptmin;
+        a.drmin = cuts->drmin;
+        a.cutmask = cuts->final_mask & ((1u << n) - 1u);
+    }
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    const bool dev_m = is_dev(momenta_out);
+    const bool dev_w = !weights_out || is_dev(weights_out);
+    const size_t mbytes = sizeof(double) * 4 * npar * (size_t)nevt;
+    double *d_m = nullptr, *d_w = nullptr;
+    unsigned long long* d_fail = nullptr;
+    int rc = ME_OK;
+    if (!dev_m && cudaMallocAsync(&d_m, mbytes, st) != cudaSuccess) return ME_ENOMEM;
+    if (weights_out && !dev_w && cudaMallocAsync(&d_w, sizeof(double) * nevt, st) != cudaSuccess) rc = ME_ENOMEM;
+    const bool want_fail = nfail_out != nullptr || !dev_m || !dev_w;
+    if (rc == ME_OK && want_fail) {
+        if (cudaMallocAsync(&d_fail, sizeof(unsigned long long), st) != cudaSuccess) rc = ME_ENOMEM;
+        else if (cudaMemsetAsync(d_fail, 0, sizeof(unsigned long long), st) != cudaSuccess) rc = ME_ECUDA;
+    }
+    a.mom = dev_m ? momenta_out : d_m;
+    a.wt = weights_out ? (dev_w ? weights_out : d_w) : nullptr;
+    a.nfail = d_fail;
+    if (rc == ME_OK) {
+        const int th = 128;
+        rambo_kernel<<<(unsigned)((nevt + th - 1) / th), th, 0, st>>>(a);
+        if (cudaGetLastError() != cudaSuccess) rc = ME_ECUDA;
+    }
+    unsigned long long nfail = 0;
+    if (rc == ME_OK && !dev_m && cudaMemcpyAsync(momenta_out, d_m, mbytes, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+        rc = ME_ECUDA;
+    if (rc == ME_OK && d_w && cudaMemcpyAsync(weights_out, d_w, sizeof(double) * nevt, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+        rc = ME_ECUDA;
+    if (rc == ME_OK && d_fail && cudaMemcpyAsync(&nfail, d_fail, sizeof(nfail), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+        rc = ME_ECUDA;
+    if (d_m) cudaFreeAsync(d_m, st);
+    if (d_w) cudaFreeAsync(d_w, st);
+    if (d_fail) cudaFreeAsync(d_fail, st);
+    if (want_fail && cudaStreamSynchronize(st) != cudaSuccess && rc == ME_OK) rc = ME_ECUDA;
+    if (rc == ME_OK && nfail_out) *nfail_out = (int64_t)nfail;
+    if (rc == ME_OK && nfail > 0) rc = ME_ESAMPLER;
+    return rc;
+}

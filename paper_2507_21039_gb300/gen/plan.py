@@ -1,0 +1,230 @@
+"""Evaluation plan of the helicity-amplitude chain for one process.
+
+Sec. 3.1 of arXiv:2507.21039: external wavefunctions (vxxxxx, oxxxxx,
+ixxxxx) are merged into off-shell currents (VVV1P0_1, FFV1_1, ...) until a
+final vertex (FFV1_0, VVV1_0, ...) gives each diagram's amplitude; the
+amplitudes enter the colour-flow partial amplitudes J.  Here every off-shell
+object is computed once per helicity and shared by all diagrams that contain
+it:
+
+* gluon trees  -> vector currents (VVV1P0_1, VVVV{1,3,4}P0_1);
+* quark-line prefixes  ubar G1 S1 ... Gj Sj          -> row spinors    (FFV1_2);
+* quark-line suffixes  S_j G_{j+1} ... Gm v          -> column spinors (FFV1_1);
+* the t tbar pair current  ubar gamma^mu v / q^2     -> vector         (FFV1P0_3).
+
+A diagram (t1 .. tm) with m >= 2 is evaluated as
+FFV1_0(prefix(t1..t_{j-1}), J(t_j), suffix(t_{j+1}..tm)) with the split j chosen
+greedily to reuse what is already planned; a diagram with a single tree (all
+gluons in one tree) is evaluated at the tree's top vertex against the pair
+current: VVV1_0 / VVVV*_0.
+
+Lines: every object carries a momentum.  Gluon clusters S (sets of gluons)
+carry P_S = sum of outgoing momenta (incoming gluons count with -p) and
+1/P_S^2; quark-line propagators carry q = p_t + P_S (S = gluons on the t side)
+and 1/(q^2 - m_t^2).  Both are evaluated per event in FP64.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+from . import diagrams as D
+
+# real flops per routine as implemented in helas.cuh (one FMA = 2 flops)
+FLOPS = {
+    "VVV1P0_1": 136,
+    "VVVV1P0_1": 86, "VVVV3P0_1": 86, "VVVV4P0_1": 86,
+    "FFV1_2": 124, "FFV1_1": 124,
+    "FFV1P0_3": 72,
+    "FFV1_0": 72,
+    "VVV1_0": 90,
+    "VVVV1_0": 70, "VVVV3_0": 70, "VVVV4_0": 70,
+}
+V4NAMES = ("VVVV1", "VVVV3", "VVVV4")
+
+
+@dataclass
+class Line:
+    kind: str          # 'g' gluon cluster, 'q' top propagator
+    gluons: frozenset  # gluon positions (indices into the gluon list)
+
+
+@dataclass
+class Op:
+    kind: str                  # routine name or ext_v / ext_fo / ext_fi
+    args: tuple = ()           # input op indices
+    line: int = -1             # output line (momentum / inverse denominator)
+    mom: tuple = ()            # line indices whose momenta the vertex needs
+    ext: int = -1              # external particle for ext_* ops
+    out: str = "V"             # V, Fo (row spinor), Fi (column spinor), A (amplitude)
+
+
+@dataclass
+class Plan:
+    process: str
+    npar: int
+    gluon_ext: tuple           # external index of each gluon position
+    gluon_incoming: tuple
+    ncol: int
+    ops: list = field(default_factory=list)
+    lines: list = field(default_factory=list)
+    amps: list = field(default_factory=list)   # (op index, ((col, (re, im)), ...))
+    ndiagrams: int = 0
+
+    def flops_per_helicity(self) -> int:
+        f = sum(FLOPS.get(o.kind, 0) for o in self.ops)
+        # J accumulation: each (amp, colour) term is a complex multiply-add by a
+        # Gaussian-integer constant; +-1 / +-i cost one complex add (2 flops)
+        for _, terms in self.amps:
+            for _, c in terms:
+                f += 2 if (abs(c[0]) + abs(c[1]) == 1) else 4
+        return f
+
+    def colour_flops_per_helicity(self) -> int:
+        n = self.ncol
+        # sum_ij C_ij (Re_i Re_j + Im_i Im_j) over the upper triangle, FMA = 2
+        return 2 * (2 * (n * (n + 1) // 2) + 2 * n)
+
+    def counts(self) -> dict:
+        c = {}
+        for o in self.ops:
+            c[o.kind] = c.get(o.kind, 0) + 1
+        return c
+
+
+QCD = {"gg_ttx": 2, "gg_ttxg": 3, "gg_ttxgg": 4, "gg_ttxggg": 5}
+
+
+def build_plan(process: str) -> Plan:
+    if process == "ee_mumu":
+        return _plan_ee()
+    k = QCD[process]
+    npar = k + 2
+    gluon_ext = tuple([0, 1] + list(range(4, npar)))
+    P = Plan(process, npar, gluon_ext, tuple(e < 2 for e in gluon_ext), math.factorial(k))
+    line_idx = {}
+
+    def line(kind, gl):
+        key = (kind, frozenset(gl))
+        if key not in line_idx:
+            line_idx[key] = len(P.lines)
+            P.lines.append(Line(kind, frozenset(gl)))
+        return line_idx[key]
+
+    def add(op):
+        P.ops.append(op)
+        return len(P.ops) - 1
+
+    # external wavefunctions
+    ext_g = [add(Op("ext_v", ext=e, line=line("g", [g]), out="V")) for g, e in enumerate(gluon_ext)]
+    ext_fo = add(Op("ext_fo", ext=2, out="Fo", line=line("q", [])))
+    ext_fi = add(Op("ext_fi", ext=3, out="Fi"))
+    allg = frozenset(range(k))
+
+    cur = {}
+
+    def current(t):
+        key = t.key()
+        if key in cur:
+            return cur[key]
+        if t.kind == "leaf":
+            cur[key] = ext_g[t.gluon]
+            return cur[key]
+        ch = [current(c) for c in t.children]
+        out_line = line("g", t.leaves)
+        if t.kind == "v3":
+            mom = tuple(P.ops[c].line for c in ch)
+            idx = add(Op("VVV1P0_1", tuple(ch), out_line, mom))
+        else:
+            idx = add(Op(V4NAMES[t.struct] + "P0_1", tuple(ch), out_line))
+        cur[key] = idx
+        return idx
+
+    pre = {(): ext_fo}
+    suf = {(): ext_fi}
+
+    def prefix(seq):
+        key = tuple(t.key() for t in seq)
+        if key in pre:
+            return pre[key]
+        base = prefix(seq[:-1])
+        J = current(seq[-1])
+        gl = frozenset().union(*(t.leaves for t in seq))
+        idx = add(Op("FFV1_2", (base, J), line("q", gl), out="Fo"))
+        pre[key] = idx
+        return idx
+
+    def suffix(seq):
+        key = tuple(t.key() for t in seq)
+        if key in suf:
+            return suf[key]
+        base = suffix(seq[1:])
+        J = current(seq[0])
+        gl_t_side = allg - frozenset().union(*(t.leaves for t in seq))
+        idx = add(Op("FFV1_1", (J, base), line("q", gl_t_side), out="Fi"))
+        suf[key] = idx
+        return idx
+
+    pair = None
+
+    def new_objects(d, j):
+        """objects a split would add: missing prefixes, suffixes, currents"""
+        n = 0
+        for r in range(1, j):
+            if tuple(t.key() for t in d[:r]) not in pre:
+                n += 1
+        for r in range(j + 1, len(d)):
+            if tuple(t.key() for t in d[r:]) not in suf:
+                n += 1
+        return n
+
+    pidx = D.permutation_index(k)
+    terms = D.diagrams(k)
+    P.ndiagrams = D.diagram_count(k)
+    # longer diagrams first: their prefixes/suffixes seed the reuse
+    order = sorted(range(len(terms)), key=lambda i: (-len(terms[i]), i))
+    for di in order:
+        d = terms[di]
+        ph = D.diagram_phase(d)
+        col = D.diagram_colour(d)
+        coeffs = []
+        for w, c in sorted(col.items()):
+            coeffs.append((pidx[w], D.cmul(ph, c)))
+        if len(d) == 1:
+            t = d[0]
+            if pair is None:
+                pair = add(Op("FFV1P0_3", (ext_fo, ext_fi), line("g", allg)))
+            ch = [current(c) for c in t.children]
+            if t.kind == "v3":
+                mom = tuple(P.ops[c].line for c in ch)
+                a = add(Op("VVV1_0", tuple(ch) + (pair,), -1, mom, out="A"))
+            else:
+                a = add(Op(V4NAMES[t.struct] + "_0", tuple(ch) + (pair,), -1, out="A"))
+        else:
+            best = min(range(len(d)), key=lambda j: (new_objects(d, j), abs(2 * j - (len(d) - 1))))
+            L = prefix(d[:best])
+            Jm = current(d[best])
+            R = suffix(d[best + 1:])
+            a = add(Op("FFV1_0", (L, Jm, R), -1, out="A"))
+        P.amps.append((a, tuple(coeffs)))
+    return P
+
+
+def _plan_ee() -> Plan:
+    """e-(1) e+(2) -> mu-(3) mu+(4) via one s-channel photon: the e+e- current
+    (FFV1P0_3 of vbar(e+) and u(e-)) contracted with the muon line (FFV1_0)."""
+    P = Plan("ee_mumu", 4, (), (), 1)
+    P.lines = [Line("a", frozenset())]   # photon line: p1 + p2, 1/s
+    P.ops = [
+        Op("ext_fi", ext=0, out="Fi"),      # u(e-)
+        Op("ext_fo", ext=1, out="Fo"),      # vbar(e+)
+        Op("ext_fo", ext=2, out="Fo"),      # ubar(mu-)
+        Op("ext_fi", ext=3, out="Fi"),      # v(mu+)
+        Op("FFV1P0_3", (1, 0), 0),
+        Op("FFV1_0", (2, 4, 3), -1, out="A"),
+    ]
+    # i e gamma at each vertex (charge -1 absorbed in the overall sign), -i/q^2:
+    # i * i * (-i) = i
+    P.amps = [(5, ((0, (0, 1)),))]
+    P.ndiagrams = 1
+    return P

@@ -1,0 +1,115 @@
+"""Test helper: evaluate a generator plan with numpy, one event and helicity.
+
+Checks the generator's host logic (diagram enumeration, colour coefficients,
+phases, reuse of sub-currents) on the CPU.  The routines below restate the
+real-coefficient Lorentz structures that the plan names; external
+wavefunctions come from the pinned oracle.  This is test code only.
+"""
+import numpy as np
+
+G = []
+_s = [np.eye(2), np.array([[0, 1], [1, 0]]), np.array([[0, -1j], [1j, 0]]), np.array([[1, 0], [0, -1]])]
+for _mu in range(4):
+    _g = np.zeros((4, 4), dtype=complex)
+    _g[:2, 2:] = _s[_mu]
+    _g[2:, :2] = _s[_mu] if _mu == 0 else -_s[_mu]
+    G.append(_g)
+METRIC = np.array([1.0, -1.0, -1.0, -1.0])
+
+
+def dot(a, b):
+    return np.sum(METRIC * a * b)
+
+
+def slash(v):
+    return G[0] * v[0] - G[1] * v[1] - G[2] * v[2] - G[3] * v[3]
+
+
+def evaluate(orc, plan, p, h, mt):
+    """Colour-flow amplitudes J (couplings stripped) for event p, helicity h."""
+    npar = plan.npar
+    lam = [1 if (h >> (npar - 1 - i)) & 1 else -1 for i in range(npar)]
+    incoming = [i < 2 for i in range(npar)]
+    out_p = np.array([(-p[i] if incoming[i] else p[i]) for i in range(npar)])
+
+    lines = []
+    for ln in plan.lines:
+        if ln.kind == "a":
+            q = p[0] + p[1]
+            lines.append((q, 1.0 / dot(q, q)))
+        elif ln.kind == "g":
+            q = sum(out_p[plan.gluon_ext[g]] for g in ln.gluons)
+            lines.append((q, 1.0 / dot(q, q) if len(ln.gluons) > 1 else 0.0))
+        else:
+            q = p[2] + sum((out_p[plan.gluon_ext[g]] for g in ln.gluons), np.zeros(4))
+            lines.append((q, 1.0 / (dot(q, q) - mt * mt)))
+
+    mass = {"ee_mumu": 0.0}.get(plan.process, mt)
+    vals = []
+    for op in plan.ops:
+        a = [vals[i] for i in op.args]
+        k = op.kind
+        if k == "ext_v":
+            e = op.ext
+            eps = orc.polvec(p[e], lam[e])
+            vals.append(eps if incoming[e] else np.conj(eps))
+        elif k == "ext_fo":
+            e = op.ext
+            if plan.process == "ee_mumu" and e == 1:
+                vals.append(orc.bar(orc.spinor_v(p[e], 0.0, lam[e])))
+            else:
+                vals.append(orc.bar(orc.spinor_u(p[e], mass, lam[e])))
+        elif k == "ext_fi":
+            e = op.ext
+            if plan.process == "ee_mumu" and e == 0:
+                vals.append(orc.spinor_u(p[e], 0.0, lam[e]))
+            else:
+                vals.append(orc.spinor_v(p[e], mass, lam[e]))
+        elif k == "VVV1P0_1":
+            A, B = a
+            PA, PB = lines[op.mom[0]][0], lines[op.mom[1]][0]
+            k1, k2, k3 = -PA, -PB, PA + PB
+            v = dot(A, B) * (k1 - k2) + B * dot(k2 - k3, A) + A * dot(k3 - k1, B)
+            vals.append(lines[op.line][1] * v)
+        elif k.startswith("VVVV") and k.endswith("P0_1"):
+            A, B, C = a
+            v = _v4(k[:5], A, B, C)
+            vals.append(lines[op.line][1] * v)
+        elif k == "FFV1_2":
+            L, V = a
+            q, inv = lines[op.line]
+            vals.append(inv * (L @ slash(V) @ (slash(q) + mt * np.eye(4))))
+        elif k == "FFV1_1":
+            V, R = a
+            q, inv = lines[op.line]
+            vals.append(inv * ((slash(q) + mt * np.eye(4)) @ slash(V) @ R))
+        elif k == "FFV1P0_3":
+            Fo, Fi = a
+            inv = lines[op.line][1]
+            vals.append(inv * np.array([Fo @ G[mu] @ Fi for mu in range(4)]))
+        elif k == "FFV1_0":
+            Fo, V, Fi = a
+            vals.append(Fo @ slash(V) @ Fi)
+        elif k == "VVV1_0":
+            A, B, Q = a
+            PA, PB = lines[op.mom[0]][0], lines[op.mom[1]][0]
+            k1, k2, k3 = -PA, -PB, PA + PB
+            vals.append(dot(A, B) * dot(k1 - k2, Q) + dot(B, Q) * dot(k2 - k3, A) + dot(Q, A) * dot(k3 - k1, B))
+        elif k.startswith("VVVV") and k.endswith("_0"):
+            A, B, C, Q = a
+            vals.append(dot(_v4(k[:5], A, B, C), Q))
+        else:
+            raise ValueError(k)
+    J = np.zeros(plan.ncol, dtype=complex)
+    for ai, terms in plan.amps:
+        for col, c in terms:
+            J[col] += complex(c[0], c[1]) * vals[ai]
+    return J
+
+
+def _v4(name, A, B, C):
+    if name == "VVVV1":
+        return dot(A, C) * B - dot(B, C) * A
+    if name == "VVVV3":
+        return dot(A, B) * C - dot(B, C) * A
+    return dot(A, B) * C - dot(A, C) * B

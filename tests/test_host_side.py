@@ -1,0 +1,135 @@
+"""Host-side checks that need no GPU: the generator's logic (diagram counts,
+exact colour matrices, colour/phase bookkeeping evaluated against the oracle)
+and the C-ABI library (builds for sm_103a, loads, exports every declared symbol,
+argument validation that happens before any device work)."""
+import ctypes
+import math
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2507_21039_gb300.gen import diagrams as D
+from paper_2507_21039_gb300.gen.colour import colour_matrix
+from paper_2507_21039_gb300.gen.plan import build_plan
+from paper_2507_21039_gb300.workloads import MT, WORKLOADS
+
+from plan_eval import evaluate
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+# ---------------------------------------------------------------- generator
+@pytest.mark.parametrize("k,n,namps", [(2, 3, 3), (3, 16, 18), (4, 123, 159), (5, 1240, 1890)])
+def test_diagram_counts(k, n, namps):
+    assert D.diagram_count(k) == n
+    assert len(D.diagrams(k)) == namps
+
+
+@pytest.mark.parametrize("k", [2, 3, 4, 5])
+def test_generator_colour_matrix_equals_oracle_brute_force(orc, k):
+    num, den = colour_matrix(k)
+    C = orc.colour_matrix(k)
+    # exact: every numerator recovered from the oracle's floating brute force
+    Cn = np.rint(C * den).astype(np.int64)
+    assert np.abs(C * den - Cn).max() < 1e-8 * den
+    assert np.array_equal(Cn, np.array(num, dtype=np.int64))
+    from fractions import Fraction
+    g = 0
+    for row in num:
+        for x in row:
+            g = math.gcd(g, x)
+    assert math.gcd(g, den) == 1  # lowest terms
+
+
+@pytest.mark.parametrize("process", ["gg_ttx", "gg_ttxg", "gg_ttxgg", "gg_ttxggg", "ee_mumu"])
+def test_generator_plan_reproduces_oracle_partial_amplitudes(orc, process):
+    """The generator's diagrams, colour decomposition and phases, evaluated with
+    numpy, give the oracle's colour-ordered partial amplitudes."""
+    P = build_plan(process)
+    w = WORKLOADS[process]
+    mom, _, _ = orc.rambo(w.seed, w.sqrt_s, w.masses_final, 0, 2, w.cut_mask, 20.0, 0.4)
+    rng = np.random.default_rng(5)
+    for p in mom:
+        if process == "ee_mumu":
+            me, hel = orc.me2("ee_mumu", p[None], per_helicity=True)
+            e4 = (4 * math.pi * w.alpha) ** 2
+            for h in range(16):
+                J = evaluate(orc, P, p, h, 0.0)
+                assert abs(abs(J[0]) ** 2 * e4 - hel[0][h]) <= 1e-13 * hel[0].max()
+            continue
+        scale = max(np.abs(orc.partial_amps(process, p, h)).max() for h in range(0, 1 << P.npar, 7))
+        for h in rng.integers(0, 1 << P.npar, size=3 if process != "gg_ttxggg" else 1):
+            J = evaluate(orc, P, p, int(h), MT)
+            A = orc.partial_amps(process, p, int(h))
+            assert np.abs(J - A).max() < 1e-12 * scale
+
+
+def test_generator_flop_counts_positive():
+    for p in ("ee_mumu", "gg_ttx", "gg_ttxg", "gg_ttxgg", "gg_ttxggg"):
+        P = build_plan(p)
+        assert P.flops_per_helicity() > 0
+        assert P.colour_flops_per_helicity() > 0
+
+
+# ---------------------------------------------------------------- C ABI
+def _declared_symbols():
+    src = open(os.path.join(ROOT, "include", "me.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?[\w\s\*]+?\b(\w+)\s*\(", src, flags=re.M)
+    return sorted(set(n for n in names if n not in ("if", "while", "switch")))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2507_21039_gb300 import build as libbuild
+
+    libbuild.build()
+    import paper_2507_21039_gb300 as me
+
+    return me.load()
+
+
+def test_library_exports_every_declared_symbol(lib):
+    import paper_2507_21039_gb300 as me
+
+    declared = _declared_symbols()
+    assert set(declared) == set(me.EXPORTS), declared
+    for name in declared:
+        assert hasattr(lib, name), name
+
+
+def test_library_is_built_for_sm_103a():
+    from paper_2507_21039_gb300 import build as libbuild
+
+    assert "arch=compute_103a,code=sm_103a" in " ".join(libbuild.ARCH)
+    assert os.path.exists(libbuild.LIB)
+
+
+def test_abi_validation_without_device(lib):
+    import paper_2507_21039_gb300 as me
+
+    assert lib.me_strerror(me.ME_EINVAL).decode() == "invalid argument"
+    assert lib.me_version().decode().startswith("libme")
+    h = ctypes.c_void_p()
+    assert lib.me_init(ctypes.byref(h), b"not_a_process", None, 0, None, 0, 0) == me.ME_EINVAL
+    assert lib.me_init(ctypes.byref(h), b"gg_ttx", None, 0, None, 0, 7) == me.ME_EINVAL
+    bad = (ctypes.c_double * 4)(0, 0, 173.0, 172.0)   # t and t~ masses differ
+    assert lib.me_init(ctypes.byref(h), b"gg_ttx", bad, 4, None, 0, 0) == me.ME_EINVAL
+    short = (ctypes.c_double * 3)(0, 0, 173.0)
+    assert lib.me_init(ctypes.byref(h), b"gg_ttx", short, 3, None, 0, 0) == me.ME_EINVAL
+    neg = (ctypes.c_double * 1)(-0.1)
+    assert lib.me_init(ctypes.byref(h), b"gg_ttx", None, 0, neg, 1, 0) == me.ME_EINVAL
+    assert lib.me_init(None, b"gg_ttx", None, 0, None, 0, 0) == me.ME_EINVAL
+    assert lib.me_sigmakin(None, None, 10, None, None) == me.ME_EINVAL
+    assert lib.me_filter_helicities(None, None, 10, None) == me.ME_EINVAL
+    assert lib.me_info(None, None, None, None, None, None) == me.ME_EINVAL
+    m = (ctypes.c_double * 4)(0, 0, 173.0, 173.0)
+    assert lib.rambo_sample(1, 0, 10, 1000.0, m, 2, None, None, None, None, None) == me.ME_EINVAL
+    assert lib.rambo_sample(1, 0, -1, 1000.0, m, 4, None, None, None, None, None) == me.ME_EINVAL
+    assert lib.rambo_sample(1, 0, 0, 1000.0, m, 4, None, None, None, None, None) == me.ME_OK
+    heavy = (ctypes.c_double * 4)(0, 0, 600.0, 600.0)
+    out = (ctypes.c_double * 16)()
+    assert lib.rambo_sample(1, 0, 1, 1000.0, heavy, 4, None, out, None, None, None) == me.ME_EINVAL
+    lib.me_free(None)
