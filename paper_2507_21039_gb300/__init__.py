@@ -15,7 +15,7 @@ import os
 import threading
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "_build", "libme.so")
+LIB_PATH = os.environ.get("ME_LIBRARY") or os.path.join(_HERE, "_build", "libme.so")
 
 ME_OK = 0
 ME_EINVAL = -1

@@ -161,18 +161,28 @@ template <class P, class T> size_t scalar_smem_bytes(int E)
     return b;
 }
 
+// Raise a kernel's dynamic shared-memory limit to `bytes` once (monotone).
+// A failed request leaves no stale error behind for later launches.
+template <class K> cudaError_t ensure_smem(K kernel, size_t bytes, size_t& granted)
+{
+    if (bytes <= 48 * 1024 || bytes <= granted) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return e;
+    }
+    granted = bytes;
+    return cudaSuccess;
+}
+
 template <class P, class T> cudaError_t launch_scalar(const LaunchArgs& a)
 {
     const int E = P::THREADS / a.slots;
     const long long grid = (a.nevt + E - 1) / E;
     const size_t smem = scalar_smem_bytes<P, T>(E);
-    static bool attr_set = false;  // per instantiation; benign race (idempotent)
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(me_kernel_scalar<P, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)scalar_smem_bytes<P, T>(P::THREADS));
-        if (e != cudaSuccess) return e;
-        attr_set = true;
-    }
+    static size_t granted = 0;  // per instantiation; idempotent if raced
+    cudaError_t e = ensure_smem(me_kernel_scalar<P, T>, smem, granted);
+    if (e != cudaSuccess) return e;
     if (grid > 0x7fffffffLL) return cudaErrorInvalidValue;
     me_kernel_scalar<P, T><<<(unsigned)grid, P::THREADS, smem, a.stream>>>(a);
     return cudaGetLastError();

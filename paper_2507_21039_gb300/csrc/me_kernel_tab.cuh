@@ -1,0 +1,127 @@
+// Helicity-recycled |M|^2 kernel: one CTA per event (arXiv:2507.21039 Sec. 3.1
+// chain, Sec. 4.1 colour sum, helicity sum).
+//
+//   1. the event's momenta (FP64) are loaded into shared memory;
+//   2. in FP64, per event: the external wavefunctions for both helicities of
+//      each particle and every line's momentum and 1/(p^2 - m^2); rounded to the
+//      amplitude precision T;
+//   3. the off-shell objects (gluon currents, quark-line prefixes/suffixes,
+//      pair current) are evaluated once per helicity configuration of their own
+//      particles into a shared-memory table, level by level, by all threads;
+//   4. each thread takes one good helicity (or several), evaluates that
+//      helicity's final amplitudes from table operands into the colour-flow
+//      vector J (registers), contracts J^+ C J, and accumulates in FP64;
+//   5. CTA reduction over helicities -> me2[event].
+// The per-thread live state is J plus the operands of the amplitudes in
+// flight, so the chain never spills.
+#pragma once
+#include "me_kernel.cuh"
+
+// Compiler-only ordering point between amplitudes: keeps ptxas from hoisting the
+// shared-memory operand loads of many amplitudes ahead of their use, which
+// would otherwise inflate register pressure past the register file.
+#define ME_SCHED_FENCE() asm volatile("" ::: "memory")
+
+namespace me {
+
+struct __align__(16) TabTask {
+    unsigned short out, in0, in1, in2;
+    unsigned char la, lb, lo, pad0;
+    unsigned int pad1;
+};
+
+__device__ __forceinline__ TabTask ld_task(const TabTask* p)
+{
+    const uint4 v = __ldg(reinterpret_cast<const uint4*>(p));
+    TabTask t;
+    t.out = (unsigned short)(v.x & 0xffff);
+    t.in0 = (unsigned short)(v.x >> 16);
+    t.in1 = (unsigned short)(v.y & 0xffff);
+    t.in2 = (unsigned short)(v.y >> 16);
+    t.la = (unsigned char)(v.z & 0xff);
+    t.lb = (unsigned char)((v.z >> 8) & 0xff);
+    t.lo = (unsigned char)((v.z >> 16) & 0xff);
+    return t;
+}
+
+template <class P, class T> __host__ __device__ constexpr size_t tab_line_offset()
+{
+    return (size_t)P::NPAR * 4 * sizeof(double);
+}
+template <class P, class T> __host__ __device__ constexpr size_t tab_table_offset()
+{
+    return (tab_line_offset<P, T>() + (size_t)P::NLINES * sizeof(Ln<T>) + 15) / 16 * 16;
+}
+template <class P, class T> __host__ __device__ constexpr size_t tab_smem_bytes()
+{
+    return tab_table_offset<P, T>() + (size_t)P::TAB * sizeof(Wf<T>);
+}
+
+template <class P, class T>
+__global__ void __launch_bounds__(P::NT, P::MIN_CTAS) me_kernel_tab(LaunchArgs a)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    constexpr int NPAR = P::NPAR, NL = P::NLINES, NT = P::NT;
+    double* smom = reinterpret_cast<double*>(smem);
+    Ln<T>* sln = reinterpret_cast<Ln<T>*>(smem + tab_line_offset<P, T>());
+    Wf<T>* tab = reinterpret_cast<Wf<T>*>(smem + tab_table_offset<P, T>());
+    __shared__ double red[NT / 32];
+    const int tid = threadIdx.x;
+
+    for (long long e = blockIdx.x; e < a.nevt; e += gridDim.x) {
+        // (a1) momenta
+        const double* g = a.mom + e * NPAR * 4;
+        if ((reinterpret_cast<uintptr_t>(g) & 15) == 0) {
+            if (tid < NPAR * 2)
+                reinterpret_cast<double2*>(smom)[tid] = __ldg(reinterpret_cast<const double2*>(g) + tid);
+        } else {
+            for (int i = tid; i < NPAR * 4; i += NT) smom[i] = __ldg(g + i);
+        }
+        __syncthreads();
+        // (a2, a3 denominators) FP64 per-event data; external wavefunctions are
+        // the first 2*NPAR table entries
+        for (int it = tid; it < 2 * NPAR + NL; it += NT) event_setup<P, T>(smom, it, a.mt, a.gauge_ext, tab, sln);
+        __syncthreads();
+        // (a3) off-shell objects for every helicity configuration of their support
+        P::template tables<T>(tab, sln, (T)a.mt, tid);
+        __syncthreads();
+        // (a4-a6) amplitudes per good helicity, colour sum, FP64 accumulation
+        double acc = 0.0;
+        for (int i = tid; i < a.nlist; i += NT) {
+            const int h = a.hel_list[i];
+            cx<T> J[P::NCOL];
+#pragma unroll
+            for (int c = 0; c < P::NCOL; ++c) J[c] = {T(0), T(0)};
+            P::template amps<T>(tab, h, sln, J);
+            const T v = P::template colour<T>(J);
+            acc += (double)v;
+            if (a.hel_out) a.hel_out[e * a.nlist + i] = (double)v * a.norm;
+        }
+        for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+        if constexpr (NT > 32) {
+            if ((tid & 31) == 0) red[tid >> 5] = acc;
+            __syncthreads();
+            if (tid == 0) {
+                double s = 0.0;
+                for (int w = 0; w < NT / 32; ++w) s += red[w];
+                a.me2[e] = s * a.norm;
+            }
+        } else {
+            if (tid == 0) a.me2[e] = acc * a.norm;
+        }
+        __syncthreads();  // shared memory is reused by the next event
+    }
+}
+
+template <class P, class T> cudaError_t launch_tab(const LaunchArgs& a)
+{
+    constexpr size_t smem = tab_smem_bytes<P, T>();
+    static size_t granted = 0;
+    cudaError_t e = ensure_smem(me_kernel_tab<P, T>, smem, granted);
+    if (e != cudaSuccess) return e;
+    const long long grid = a.nevt < 0x7fffffffLL ? a.nevt : 0x7fffffffLL;
+    me_kernel_tab<P, T><<<(unsigned)grid, P::NT, smem, a.stream>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace me

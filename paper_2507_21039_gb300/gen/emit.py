@@ -12,9 +12,11 @@ import math
 
 from .colour import colour_matrix
 from .plan import Plan, build_plan
+from .tabplan import build_tabplan
 
 EXT_KINDS = {"VIN": 0, "VOUT": 1, "FO_U": 2, "FO_V": 3, "FI_U": 4, "FI_V": 5}
-CHUNK_ROUTINES = ()
+# processes evaluated with the helicity-recycled table kernel (me_kernel_tab.cuh)
+TAB_PROCESSES = {"gg_ttxg": 32, "gg_ttxgg": 64}   # process -> threads per event
 
 
 def _ext_table(process: str):
@@ -123,6 +125,16 @@ def emit_process(process: str) -> tuple[str, dict]:
         cbody.append("  s = fma(a.re, zr, fma(a.im, zi, s));")
         cbody.append("}")
 
+    tab_src, TP = ("", None)
+    if process in TAB_PROCESSES:
+        tab_src, TP = emit_tab_struct(process, TAB_PROCESSES[process], ncol, nlines, cbody)
+    kernel_struct = "ProcTab" if TP else "Proc"
+    launch_fn = "launch_tab" if TP else "launch_scalar"
+    if TP:
+        nhel_all = 1 << npar
+        flops_hel = TP.amplitude_flops_per_helicity() + -(-TP.table_flops() // nhel_all)
+    else:
+        flops_hel = P.flops_per_helicity()
     ns = f"p_{process}"
     cnum_flat = ", ".join(str(x) for row in num for x in row)
     src = f"""// Generated by paper_2507_21039_gb300/gen/emit.py for {process}: do not edit.
@@ -130,6 +142,7 @@ def emit_process(process: str) -> tuple[str, dict]:
 // {ncol} colour flows, {nlines} lines, {P.flops_per_helicity()} chain flops per helicity.
 #include "me_kernel.cuh"
 #include "me_colour_tc.cuh"
+#include "me_kernel_tab.cuh"
 
 namespace me {{
 namespace {ns} {{
@@ -145,6 +158,7 @@ struct Proc {{
     static constexpr int NPAR = {npar}, NCOL = {ncol}, NLINES = {nlines}, THREADS = {threads};
     static constexpr int CDEN = {den};
     static constexpr bool J_SMEM = {"true" if j_smem else "false"};
+    static constexpr bool IS_TAB = false;
     __device__ static __forceinline__ unsigned ext_kind(int e) {{ return c_ext_kind[e]; }}
     __device__ static __forceinline__ unsigned ext_massive(int e) {{ return c_ext_massive[e]; }}
     __device__ static __forceinline__ unsigned line_plus(int l) {{ return c_line_plus[l]; }}
@@ -166,13 +180,13 @@ struct Proc {{
         return s;
     }}
 }};
-
+{tab_src}
 static cudaError_t launch(int precision, const LaunchArgs& a)
 {{
     switch (precision) {{
-    case PREC_FP64: return launch_scalar<Proc, double>(a);
-    case PREC_FP32: return launch_scalar<Proc, float>(a);
-    case PREC_MIXED: return launch_mixed<Proc>(a);
+    case PREC_FP64: return {launch_fn}<{kernel_struct}, double>(a);
+    case PREC_FP32: return {launch_fn}<{kernel_struct}, float>(a);
+    case PREC_MIXED: return launch_mixed<{kernel_struct}>(a);
     default: return cudaErrorInvalidValue;
     }}
 }}
@@ -182,7 +196,7 @@ static cudaError_t launch(int precision, const LaunchArgs& a)
 const ProcDesc* procdesc_{process}()
 {{
     static const ProcDesc d = {{"{process}", {npar}, {1 << npar}, {ncol}, {P.ndiagrams}, {len(P.amps)}, {k}, {nlines},
-                               {threads}, {iden!r}, {den}, {ns}::h_cnum, {P.flops_per_helicity()}LL,
+                               {threads}, {iden!r}, {den}, {ns}::h_cnum, {flops_hel}LL,
                                {P.colour_flops_per_helicity()}LL, {cpow}, &{ns}::launch}};
     return &d;
 }}
@@ -196,12 +210,110 @@ const ProcDesc* procdesc_{process}()
         "nops": len(P.ops),
         "ncol": ncol,
         "nlines": nlines,
-        "flops_per_helicity": P.flops_per_helicity(),
+        "flops_per_helicity": flops_hel,
+        "flops_per_helicity_unrecycled": P.flops_per_helicity(),
+        "table_entries": TP.size if TP else 0,
         "colour_flops_per_helicity": P.colour_flops_per_helicity(),
         "counts": P.counts(),
         "cden": den,
     }
     return src, meta
+
+
+def _support_name(S):
+    return "v_" + "_".join(str(p) for p in S)
+
+
+def _table_call(kind, k="k"):
+    if kind == "VVV1P0_1":
+        return f"VVV1P0_1<T>(tab[{k}.in0], ln[{k}.la].p, tab[{k}.in1], ln[{k}.lb].p, ln[{k}.lo].inv, tab[{k}.out]);"
+    if kind.endswith("P0_1"):
+        return f"{kind}<T>(tab[{k}.in0], tab[{k}.in1], tab[{k}.in2], ln[{k}.lo].inv, tab[{k}.out]);"
+    if kind in ("FFV1_2", "FFV1_1"):
+        return f"{kind}<T>(tab[{k}.in0], tab[{k}.in1], ln[{k}.lo], mt, tab[{k}.out]);"
+    if kind == "FFV1P0_3":
+        return f"FFV1P0_3<T>(tab[{k}.in0], tab[{k}.in1], ln[{k}.lo].inv, tab[{k}.out]);"
+    raise ValueError(kind)
+
+
+def emit_tab_struct(process: str, nt: int, ncol: int, nlines: int, colour_body: list):
+    """ProcTab: task table, level-by-level table rounds, per-helicity amplitudes."""
+    TP = build_tabplan(process)
+    P = TP.plan
+    npar = P.npar
+    tasks = []
+    rounds_code = []
+    prev_level = None
+    for r in TP.rounds:
+        if prev_level is not None and r.level != prev_level:
+            rounds_code.append("__syncthreads();")
+        prev_level = r.level
+        start = len(tasks)
+        for t in r.tasks:
+            ins = list(t.ins) + [0] * (3 - len(t.ins))
+            la, lb, lo = (x if x >= 0 else 0 for x in t.lines)
+            tasks.append((t.out, ins[0], ins[1], ins[2], la, lb, lo))
+        n = len(r.tasks)
+        rounds_code.append(f"for (int t = tid; t < {n}; t += NT) {{ const TabTask k = ld_task(c_tasks + {start} + t); "
+                           f"{_table_call(r.kind)} }}  // level {r.level}: {r.kind}")
+    # amplitude code
+    used = set()
+    acode = []
+    for ai, terms in P.amps:
+        op = P.ops[ai]
+        args = []
+        for a in op.args:
+            S = TP.support[a]
+            used.add(S)
+            args.append(f"tab[{TP.base[a]} + {_support_name(S)}]")
+        if op.kind == "FFV1_0":
+            call = f"FFV1_0<T>({args[0]}, {args[1]}, {args[2]})"
+        elif op.kind == "VVV1_0":
+            la, lb = op.mom
+            call = f"VVV1_0<T>({args[0]}, ln[{la}].p, {args[1]}, ln[{lb}].p, {args[2]})"
+        else:
+            call = f"{op.kind}<T>({args[0]}, {args[1]}, {args[2]}, {args[3]})"
+        acode.append(f"{{ const cx<T> x = {call};")
+        for col, c in terms:
+            acode.append(f"  jacc<{c[0]}, {c[1]}, T>(J[{col}], x);")
+        acode.append("}")
+        acode.append("ME_SCHED_FENCE();")
+    bits = [f"const int b{p} = (h >> {npar - 1 - p}) & 1;" for p in range(npar)]
+    sups = []
+    for S in sorted(used, key=lambda x: (len(x), x)):
+        expr = " | ".join(f"(b{p} << {j})" if j else f"b{p}" for j, p in enumerate(S))
+        sups.append(f"const int {_support_name(S)} = {expr};")
+    task_init = ",\n    ".join("{%d, %d, %d, %d, %d, %d, %d, 0, 0}" % t for t in tasks)
+    nl = "\n"
+    return f"""
+__device__ const TabTask c_tasks[{max(len(tasks), 1)}] = {{
+    {task_init if tasks else "{0, 0, 0, 0, 0, 0, 0, 0, 0}"}
+}};
+
+// helicity-recycled evaluation: {TP.size} table entries, {len(tasks)} table tasks,
+// {TP.table_flops()} table flops per event, {TP.amplitude_flops_per_helicity()} amplitude flops per helicity
+struct ProcTab : Proc {{
+    static constexpr int NT = {nt}, TAB = {TP.size};
+    static constexpr int MIN_CTAS = {max(1, 65536 // (nt * 128))};   // <= 128 registers per thread
+    static constexpr bool IS_TAB = true;
+    static constexpr long long TABLE_FLOPS = {TP.table_flops()}LL, AMP_FLOPS = {TP.amplitude_flops_per_helicity()}LL;
+
+    template <class T>
+    __device__ static __forceinline__ void tables(Wf<T>* __restrict__ tab, const Ln<T>* __restrict__ ln, T mt, int tid)
+    {{
+        (void)mt;
+{nl.join("        " + x for x in rounds_code)}
+    }}
+
+    template <class T, class JT>
+    __device__ static __forceinline__ void amps(const Wf<T>* __restrict__ tab, int h, const Ln<T>* __restrict__ ln, JT& J)
+    {{
+{nl.join("        " + x for x in bits)}
+{nl.join("        " + x for x in sups)}
+{nl.join("        " + x for x in acode)}
+    }}
+}};
+""", TP
 
 
 PROCESSES = ("ee_mumu", "gg_ttx", "gg_ttxg", "gg_ttxgg", "gg_ttxggg")

@@ -1,0 +1,119 @@
+"""Helicity-recycled evaluation layout for the shared-memory table kernel.
+
+Every off-shell object of the chain (gluon-tree currents, quark-line prefixes
+and suffixes, the t tbar pair current) depends only on the helicities of its
+own external particles -- its *support*.  Instead of recomputing it for each of
+the event's helicity configurations (2^npar), the kernel evaluates each object
+once per configuration of its support (2^|support| variants) into a per-event
+shared-memory table; the lanes of the event then evaluate only the final
+amplitudes (FFV1_0, VVV1_0, VVVV*_0) for their own helicity, reading operands
+from the tables.  The Feynman diagrams, vertices and colour coefficients are
+exactly those of the plan (Sec. 3.1 of arXiv:2507.21039); only the reuse of
+sub-expressions across helicities is new.
+
+Table layout (units of one wavefunction, Wf = 4 complex numbers):
+  [0, 2*npar)           external wavefunctions: particle e, helicity bit b at 2e+b
+  then, per object X    2^|S_X| consecutive variants; variant index
+                        v = sum_j b(p_j) << j over the support particles
+                        p_0 < p_1 < ... (b = 1 for helicity +1).
+Helicity index h: particle i has helicity +1 iff bit (npar-1-i) of h is set.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+from .plan import FLOPS, Plan, build_plan
+
+
+@dataclass
+class Task:
+    out: int
+    ins: tuple
+    lines: tuple   # (la, lb, lo) line indices used by the routine (-1 if unused)
+
+
+@dataclass
+class Round:
+    level: int
+    kind: str
+    tasks: list = field(default_factory=list)
+
+
+@dataclass
+class TabPlan:
+    plan: Plan
+    support: dict            # op index -> tuple of particles (sorted)
+    base: dict               # op index -> table base (Wf units)
+    size: int                # table size (Wf units)
+    rounds: list             # Round, in dependency order
+    nlevels: int
+    amp_supports: list       # distinct supports of amplitude operands
+
+    def table_flops(self) -> int:
+        return sum(FLOPS[r.kind] * len(r.tasks) for r in self.rounds)
+
+    def amplitude_flops_per_helicity(self) -> int:
+        P = self.plan
+        f = sum(FLOPS[P.ops[a].kind] for a, _ in P.amps)
+        for _, terms in P.amps:
+            for _, c in terms:
+                f += 2 if (abs(c[0]) + abs(c[1]) == 1) else 4
+        return f
+
+
+def _support(P: Plan, i: int, memo: dict):
+    if i in memo:
+        return memo[i]
+    op = P.ops[i]
+    if op.kind.startswith("ext_"):
+        s = (op.ext,)
+    else:
+        acc = set()
+        for a in op.args:
+            acc |= set(_support(P, a, memo))
+        s = tuple(sorted(acc))
+    memo[i] = s
+    return s
+
+
+def compress(full_bits: dict, support) -> int:
+    """variant index of `support` given particle -> bit"""
+    return sum(full_bits[p] << j for j, p in enumerate(support))
+
+
+def build_tabplan(process: str) -> TabPlan:
+    P = build_plan(process)
+    memo = {}
+    sup = {i: _support(P, i, memo) for i in range(len(P.ops))}
+    base = {}
+    for i, op in enumerate(P.ops):
+        if op.kind.startswith("ext_"):
+            base[i] = 2 * op.ext
+    nxt = 2 * P.npar
+    level = {}
+    for i, op in enumerate(P.ops):
+        if op.kind.startswith("ext_"):
+            level[i] = 0
+        else:
+            level[i] = 1 + max(level[a] for a in op.args)
+        if op.out != "A" and not op.kind.startswith("ext_"):
+            base[i] = nxt
+            nxt += 1 << len(sup[i])
+    rounds = {}
+    for i, op in enumerate(P.ops):
+        if op.out == "A" or op.kind.startswith("ext_"):
+            continue
+        key = (level[i], op.kind)
+        r = rounds.setdefault(key, Round(level[i], op.kind))
+        S = sup[i]
+        for v in range(1 << len(S)):
+            bits = {p: (v >> j) & 1 for j, p in enumerate(S)}
+            ins = tuple(base[a] + compress(bits, sup[a]) for a in op.args)
+            if op.kind == "VVV1P0_1":
+                ln = (op.mom[0], op.mom[1], op.line)
+            else:
+                ln = (-1, -1, op.line)
+            r.tasks.append(Task(base[i] + v, ins, ln))
+    order = sorted(rounds, key=lambda k: (k[0], k[1]))
+    amp_sup = sorted({sup[a] for ai, _ in P.amps for a in P.ops[ai].args}, key=lambda s: (len(s), s))
+    return TabPlan(P, sup, base, nxt, [rounds[k] for k in order], max(k[0] for k in order) if order else 0, amp_sup)
