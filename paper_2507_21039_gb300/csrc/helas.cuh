@@ -240,58 +240,62 @@ template <int R, int I, class T, class C> __device__ __forceinline__ void jacc(C
 // ---------------------------------------------------------------------------
 // external wavefunctions (evaluated per event in FP64, then rounded to T)
 // ---------------------------------------------------------------------------
+// In FP64 mode these run in FP64; in FP32 / mixed mode in FP32 from the
+// rounded momenta (their relative error, ~1e-7, is that of the FP32 chain).
+__device__ __forceinline__ double rsq(double x) { return rsqrt(x); }
+__device__ __forceinline__ float rsq(float x) { return rsqrtf(x); }
+
 // two-spinors chi_lam(p): chi_+ = (P+pz, px+i py)/n, chi_- = (-px+i py, P+pz)/n,
 // n = sqrt(2P(P+pz)); p along -z: chi_+ = (0,1), chi_- = (-1,0); at rest along +z.
-__device__ __forceinline__ void chi2(const double* p, int lam, cx<double>* out)
+template <class C> __device__ __forceinline__ void chi2(const C* p, int lam, cx<C>* out)
 {
-    const double px = p[1], py = p[2], pz = p[3];
-    const double pt2 = px * px + py * py;
-    const double P = sqrt(pt2 + pz * pz);
-    if (P == 0.0) {
-        out[0] = {lam > 0 ? 1.0 : 0.0, 0.0};
-        out[1] = {lam > 0 ? 0.0 : 1.0, 0.0};
+    const C px = p[1], py = p[2], pz = p[3];
+    const C pt2 = px * px + py * py;
+    const C P = sqrt(pt2 + pz * pz);
+    if (P == C(0)) {
+        out[0] = {lam > 0 ? C(1) : C(0), C(0)};
+        out[1] = {lam > 0 ? C(0) : C(1), C(0)};
         return;
     }
-    const double ppz = pz >= 0.0 ? P + pz : pt2 / (P - pz);
-    if (ppz == 0.0) {
-        out[0] = {lam > 0 ? 0.0 : -1.0, 0.0};
-        out[1] = {lam > 0 ? 1.0 : 0.0, 0.0};
+    const C ppz = pz >= C(0) ? P + pz : pt2 / (P - pz);
+    if (ppz == C(0)) {
+        out[0] = {lam > 0 ? C(0) : C(-1), C(0)};
+        out[1] = {lam > 0 ? C(1) : C(0), C(0)};
         return;
     }
-    const double rn = rsqrt(2.0 * P * ppz);
+    const C rn = rsq(C(2) * P * ppz);
     if (lam > 0) {
-        out[0] = {ppz * rn, 0.0};
+        out[0] = {ppz * rn, C(0)};
         out[1] = {px * rn, py * rn};
     } else {
         out[0] = {-px * rn, py * rn};
-        out[1] = {ppz * rn, 0.0};
+        out[1] = {ppz * rn, C(0)};
     }
 }
 
 // omega_+ = sqrt(E + |p|), omega_- = m / sqrt(E + |p|)
-__device__ __forceinline__ void omegas(const double* p, double m, double& wp, double& wm)
+template <class C> __device__ __forceinline__ void omegas(const C* p, C m, C& wp, C& wm)
 {
-    const double P = sqrt(p[1] * p[1] + p[2] * p[2] + p[3] * p[3]);
+    const C P = sqrt(p[1] * p[1] + p[2] * p[2] + p[3] * p[3]);
     wp = sqrt(p[0] + P);
-    wm = m == 0.0 ? 0.0 : m / wp;
+    wm = m == C(0) ? C(0) : m / wp;
 }
 
 // ixxxxx: flowing-in spinor; nsf = +1 -> u(p, lam) (incoming fermion),
 // nsf = -1 -> v(p, lam) (outgoing antifermion)
-__device__ __forceinline__ void ixxxxx(const double* p, double m, int lam, int nsf, cx<double>* w)
+template <class C> __device__ __forceinline__ void ixxxxx(const C* p, C m, int lam, int nsf, cx<C>* w)
 {
-    double wp, wm;
+    C wp, wm;
     omegas(p, m, wp, wm);
-    cx<double> c[2];
+    cx<C> c[2];
+    const C wl = lam > 0 ? wp : wm, wml = lam > 0 ? wm : wp;
     if (nsf > 0) {
         chi2(p, lam, c);
-        const double wl = lam > 0 ? wp : wm, wml = lam > 0 ? wm : wp;
         w[0] = wml * c[0]; w[1] = wml * c[1];
         w[2] = wl * c[0];  w[3] = wl * c[1];
     } else {
         chi2(p, -lam, c);
-        const double wl = lam > 0 ? wp : wm, wml = lam > 0 ? wm : wp;
-        const double sl = lam > 0 ? 1.0 : -1.0;
+        const C sl = lam > 0 ? C(1) : C(-1);
         w[0] = (-sl * wl) * c[0]; w[1] = (-sl * wl) * c[1];
         w[2] = (sl * wml) * c[0]; w[3] = (sl * wml) * c[1];
     }
@@ -299,9 +303,9 @@ __device__ __forceinline__ void ixxxxx(const double* p, double m, int lam, int n
 
 // oxxxxx: flowing-out (barred) spinor; nsf = +1 -> ubar(p, lam) (outgoing
 // fermion), nsf = -1 -> vbar(p, lam) (incoming antifermion).  psibar = psi^+ gamma^0.
-__device__ __forceinline__ void oxxxxx(const double* p, double m, int lam, int nsf, cx<double>* w)
+template <class C> __device__ __forceinline__ void oxxxxx(const C* p, C m, int lam, int nsf, cx<C>* w)
 {
-    cx<double> s[4];
+    cx<C> s[4];
     ixxxxx(p, m, lam, nsf, s);
     w[0] = {s[2].re, -s[2].im};
     w[1] = {s[3].re, -s[3].im};
@@ -312,20 +316,20 @@ __device__ __forceinline__ void oxxxxx(const double* p, double m, int lam, int n
 // vxxxxx: massless vector boson polarisation eps(k, lam) = (-lam e1 - i e2)/sqrt2,
 // e1 = (0, ct cf, ct sf, -st), e2 = (0, -sf, cf, 0); nsv = -1 incoming (eps),
 // nsv = +1 outgoing (conj eps)
-__device__ __forceinline__ void vxxxxx(const double* k, int lam, int nsv, cx<double>* w)
+template <class C> __device__ __forceinline__ void vxxxxx(const C* k, int lam, int nsv, cx<C>* w)
 {
-    const double kx = k[1], ky = k[2], kz = k[3];
-    const double pt = sqrt(kx * kx + ky * ky);
-    const double P = sqrt(pt * pt + kz * kz);
-    const double ct = kz / P, st = pt / P;
-    const double cf = pt > 0.0 ? kx / pt : 1.0, sf = pt > 0.0 ? ky / pt : 0.0;
-    const double r2 = 0.70710678118654752440;
-    const double sl = lam > 0 ? 1.0 : -1.0;
-    const double im_sign = nsv < 0 ? 1.0 : -1.0;   // conj for outgoing
-    w[0] = {0.0, 0.0};
+    const C kx = k[1], ky = k[2], kz = k[3];
+    const C pt = sqrt(kx * kx + ky * ky);
+    const C P = sqrt(pt * pt + kz * kz);
+    const C ct = kz / P, st = pt / P;
+    const C cf = pt > C(0) ? kx / pt : C(1), sf = pt > C(0) ? ky / pt : C(0);
+    const C r2 = C(0.70710678118654752440);
+    const C sl = lam > 0 ? C(1) : C(-1);
+    const C im_sign = nsv < 0 ? C(1) : C(-1);   // conj for outgoing
+    w[0] = {C(0), C(0)};
     w[1] = {-sl * ct * cf * r2, im_sign * sf * r2};
     w[2] = {-sl * ct * sf * r2, -im_sign * cf * r2};
-    w[3] = {sl * st * r2, 0.0};
+    w[3] = {sl * st * r2, C(0)};
 }
 
 }  // namespace me

@@ -39,53 +39,64 @@ template <class T, int STRIDE> struct JSmem {
     __device__ __forceinline__ cx<T>& operator[](int c) const { return base[c * STRIDE]; }
 };
 
+// External wavefunction `item` = 2 e + b (particle e, helicity bit b), computed
+// in the amplitude precision T from the FP64 momenta
+template <class P, class T>
+__device__ __forceinline__ Wf<T> ext_wavefunction(const double* __restrict__ p, int item, double mt, int gauge_ext)
+{
+    const int e = item >> 1, b = item & 1, lam = b ? 1 : -1;
+    T pe[4];
+#pragma unroll
+    for (int mu = 0; mu < 4; ++mu) pe[mu] = (T)p[4 * e + mu];
+    const T m = P::ext_massive(e) ? (T)mt : T(0);
+    Wf<T> o;
+    if (e == gauge_ext) {  // diagnostic: gluon polarisation replaced by its momentum
+        for (int mu = 0; mu < 4; ++mu) o.c[mu] = {pe[mu], T(0)};
+        return o;
+    }
+    switch (P::ext_kind(e)) {
+    case VIN: vxxxxx<T>(pe, lam, -1, o.c); break;
+    case VOUT: vxxxxx<T>(pe, lam, +1, o.c); break;
+    case FO_U: oxxxxx<T>(pe, m, lam, +1, o.c); break;
+    case FO_V: oxxxxx<T>(pe, m, lam, -1, o.c); break;
+    case FI_U: ixxxxx<T>(pe, m, lam, +1, o.c); break;
+    default: ixxxxx<T>(pe, m, lam, -1, o.c); break;
+    }
+    return o;
+}
+
+// Line l: momentum (signed sum of external momenta, FP64) and 1/(p^2 - m^2)
+template <class P, class T> __device__ __forceinline__ Ln<T> line_data(const double* __restrict__ p, int l, double mt)
+{
+    const unsigned plus = P::line_plus(l), minus = P::line_minus(l);
+    double q[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int e = 0; e < P::NPAR; ++e) {
+        const double s = ((plus >> e) & 1) ? 1.0 : (((minus >> e) & 1) ? -1.0 : 0.0);
+        if (s != 0.0)
+            for (int mu = 0; mu < 4; ++mu) q[mu] += s * p[4 * e + mu];
+    }
+    const unsigned kind = P::line_kind(l);
+    Ln<T> o;
+    o.inv = T(0);
+    if (kind != L_EXT) {
+        // the denominator p^2 - m^2 in FP64: its cancellation near collinear
+        // and soft limits is what FP32 cannot resolve; once formed, rounding it
+        // to T keeps T's relative precision, so the reciprocal is taken in T
+        const double m2 = kind == L_MASSIVE ? mt * mt : 0.0;
+        const double d = q[0] * q[0] - q[1] * q[1] - q[2] * q[2] - q[3] * q[3] - m2;
+        o.inv = T(1) / (T)d;
+    }
+#pragma unroll
+    for (int mu = 0; mu < 4; ++mu) o.p[mu] = (T)q[mu];
+    return o;
+}
+
 template <class P, class T>
 __device__ __forceinline__ void event_setup(const double* __restrict__ p, int item, double mt, int gauge_ext,
                                             Wf<T>* __restrict__ ext, Ln<T>* __restrict__ ln)
 {
-    if (item < 2 * P::NPAR) {
-        const int e = item >> 1, b = item & 1, lam = b ? 1 : -1;
-        const double* pe = p + 4 * e;
-        const double m = P::ext_massive(e) ? mt : 0.0;
-        cx<double> w[4];
-        if (e == gauge_ext) {  // diagnostic: gluon polarisation replaced by its momentum
-            for (int mu = 0; mu < 4; ++mu) w[mu] = {pe[mu], 0.0};
-        } else {
-            switch (P::ext_kind(e)) {
-            case VIN: vxxxxx(pe, lam, -1, w); break;
-            case VOUT: vxxxxx(pe, lam, +1, w); break;
-            case FO_U: oxxxxx(pe, m, lam, +1, w); break;
-            case FO_V: oxxxxx(pe, m, lam, -1, w); break;
-            case FI_U: ixxxxx(pe, m, lam, +1, w); break;
-            default: ixxxxx(pe, m, lam, -1, w); break;
-            }
-        }
-        Wf<T>& o = ext[item];
-#pragma unroll
-        for (int mu = 0; mu < 4; ++mu) o.c[mu] = {(T)w[mu].re, (T)w[mu].im};
-    } else {
-        const int l = item - 2 * P::NPAR;
-        const unsigned plus = P::line_plus(l), minus = P::line_minus(l);
-        double q[4] = {0.0, 0.0, 0.0, 0.0};
-        for (int e = 0; e < P::NPAR; ++e) {
-            const double s = ((plus >> e) & 1) ? 1.0 : (((minus >> e) & 1) ? -1.0 : 0.0);
-            if (s != 0.0)
-                for (int mu = 0; mu < 4; ++mu) q[mu] += s * p[4 * e + mu];
-        }
-        const unsigned kind = P::line_kind(l);
-        double inv = 0.0;
-        if (kind != L_EXT) {
-            // the denominator p^2 - m^2 in FP64: its cancellation near collinear
-            // and soft limits is what FP32 cannot resolve
-            const double m2 = kind == L_MASSIVE ? mt * mt : 0.0;
-            const double d = q[0] * q[0] - q[1] * q[1] - q[2] * q[2] - q[3] * q[3] - m2;
-            inv = 1.0 / d;
-        }
-        Ln<T>& o = ln[l];
-#pragma unroll
-        for (int mu = 0; mu < 4; ++mu) o.p[mu] = (T)q[mu];
-        o.inv = (T)inv;
-    }
+    if (item < 2 * P::NPAR) ext[item] = ext_wavefunction<P, T>(p, item, mt, gauge_ext);
+    else ln[item - 2 * P::NPAR] = line_data<P, T>(p, item - 2 * P::NPAR, mt);
 }
 
 // Scalar colour contraction and helicity sum.  T: chain/colour precision.

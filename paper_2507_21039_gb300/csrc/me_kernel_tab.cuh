@@ -2,9 +2,9 @@
 // chain, Sec. 4.1 colour sum, helicity sum).
 //
 //   1. the event's momenta (FP64) are loaded into shared memory;
-//   2. in FP64, per event: the external wavefunctions for both helicities of
-//      each particle and every line's momentum and 1/(p^2 - m^2); rounded to the
-//      amplitude precision T;
+//   2. per event: the external wavefunctions for both helicities of each
+//      particle (in the amplitude precision T) and every line's momentum and
+//      1/(p^2 - m^2) (momentum sums and p^2 - m^2 in FP64);
 //   3. the off-shell objects (gluon currents, quark-line prefixes/suffixes,
 //      pair current) are evaluated once per helicity configuration of their own
 //      particles into a shared-memory table, level by level, by all threads;
@@ -17,10 +17,23 @@
 #pragma once
 #include "me_kernel.cuh"
 
-// Compiler-only ordering point between amplitudes: keeps ptxas from hoisting the
-// shared-memory operand loads of many amplitudes ahead of their use, which
-// would otherwise inflate register pressure past the register file.
-#define ME_SCHED_FENCE() asm volatile("" ::: "memory")
+// Ordering point between amplitudes (a warp barrier, which ptxas does not move
+// shared-memory loads across): keeps the operand loads of many amplitudes from
+// being hoisted ahead of their use, which would push register pressure past the
+// register file and spill.
+#ifndef ME_FENCE_EVERY_F
+#define ME_FENCE_EVERY_F 1
+#endif
+#ifndef ME_FENCE_EVERY_D
+#define ME_FENCE_EVERY_D 4
+#endif
+// fence after amplitude i: every amplitude in FP32 (tight register budget),
+// every few in FP64 (its long-latency pipe needs the cross-amplitude ILP)
+#define ME_FENCE(T, i)                                                                            \
+    do {                                                                                          \
+        if constexpr (((i) + 1) % (sizeof(T) == 8 ? ME_FENCE_EVERY_D : ME_FENCE_EVERY_F) == 0) \
+            __syncwarp();                                                                         \
+    } while (0)
 
 namespace me {
 
@@ -44,6 +57,29 @@ __device__ __forceinline__ TabTask ld_task(const TabTask* p)
     return t;
 }
 
+// Tables are stored as planes of 16-byte chunks: chunk c of entry i lives at
+// c * TAB + i.  Lanes that read consecutive variants then touch consecutive
+// banks (a plain array of 32- or 64-byte entries makes 2- or 4-way conflicts).
+template <class T> struct Chunks { static constexpr int N = (int)(sizeof(Wf<T>) / 16); };
+
+template <class T, int TAB> struct TabRef {
+    uint4* base;
+    __device__ __forceinline__ Wf<T> ld(int i) const
+    {
+        Wf<T> w;
+        uint4* dst = reinterpret_cast<uint4*>(&w);
+#pragma unroll
+        for (int c = 0; c < Chunks<T>::N; ++c) dst[c] = base[c * TAB + i];
+        return w;
+    }
+    __device__ __forceinline__ void st(int i, const Wf<T>& w) const
+    {
+        const uint4* src = reinterpret_cast<const uint4*>(&w);
+#pragma unroll
+        for (int c = 0; c < Chunks<T>::N; ++c) base[c * TAB + i] = src[c];
+    }
+};
+
 template <class P, class T> __host__ __device__ constexpr size_t tab_line_offset()
 {
     return (size_t)P::NPAR * 4 * sizeof(double);
@@ -58,13 +94,13 @@ template <class P, class T> __host__ __device__ constexpr size_t tab_smem_bytes(
 }
 
 template <class P, class T>
-__global__ void __launch_bounds__(P::NT, P::MIN_CTAS) me_kernel_tab(LaunchArgs a)
+__global__ void __launch_bounds__(P::NT, sizeof(T) == 8 ? P::MIN_CTAS_D : P::MIN_CTAS_F) me_kernel_tab(LaunchArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     constexpr int NPAR = P::NPAR, NL = P::NLINES, NT = P::NT;
     double* smom = reinterpret_cast<double*>(smem);
     Ln<T>* sln = reinterpret_cast<Ln<T>*>(smem + tab_line_offset<P, T>());
-    Wf<T>* tab = reinterpret_cast<Wf<T>*>(smem + tab_table_offset<P, T>());
+    const TabRef<T, P::TAB> tab{reinterpret_cast<uint4*>(smem + tab_table_offset<P, T>())};
     __shared__ double red[NT / 32];
     const int tid = threadIdx.x;
 
@@ -80,7 +116,10 @@ __global__ void __launch_bounds__(P::NT, P::MIN_CTAS) me_kernel_tab(LaunchArgs a
         __syncthreads();
         // (a2, a3 denominators) FP64 per-event data; external wavefunctions are
         // the first 2*NPAR table entries
-        for (int it = tid; it < 2 * NPAR + NL; it += NT) event_setup<P, T>(smom, it, a.mt, a.gauge_ext, tab, sln);
+        for (int it = tid; it < 2 * NPAR + NL; it += NT) {
+            if (it < 2 * NPAR) tab.st(it, ext_wavefunction<P, T>(smom, it, a.mt, a.gauge_ext));
+            else sln[it - 2 * NPAR] = line_data<P, T>(smom, it - 2 * NPAR, a.mt);
+        }
         __syncthreads();
         // (a3) off-shell objects for every helicity configuration of their support
         P::template tables<T>(tab, sln, (T)a.mt, tid);

@@ -226,14 +226,16 @@ def _support_name(S):
 
 def _table_call(kind, k="k"):
     if kind == "VVV1P0_1":
-        return f"VVV1P0_1<T>(tab[{k}.in0], ln[{k}.la].p, tab[{k}.in1], ln[{k}.lb].p, ln[{k}.lo].inv, tab[{k}.out]);"
-    if kind.endswith("P0_1"):
-        return f"{kind}<T>(tab[{k}.in0], tab[{k}.in1], tab[{k}.in2], ln[{k}.lo].inv, tab[{k}.out]);"
-    if kind in ("FFV1_2", "FFV1_1"):
-        return f"{kind}<T>(tab[{k}.in0], tab[{k}.in1], ln[{k}.lo], mt, tab[{k}.out]);"
-    if kind == "FFV1P0_3":
-        return f"FFV1P0_3<T>(tab[{k}.in0], tab[{k}.in1], ln[{k}.lo].inv, tab[{k}.out]);"
-    raise ValueError(kind)
+        c = f"VVV1P0_1<T>(tab.ld({k}.in0), ln[{k}.la].p, tab.ld({k}.in1), ln[{k}.lb].p, ln[{k}.lo].inv, o);"
+    elif kind.endswith("P0_1"):
+        c = f"{kind}<T>(tab.ld({k}.in0), tab.ld({k}.in1), tab.ld({k}.in2), ln[{k}.lo].inv, o);"
+    elif kind in ("FFV1_2", "FFV1_1"):
+        c = f"{kind}<T>(tab.ld({k}.in0), tab.ld({k}.in1), ln[{k}.lo], mt, o);"
+    elif kind == "FFV1P0_3":
+        c = f"FFV1P0_3<T>(tab.ld({k}.in0), tab.ld({k}.in1), ln[{k}.lo].inv, o);"
+    else:
+        raise ValueError(kind)
+    return f"Wf<T> o; {c} tab.st({k}.out, o);"
 
 
 def emit_tab_struct(process: str, nt: int, ncol: int, nlines: int, colour_body: list):
@@ -259,13 +261,13 @@ def emit_tab_struct(process: str, nt: int, ncol: int, nlines: int, colour_body: 
     # amplitude code
     used = set()
     acode = []
-    for ai, terms in P.amps:
+    for n_amp, (ai, terms) in enumerate(P.amps):
         op = P.ops[ai]
         args = []
         for a in op.args:
             S = TP.support[a]
             used.add(S)
-            args.append(f"tab[{TP.base[a]} + {_support_name(S)}]")
+            args.append(f"tab.ld({TP.base[a]} + {_support_name(S)})")
         if op.kind == "FFV1_0":
             call = f"FFV1_0<T>({args[0]}, {args[1]}, {args[2]})"
         elif op.kind == "VVV1_0":
@@ -277,7 +279,7 @@ def emit_tab_struct(process: str, nt: int, ncol: int, nlines: int, colour_body: 
         for col, c in terms:
             acode.append(f"  jacc<{c[0]}, {c[1]}, T>(J[{col}], x);")
         acode.append("}")
-        acode.append("ME_SCHED_FENCE();")
+        acode.append(f"ME_FENCE(T, {n_amp});")
     bits = [f"const int b{p} = (h >> {npar - 1 - p}) & 1;" for p in range(npar)]
     sups = []
     for S in sorted(used, key=lambda x: (len(x), x)):
@@ -294,19 +296,21 @@ __device__ const TabTask c_tasks[{max(len(tasks), 1)}] = {{
 // {TP.table_flops()} table flops per event, {TP.amplitude_flops_per_helicity()} amplitude flops per helicity
 struct ProcTab : Proc {{
     static constexpr int NT = {nt}, TAB = {TP.size};
-    static constexpr int MIN_CTAS = {max(1, 65536 // (nt * 128))};   // <= 128 registers per thread
+    // register budget: FP32 <= 128 per thread (occupancy bound by shared memory
+    // anyway), FP64 <= 255 (its tables are twice as large)
+    static constexpr int MIN_CTAS_F = {max(1, 65536 // (nt * 128))}, MIN_CTAS_D = {max(1, 65536 // (nt * 255))};
     static constexpr bool IS_TAB = true;
     static constexpr long long TABLE_FLOPS = {TP.table_flops()}LL, AMP_FLOPS = {TP.amplitude_flops_per_helicity()}LL;
 
     template <class T>
-    __device__ static __forceinline__ void tables(Wf<T>* __restrict__ tab, const Ln<T>* __restrict__ ln, T mt, int tid)
+    __device__ static __forceinline__ void tables(const TabRef<T, TAB>& tab, const Ln<T>* __restrict__ ln, T mt, int tid)
     {{
         (void)mt;
 {nl.join("        " + x for x in rounds_code)}
     }}
 
     template <class T, class JT>
-    __device__ static __forceinline__ void amps(const Wf<T>* __restrict__ tab, int h, const Ln<T>* __restrict__ ln, JT& J)
+    __device__ static __forceinline__ void amps(const TabRef<T, TAB>& tab, int h, const Ln<T>* __restrict__ ln, JT& J)
     {{
 {nl.join("        " + x for x in bits)}
 {nl.join("        " + x for x in sups)}
