@@ -1,0 +1,351 @@
+#!/usr/bin/env python
+"""Benchmark: |M|^2 events/s for g g -> t tbar g g on GB300 (mixed vs FP64).
+
+One step = the whole hot path over one batch: seeded RAMBO phase space with
+gluon cuts on the device (rambo_sample) + helicity- and colour-summed |M|^2
+(me_sigmakin) for 2^20 events at sqrt(s) = 1.5 TeV.  The momenta batch
+(201 MB) is larger than L2, so no flush is needed between steps.
+
+  python bench.py [--gpus N --steps K --warmup W]           # this library
+  python bench.py --impl reference [...]                    # FP64 CPU oracle
+
+Multi-GPU (torchrun, one rank per GPU): every rank evaluates its own event
+range (weak scaling, no data-path collective); the timed region is bracketed by
+barriers and the maximum over ranks is reported.  Prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "|M|^2 events/s gg->t tbar gg (mixed vs FP64, 1 GB300); serving p50/p99 latency"
+FP32_LANES_PER_SM = 128     # FP32 FMA lanes per SM (4 SMSPs x 32)
+N_SM = 152
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=("ours", "reference"))
+    ap.add_argument("--workload", default="gg_ttxgg")
+    ap.add_argument("--fp64-steps", type=int, default=2)
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------ helpers
+class ClockSampler:
+    """nvidia-smi sampled every 200 ms during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.proc = None
+        self.file = None
+
+    def __enter__(self):
+        try:
+            self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=self.file, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if self.proc is None or self.file is None:
+            return None
+        self.file.flush()
+        rows = []
+        with open(self.file.name) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.file.name)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        reasons = sorted({n for r in rows for n, v in zip(names, r[5:9]) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def dist_setup(want_cuda=True):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+
+        backend = "nccl" if (want_cuda and torch.cuda.is_available()) else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend=backend)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+def allreduce_max(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([x], dtype=torch.float64, device="cuda" if dist.get_backend() == "nccl" else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def cpu_baseline(name, seconds, rank):
+    """The FP64 CPU oracle as it stands, on the host cores, on a bounded sample."""
+    import oracle
+    from paper_2507_21039_gb300.workloads import DR_MIN, MT, PT_MIN, WORKLOADS
+
+    w = WORKLOADS[name]
+    mom, _, _ = oracle.rambo(w.seed, w.sqrt_s, w.masses_final, 0, 256, w.cut_mask, PT_MIN, DR_MIN)
+    t = time.perf_counter()
+    oracle.me2(name, mom, mt=MT, alpha=w.alpha)
+    rate = 256 / (time.perf_counter() - t)
+    n = int(max(256, min(1 << 17, rate * seconds)))
+    mom, _, _ = oracle.rambo(w.seed, w.sqrt_s, w.masses_final, 0, n, w.cut_mask, PT_MIN, DR_MIN)
+    t = time.perf_counter()
+    oracle.me2(name, mom, mt=MT, alpha=w.alpha)
+    dt = time.perf_counter() - t
+    return {"value": n / dt, "unit": "events/s", "cores": oracle.max_threads(), "kind": "oracle",
+            "sample": f"first {n} events of the {name} workload (seed {w.seed}), FP64 Berends-Giele "
+                      f"colour-ordered recursion + brute-force colour matrix, all helicities, "
+                      f"OpenMP over events; {dt:.1f} s"}
+
+
+# ------------------------------------------------------------------ arms
+def run_reference(args):
+    world, rank, _ = dist_setup(want_cuda=False)
+    if rank != 0:
+        return
+    from paper_2507_21039_gb300.workloads import WORKLOADS
+
+    import oracle
+    from paper_2507_21039_gb300.workloads import DR_MIN, MT, PT_MIN
+
+    name = args.workload
+    w = WORKLOADS[name]
+    oracle.build()
+    # size each step so that warmup + steps end within a few minutes
+    mom, _, _ = oracle.rambo(w.seed, w.sqrt_s, w.masses_final, 0, 128, w.cut_mask, PT_MIN, DR_MIN)
+    t = time.perf_counter()
+    oracle.me2(name, mom, mt=MT, alpha=w.alpha)
+    rate = 128 / (time.perf_counter() - t)
+    per_step = max(64, int(rate * min(20.0, 150.0 / max(1, args.steps + args.warmup))))
+    times = []
+    for s in range(args.warmup + args.steps):
+        mom, _, _ = oracle.rambo(w.seed, w.sqrt_s, w.masses_final, s * per_step, per_step, w.cut_mask, PT_MIN, DR_MIN)
+        t = time.perf_counter()
+        oracle.me2(name, mom, mt=MT, alpha=w.alpha)
+        dt = time.perf_counter() - t
+        if s >= args.warmup:
+            times.append(dt)
+    total = sum(times)
+    value = per_step * len(times) / total
+    out = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "events/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / len(times),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": name, "events_per_step": per_step, "sqrt_s": w.sqrt_s, "seed": w.seed,
+                   "precision": "fp64", "note": "reference arm = FP64 CPU oracle (the paper ships no code)"},
+        "cpu_baseline": {"value": value, "unit": "events/s", "cores": oracle.max_threads(), "kind": "oracle",
+                         "sample": f"{per_step} events per step of the {name} workload"},
+        "e2e": {"value": value, "unit": "events/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out), flush=True)
+
+
+def run_ours(args):
+    import torch
+
+    world, rank, local = dist_setup(want_cuda=True)
+    import __graft_entry__
+
+    __graft_entry__.build()
+    import paper_2507_21039_gb300 as me
+    from paper_2507_21039_gb300.workloads import WORKLOADS
+
+    torch.cuda.set_device(local)
+    name = args.workload
+    w = WORKLOADS[name]
+    n = w.nevt
+    masses = [0.0, 0.0] + list(w.masses_final)
+    cuts = me.cuts_for(name)
+    ev0 = rank * n  # weak scaling: each rank owns its own event range
+    stream = torch.cuda.current_stream()
+    mom = torch.empty((n, w.npar, 4), dtype=torch.float64, device="cuda")
+    me2 = torch.empty(n, dtype=torch.float64, device="cuda")
+    h_mixed = me.workload_handle(name, "mixed")
+    h_fp64 = me.workload_handle(name, "fp64")
+    me.rambo_sample(w.seed, ev0, n, w.sqrt_s, masses, cuts, momenta_out=mom, check=True)
+    me.me_filter_helicities(h_mixed, mom)
+    me.me_filter_helicities(h_fp64, mom)
+    ngood = len(me.me_good_helicities(h_mixed))
+
+    def step(h, seed_ev0, ev_pair=None):
+        me.rambo_sample(w.seed, seed_ev0, n, w.sqrt_s, masses, cuts, momenta_out=mom, stream=stream)
+        if ev_pair:
+            ev_pair[0].record(stream)
+        me.me_sigmakin(h, mom, me2, stream=stream)
+        if ev_pair:
+            ev_pair[1].record(stream)
+
+    def timed(h, steps, warmup, clocks=False):
+        for s in range(warmup):
+            step(h, ev0)
+        torch.cuda.synchronize()
+        barrier(world)
+        torch.cuda.synchronize()
+        s0 = torch.cuda.Event(enable_timing=True)
+        s1 = torch.cuda.Event(enable_timing=True)
+        kern = []
+        sampler = ClockSampler(local) if clocks else None
+        if sampler:
+            sampler.__enter__()
+        pairs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        s0.record(stream)
+        for s in range(steps):
+            step(h, ev0, pairs[s])
+        s1.record(stream)
+        torch.cuda.synchronize()
+        kern = [a.elapsed_time(b) for a, b in pairs]
+        if sampler:
+            sampler.__exit__(None, None, None)
+        barrier(world)
+        elapsed = s0.elapsed_time(s1) / 1e3
+        return elapsed, kern, (sampler.summary() if sampler else None)
+
+    elapsed, kern_ms, clocks = timed(h_mixed, args.steps, args.warmup, clocks=(rank == 0))
+    elapsed_max = allreduce_max(elapsed, world)
+    value = n * world * args.steps / elapsed_max
+    me_ms = statistics.mean(kern_ms)
+
+    el64, kern64, _ = timed(h_fp64, args.fp64_steps, 1)
+    el64 = allreduce_max(el64, world)
+    value64 = n * world * args.fp64_steps / el64
+
+    # end to end through the C ABI with host buffers (pinned): H2D momenta,
+    # kernel, D2H |M|^2, every step inside the timed region
+    host_mom = torch.empty((n, w.npar, 4), dtype=torch.float64, pin_memory=True)
+    host_me2 = torch.empty(n, dtype=torch.float64, pin_memory=True)
+    host_mom.copy_(mom)
+    me.me_sigmakin(h_mixed, host_mom, host_me2)
+    barrier(world)
+    t = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        me.me_sigmakin(h_mixed, host_mom, host_me2)
+    e2e_dt = allreduce_max(time.perf_counter() - t, world)
+    e2e = {"value": n * world * args.e2e_steps / e2e_dt, "unit": "events/s",
+           "h2d_bytes_per_step": host_mom.numel() * 8, "d2h_bytes_per_step": host_me2.numel() * 8,
+           "path": "me_sigmakin with pinned host momenta and host |M|^2"}
+
+    chain_f, colour_f = me.me_flops_per_event(h_mixed)
+    flops = (chain_f + colour_f) * n
+    peaks, peak_src = measured_peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    fp32_peak = N_SM * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    achieved = flops / (me_ms / 1e3) / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+                "frac": achieved / fp32_peak, "traffic": None,
+                "kernel": "me_kernel_tab<gg_ttxgg, float>",
+                "peak_source": f"derived: {N_SM} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 flops x "
+                               f"{sm_max:.0f} MHz ({peak_src} sm_max_mhz)",
+                "flops_per_event": chain_f + colour_f, "me_kernel_ms": me_ms}
+    traffic_file = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(traffic_file):
+        with open(traffic_file) as f:
+            tr = json.load(f)
+        if tr.get("kernel") == roofline["kernel"] and tr.get("flops_per_event") == roofline["flops_per_event"]:
+            roofline["traffic"] = tr.get("bytes_per_launch")
+
+    out = {
+        "metric": METRIC, "value": value, "unit": "events/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * elapsed_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": name, "process": "g g -> t t~ g g", "global_batch": n * world,
+                   "events_per_gpu": n, "sqrt_s": w.sqrt_s, "seed": w.seed, "precision": "mixed",
+                   "cuts": "gluon pT > 20 GeV, pairwise dR > 0.4", "good_helicities": ngood,
+                   "l2": "inputs larger than L2 (momenta 201 MB per step)",
+                   "step": "rambo_sample (device) + me_sigmakin", "parallelism": f"replicas x{world}"},
+        "fp64": {"value": value64, "unit": "events/s", "ms_per_step": 1e3 * el64 / args.fp64_steps,
+                 "me_kernel_ms": statistics.mean(kern64)},
+        "mixed_over_fp64": value / value64,
+        "e2e": e2e,
+        "gpu_launches": 2 * args.steps,
+        "roofline": roofline,
+        "clocks": clocks,
+    }
+    if not args.no_serving and rank == 0:
+        try:
+            from paper_2507_21039_gb300 import serving
+
+            out["serving"] = serving.bench_point()
+        except (ImportError, AttributeError):
+            pass
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(name, args.cpu_seconds, rank)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    h_mixed.close()
+    h_fp64.close()
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)
