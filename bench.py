@@ -45,6 +45,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--case", nargs=3, metavar=("WORKLOAD", "PRECISION", "NEVT"),
+                    help="profiling case: sample NEVT events, then one warm and one measured me_sigmakin")
     return ap.parse_args()
 
 
@@ -273,20 +275,26 @@ def run_ours(args):
     el64 = allreduce_max(el64, world)
     value64 = n * world * args.fp64_steps / el64
 
-    # end to end through the C ABI with host buffers (pinned): H2D momenta,
-    # kernel, D2H |M|^2, every step inside the timed region
+    # end to end through the C ABI with host buffers (pinned), the same step:
+    # rambo_sample into host momenta (D2H), me_sigmakin from host momenta (H2D)
+    # into host |M|^2 (D2H); every copy inside the timed region
     host_mom = torch.empty((n, w.npar, 4), dtype=torch.float64, pin_memory=True)
     host_me2 = torch.empty(n, dtype=torch.float64, pin_memory=True)
-    host_mom.copy_(mom)
-    me.me_sigmakin(h_mixed, host_mom, host_me2)
+
+    def host_step():
+        me.rambo_sample(w.seed, ev0, n, w.sqrt_s, masses, cuts, momenta_out=host_mom)
+        me.me_sigmakin(h_mixed, host_mom, host_me2)
+
+    host_step()
     barrier(world)
     t = time.perf_counter()
     for _ in range(args.e2e_steps):
-        me.me_sigmakin(h_mixed, host_mom, host_me2)
+        host_step()
     e2e_dt = allreduce_max(time.perf_counter() - t, world)
     e2e = {"value": n * world * args.e2e_steps / e2e_dt, "unit": "events/s",
-           "h2d_bytes_per_step": host_mom.numel() * 8, "d2h_bytes_per_step": host_me2.numel() * 8,
-           "path": "me_sigmakin with pinned host momenta and host |M|^2"}
+           "h2d_bytes_per_step": host_mom.numel() * 8,
+           "d2h_bytes_per_step": host_mom.numel() * 8 + host_me2.numel() * 8,
+           "path": "rambo_sample into pinned host momenta, me_sigmakin from them into pinned host |M|^2"}
 
     chain_f, colour_f = me.me_flops_per_event(h_mixed)
     flops = (chain_f + colour_f) * n
@@ -300,12 +308,18 @@ def run_ours(args):
                 "peak_source": f"derived: {N_SM} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 flops x "
                                f"{sm_max:.0f} MHz ({peak_src} sm_max_mhz)",
                 "flops_per_event": chain_f + colour_f, "me_kernel_ms": me_ms}
-    traffic_file = os.path.join(ROOT, "profiles", "traffic.json")
+    # DRAM bytes of one launch from the committed ncu summary, if it was taken on
+    # this kernel version (same generator flop count); null otherwise
+    traffic_file = os.path.join(ROOT, "profiles", "me_kernel_tab_gg_ttxgg_f32.traffic.txt")
     if os.path.exists(traffic_file):
+        kv = {}
         with open(traffic_file) as f:
-            tr = json.load(f)
-        if tr.get("kernel") == roofline["kernel"] and tr.get("flops_per_event") == roofline["flops_per_event"]:
-            roofline["traffic"] = tr.get("bytes_per_launch")
+            for line in f:
+                if "=" in line and not line.startswith("#"):
+                    k, v = line.strip().split("=", 1)
+                    kv[k] = v
+        if kv.get("kernel") == roofline["kernel"] and float(kv.get("flops_per_event", -1)) == roofline["flops_per_event"]:
+            roofline["traffic"] = float(kv["bytes_per_event"]) * n
 
     out = {
         "metric": METRIC, "value": value, "unit": "events/s", "n_gpus": world, "steps": args.steps,
@@ -343,9 +357,34 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_case(name, prec, nevt):
+    """Small fixed case for ncu captures: sampler, filter, two |M|^2 launches."""
+    import torch
+
+    import __graft_entry__
+
+    __graft_entry__.build()
+    import paper_2507_21039_gb300 as me
+    from paper_2507_21039_gb300.workloads import WORKLOADS
+
+    w = WORKLOADS[name]
+    masses = [0.0, 0.0] + list(w.masses_final)
+    mom = me.rambo_sample(w.seed, 0, nevt, w.sqrt_s, masses, me.cuts_for(name), check=True)
+    h = me.workload_handle(name, prec)
+    me.me_filter_helicities(h, mom[:4096])
+    out = me.me_sigmakin(h, mom)
+    torch.cuda.synchronize()
+    out = me.me_sigmakin(h, mom)
+    torch.cuda.synchronize()
+    print(json.dumps({"case": name, "precision": prec, "nevt": nevt, "checksum": float(out.sum())}))
+    h.close()
+
+
 if __name__ == "__main__":
     a = parse()
-    if a.impl == "reference":
+    if a.case:
+        run_case(a.case[0], a.case[1], int(a.case[2]))
+    elif a.impl == "reference":
         run_reference(a)
     else:
         run_ours(a)
