@@ -33,7 +33,8 @@
  *   - every call returns 0 on success or a negative ME_E* code; nothing
  *     throws across the ABI.  nevt == 0 is a no-op returning 0.
  *   - handles are independent; one handle must not be used from two host
- *     threads at the same time.  There is no global mutable state.
+ *     threads at the same time.  The only global mutable state is the fixed
+ *     scratch array of me_filter_helicities_noalloc.
  */
 #ifndef LIBME_ME_H
 #define LIBME_ME_H
@@ -53,6 +54,7 @@ extern "C" {
 #define ME_ENONFINITE (-5)    /* non-finite momenta found (ME_OPT_CHECK_FINITE) */
 #define ME_ETIMEOUT (-6)      /* a bounded wait expired (serving layer) */
 #define ME_ESAMPLER (-7)      /* RAMBO: an event needed more than 1000 attempts or Newton failed */
+#define ME_ETOOLARGE (-8)     /* me_filter_helicities_noalloc: the probe batch does not fit its fixed scratch */
 
 /* precision modes (Sec. 4.1, Table 1: FP64, FP32, mixed) */
 #define ME_PREC_FP64 0   /* chain, colour sum and helicity sum in FP64 */
@@ -88,6 +90,27 @@ int me_init(me_handle** h, const char* process, const double* masses, int nmass,
  * Errors: ME_EINVAL (null handle/momenta, nevt <= 0), ME_ENOMEM, ME_ECUDA.
  */
 int me_filter_helicities(me_handle* h, const double* momenta, int64_t nevt, int* ngood_out);
+
+/*
+ * me_filter_helicities_noalloc -- the same filter as me_filter_helicities,
+ * for host programs that cannot let a library allocate device memory (they
+ * reserve the device's memory up front through their own pool, or run loops in
+ * which cudaMalloc / cudaFree, which may synchronise the whole device, are not
+ * acceptable).  The paper has no counterpart: this is a deployment variant.
+ * It allocates nothing: its scratch is one fixed 4 MiB array inside the
+ * library, present on every device that loads the library until the process
+ * exits.  The probe events are all nevt events of `momenta`, which must be
+ * device memory; scratch needed = 8 * nevt * (nhel + 1) bytes plus a little,
+ * so nevt <= 8000 for 64 helicities and <= 4000 for 128; larger batches are
+ * rejected with ME_ETOOLARGE (pass fewer probe events).  The first call on each
+ * device looks up that device's copy of the array (cudaGetSymbolAddress) with
+ * the device current; make that first call before any stream capture.  All
+ * calls share the one array and overwrite it: calls that overlap on the same
+ * device (from several host threads) race and must be serialised by the
+ * caller.  Synchronous.  Errors: ME_EINVAL (null handle or momenta, host
+ * momenta, nevt <= 0), ME_ETOOLARGE, ME_ECUDA.
+ */
+int me_filter_helicities_noalloc(me_handle* h, const double* momenta, int64_t nevt, int* ngood_out);
 
 /*
  * me_sigmakin -- |M|^2 for nevt events: momenta [nevt][npar][4] -> me2[nevt]

@@ -25,6 +25,7 @@ ME_ENOTFILTERED = -4
 ME_ENONFINITE = -5
 ME_ETIMEOUT = -6
 ME_ESAMPLER = -7
+ME_ETOOLARGE = -8
 
 ME_PREC_FP64 = 0
 ME_PREC_FP32 = 1
@@ -36,7 +37,7 @@ ME_OPT_CHECK_FINITE = 2
 ME_OPT_GAUGE_CHECK = 3
 
 #: symbols declared in include/me.h
-EXPORTS = ("me_init", "me_filter_helicities", "me_sigmakin", "me_sigmakin_hel", "me_info",
+EXPORTS = ("me_init", "me_filter_helicities", "me_filter_helicities_noalloc", "me_sigmakin", "me_sigmakin_hel", "me_info",
            "me_good_helicities", "me_flops_per_event", "me_set_option", "me_free", "rambo_sample",
            "me_strerror", "me_version")
 
@@ -67,6 +68,7 @@ def load():
         P, i, i64, u64, d = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_uint64, ctypes.c_double
         lib.me_init.argtypes = [ctypes.POINTER(P), ctypes.c_char_p, P, i, P, i, i]
         lib.me_filter_helicities.argtypes = [P, P, i64, ctypes.POINTER(i)]
+        lib.me_filter_helicities_noalloc.argtypes = [P, P, i64, ctypes.POINTER(i)]
         lib.me_sigmakin.argtypes = [P, P, i64, P, P]
         lib.me_sigmakin_hel.argtypes = [P, P, i64, P, P, P]
         lib.me_info.argtypes = [P, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i), P]
@@ -80,7 +82,7 @@ def load():
         lib.me_strerror.argtypes = [i]
         lib.me_strerror.restype = ctypes.c_char_p
         lib.me_version.restype = ctypes.c_char_p
-        for name in ("me_init", "me_filter_helicities", "me_sigmakin", "me_sigmakin_hel", "me_info",
+        for name in ("me_init", "me_filter_helicities", "me_filter_helicities_noalloc", "me_sigmakin", "me_sigmakin_hel", "me_info",
                      "me_good_helicities", "me_flops_per_event", "me_set_option", "rambo_sample"):
             getattr(lib, name).restype = i
         _lib = lib
@@ -168,6 +170,15 @@ def me_filter_helicities(h: Handle, momenta) -> int:
     n = ctypes.c_int()
     _check(load().me_filter_helicities(h.ptr, _ptr(momenta), momenta.shape[0], ctypes.byref(n)),
            "me_filter_helicities")
+    return n.value
+
+
+def me_filter_helicities_noalloc(h: Handle, momenta) -> int:
+    """Helicity filter that allocates no device memory (device momenta only;
+    see include/me.h for the size limit and the shared-scratch caveats)."""
+    n = ctypes.c_int()
+    _check(load().me_filter_helicities_noalloc(h.ptr, _ptr(momenta), momenta.shape[0], ctypes.byref(n)),
+           "me_filter_helicities_noalloc")
     return n.value
 
 

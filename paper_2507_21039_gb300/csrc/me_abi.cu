@@ -5,6 +5,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <new>
 
 #include "me.h"
@@ -190,6 +191,7 @@ const char* me_strerror(int status)
     case ME_ENONFINITE: return "non-finite momenta";
     case ME_ETIMEOUT: return "timeout";
     case ME_ESAMPLER: return "phase-space sampler failed";
+    case ME_ETOOLARGE: return "batch exceeds the library's static scratch";
     default: return "unknown status";
     }
 }
@@ -378,3 +380,100 @@ int me_sigmakin_hel(me_handle* h, const double* momenta, int64_t nevt, double* m
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Helicity filter that allocates nothing.
+//
+// Some host programs cannot let a library allocate device memory: they reserve
+// the device's memory up front through their own pool (and would see a library
+// cudaMalloc fail or fragment that pool), or they run latency-critical loops in
+// which cudaMalloc / cudaFree, which may synchronise the whole device, are not
+// acceptable.  For them, me_filter_helicities_noalloc runs the same FP64
+// per-helicity evaluation and reduction as me_filter_helicities, but keeps its
+// scratch (per-event x per-helicity values, per-event totals, per-helicity
+// ratios, the list of all helicities) in one fixed array compiled into this
+// library instead of allocating it.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr size_t kStaticScratchBytes = size_t(4) << 20;  // 4 MiB on every device that loads the library
+constexpr int kMaxDevices = 64;
+
+__device__ __align__(256) unsigned char g_filter_scratch[kStaticScratchBytes];
+
+std::mutex g_scratch_mutex;
+void* g_scratch_addr[kMaxDevices] = {};
+
+// Device address of g_filter_scratch on the current device.  In host code the
+// array's name is only a host-side stand-in; the runtime maps it to the
+// current device's copy here, once per device, and the address is cached.
+int scratch_address(void** out)
+{
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+        cudaGetLastError();
+        return ME_ECUDA;
+    }
+    std::lock_guard<std::mutex> lock(g_scratch_mutex);
+    if (!g_scratch_addr[dev]) {
+        void* p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_filter_scratch) != cudaSuccess || !p) {
+            cudaGetLastError();
+            return ME_ECUDA;
+        }
+        g_scratch_addr[dev] = p;
+    }
+    *out = g_scratch_addr[dev];
+    return ME_OK;
+}
+
+size_t align256(size_t x) { return (x + 255) / 256 * 256; }
+
+}  // namespace
+
+extern "C" int me_filter_helicities_noalloc(me_handle* h, const double* momenta, int64_t nevt, int* ngood_out)
+{
+    if (!h || !momenta || nevt <= 0) return ME_EINVAL;
+    if (!is_device_ptr(momenta)) return ME_EINVAL;  // staging host momenta would need an allocation
+    const int nhel = h->nhel;
+    const size_t b_hel = align256(sizeof(double) * (size_t)nevt * nhel);
+    const size_t b_me2 = align256(sizeof(double) * (size_t)nevt);
+    const size_t b_ratio = align256(sizeof(double) * nhel);
+    const size_t b_list = align256(sizeof(short) * nhel);
+    if ((size_t)nevt > kStaticScratchBytes || b_hel + b_me2 + b_ratio + b_list > kStaticScratchBytes)
+        return ME_ETOOLARGE;
+    void* base = nullptr;
+    int rc = scratch_address(&base);
+    if (rc != ME_OK) return rc;
+    unsigned char* sp = static_cast<unsigned char*>(base);
+    double* d_hel_out = reinterpret_cast<double*>(sp);
+    double* d_me2 = reinterpret_cast<double*>(sp + b_hel);
+    double* d_ratio = reinterpret_cast<double*>(sp + b_hel + b_me2);
+    short* d_all = reinterpret_cast<short*>(sp + b_hel + b_me2 + b_ratio);
+    // every scratch word read below is written first in this call: the
+    // per-helicity values and totals by the |M|^2 kernel, the ratios by the
+    // reduction, the helicity list by the copy; nothing needs clearing
+    short all[128];
+    for (int i = 0; i < nhel; ++i) all[i] = (short)i;
+    if (cudaDeviceSynchronize() != cudaSuccess) return ME_ECUDA;
+    if (cudaMemcpy(d_all, all, sizeof(short) * nhel, cudaMemcpyHostToDevice) != cudaSuccess) return ME_ECUDA;
+    rc = launch_me(h, me::PREC_FP64, momenta, nevt, d_me2, d_hel_out, d_all, nhel, 0);
+    if (rc != ME_OK) return rc;
+    filter_reduce<<<nhel, 256>>>(d_hel_out, d_me2, (int)nevt, nhel, d_ratio);
+    if (cudaGetLastError() != cudaSuccess) return ME_ECUDA;
+    double ratio[128];
+    if (cudaMemcpy(ratio, d_ratio, sizeof(double) * nhel, cudaMemcpyDeviceToHost) != cudaSuccess) return ME_ECUDA;
+    short good[128];
+    int n = 0;
+    for (int i = 0; i < nhel; ++i)
+        if (ratio[i] > kFilterThreshold) good[n++] = (short)i;
+    if (n == 0) {
+        for (int i = 0; i < nhel; ++i) good[i] = (short)i;
+        n = nhel;
+    }
+    rc = set_good(h, good, n);
+    if (rc != ME_OK) return rc;
+    h->filtered = 1;
+    if (ngood_out) *ngood_out = h->ngood;
+    return ME_OK;
+}
