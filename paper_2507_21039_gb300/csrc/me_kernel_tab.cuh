@@ -15,6 +15,7 @@
 // The per-thread live state is J plus the operands of the amplitudes in
 // flight, so the chain never spills.
 #pragma once
+#include "me_colour_tc.cuh"
 #include "me_kernel.cuh"
 
 // Ordering point between amplitudes (a warp barrier, which ptxas does not move
@@ -93,7 +94,9 @@ template <class P, class T> __host__ __device__ constexpr size_t tab_smem_bytes(
     return tab_table_offset<P, T>() + (size_t)P::TAB * sizeof(Wf<T>);
 }
 
-template <class P, class T>
+// TC: colour sum on the tensor cores (T = float, NCOL >= 24, one helicity per
+// thread: nlist <= NT); otherwise the scalar quadratic form in precision T.
+template <class P, class T, bool TC>
 __global__ void __launch_bounds__(P::NT, sizeof(T) == 8 ? P::MIN_CTAS_D : P::MIN_CTAS_F) me_kernel_tab(LaunchArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -124,17 +127,31 @@ __global__ void __launch_bounds__(P::NT, sizeof(T) == 8 ? P::MIN_CTAS_D : P::MIN
         // (a3) off-shell objects for every helicity configuration of their support
         P::template tables<T>(tab, sln, (T)a.mt, tid);
         __syncthreads();
-        // (a4-a6) amplitudes per good helicity, colour sum, FP64 accumulation
+        // (a4-a6) amplitudes per good helicity, colour sum, FP64 accumulation.
+        // Every lane runs every pass (lanes past the end of the list evaluate a
+        // real helicity and discard it), so the warp barriers inside the
+        // amplitude code are always reached by all 32 lanes.
         double acc = 0.0;
-        for (int i = tid; i < a.nlist; i += NT) {
-            const int h = a.hel_list[i];
+        for (int base = 0; base < a.nlist; base += NT) {
+            const int i = base + tid;
+            const bool act = i < a.nlist;
+            const int h = a.hel_list[act ? i : 0];
             cx<T> J[P::NCOL];
 #pragma unroll
             for (int c = 0; c < P::NCOL; ++c) J[c] = {T(0), T(0)};
             P::template amps<T>(tab, h, sln, J);
-            const T v = P::template colour<T>(J);
-            acc += (double)v;
-            if (a.hel_out) a.hel_out[e * a.nlist + i] = (double)v * a.norm;
+            T v;
+            if constexpr (TC) {
+                __syncthreads();  // single pass (nlist <= NT): the tables are dead, reuse them as staging
+                unsigned char* stage = smem + tab_table_offset<P, T>() + (tid >> 5) * TcShape<P::NCOL>::WARP_BYTES;
+                v = colour_tc_warp<P::NCOL, P::NSPLIT>(J, stage, P::bfrag(), tid & 31);
+            } else {
+                v = P::template colour<T>(J);
+            }
+            if (act) {
+                acc += (double)v;
+                if (a.hel_out) a.hel_out[e * a.nlist + i] = (double)v * a.norm;
+            }
         }
         for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
         if constexpr (NT > 32) {
@@ -152,15 +169,32 @@ __global__ void __launch_bounds__(P::NT, sizeof(T) == 8 ? P::MIN_CTAS_D : P::MIN
     }
 }
 
-template <class P, class T> cudaError_t launch_tab(const LaunchArgs& a)
+template <class P, class T, bool TC = false> cudaError_t launch_tab(const LaunchArgs& a)
 {
     constexpr size_t smem = tab_smem_bytes<P, T>();
+    if constexpr (TC)
+        static_assert((P::NT / 32) * TcShape<P::NCOL>::WARP_BYTES <= P::TAB * sizeof(Wf<T>),
+                      "tensor-core staging must fit in the table region");
     static size_t granted = 0;
-    cudaError_t e = ensure_smem(me_kernel_tab<P, T>, smem, granted);
+    cudaError_t e = ensure_smem(me_kernel_tab<P, T, TC>, smem, granted);
     if (e != cudaSuccess) return e;
     const long long grid = a.nevt < 0x7fffffffLL ? a.nevt : 0x7fffffffLL;
-    me_kernel_tab<P, T><<<(unsigned)grid, P::NT, smem, a.stream>>>(a);
+    me_kernel_tab<P, T, TC><<<(unsigned)grid, P::NT, smem, a.stream>>>(a);
     return cudaGetLastError();
+}
+
+// Mixed precision: FP32 chain; colour sum on BF16 tensor cores for 24 or more
+// colour flows when every thread holds one helicity, FP32 scalar otherwise.
+template <class P> cudaError_t launch_mixed(const LaunchArgs& a)
+{
+    if constexpr (P::IS_TAB) {
+        if constexpr (P::NCOL >= 24) {
+            if (a.nlist <= P::NT) return launch_tab<P, float, true>(a);
+        }
+        return launch_tab<P, float, false>(a);
+    } else {
+        return launch_scalar<P, float>(a);
+    }
 }
 
 }  // namespace me

@@ -9,6 +9,7 @@ the three precision modes, and a process descriptor for the C ABI.
 from __future__ import annotations
 
 import math
+import struct
 
 from .colour import colour_matrix
 from .plan import Plan, build_plan
@@ -56,6 +57,50 @@ def _line_tables(P: Plan):
         plus.append(pm)
         minus.append(mm)
     return plus, minus, kind
+
+
+def _bf16_bits(x: float) -> int:
+    """float -> bfloat16 bits, round to nearest even"""
+    f = struct.unpack("<I", struct.pack("<f", float(x)))[0]
+    return ((f + 0x7FFF + ((f >> 16) & 1)) >> 16) & 0xFFFF
+
+
+def _bf16_value(bits: int) -> float:
+    return struct.unpack("<f", struct.pack("<I", bits << 16))[0]
+
+
+def tc_fragments(num):
+    """mma.sync m16n8k16 B-operand fragments of the colour numerators: for each
+    k-step, n-tile and lane, (b0, b1) packing B[k][n], B[k+1][n] (low, high) at
+    k = 16 ks + 2t (+8), n = 8 nt + g (g = lane/4, t = lane%4).  Numerators with
+    more than 8 significant bits are split hi + lo, both exact in BF16."""
+    n = len(num)
+    kp, np_ = (n + 15) // 16 * 16, (n + 7) // 8 * 8
+    hi = [[0] * np_ for _ in range(kp)]
+    lo = [[0] * np_ for _ in range(kp)]
+    split = False
+    for k in range(n):
+        for j in range(n):
+            v = num[k][j]
+            hb = _bf16_bits(v)
+            rest = v - _bf16_value(hb)
+            lb = _bf16_bits(rest)
+            assert _bf16_value(hb) + _bf16_value(lb) == v, v
+            hi[k][j], lo[k][j] = hb, lb
+            split |= rest != 0
+    def frags(B):
+        out = []
+        for ks in range(kp // 16):
+            for nt in range(np_ // 8):
+                for lane in range(32):
+                    g, t = lane >> 2, lane & 3
+                    k0, col = 16 * ks + 2 * t, 8 * nt + g
+                    b0 = B[k0][col] | (B[k0 + 1][col] << 16)
+                    b1 = B[k0 + 8][col] | (B[k0 + 9][col] << 16)
+                    out.append((b0, b1))
+        return out
+    f = frags(hi) + (frags(lo) if split else [])
+    return f, split
 
 
 def _coef_call(col, c, var):
@@ -135,6 +180,14 @@ def emit_process(process: str) -> tuple[str, dict]:
         flops_hel = TP.amplitude_flops_per_helicity() + -(-TP.table_flops() // nhel_all)
     else:
         flops_hel = P.flops_per_helicity()
+    tc_members, tc_array = "", ""
+    if ncol >= 24:
+        fr, nsplit = tc_fragments(num)
+        tc_array = (f"__device__ const uint2 c_bfrag[{len(fr)}] = {{\n    "
+                    + ",\n    ".join(", ".join("{%du, %du}" % x for x in fr[i:i + 8]) for i in range(0, len(fr), 8))
+                    + "\n};\n")
+        tc_members = (f"\n    static constexpr bool NSPLIT = {'true' if nsplit else 'false'};"
+                      f"\n    __device__ static __forceinline__ const uint2* bfrag() {{ return c_bfrag; }}")
     ns = f"p_{process}"
     cnum_flat = ", ".join(str(x) for row in num for x in row)
     src = f"""// Generated by paper_2507_21039_gb300/gen/emit.py for {process}: do not edit.
@@ -153,12 +206,12 @@ __constant__ unsigned short c_line_plus[{nlines}] = {{{", ".join(str(x) for x in
 __constant__ unsigned short c_line_minus[{nlines}] = {{{", ".join(str(x) for x in minus)}}};
 __constant__ unsigned char c_line_kind[{nlines}] = {{{", ".join(str(x) for x in lkind)}}};
 static const int h_cnum[{ncol * ncol}] = {{{cnum_flat}}};
-
+{tc_array}
 struct Proc {{
     static constexpr int NPAR = {npar}, NCOL = {ncol}, NLINES = {nlines}, THREADS = {threads};
     static constexpr int CDEN = {den};
     static constexpr bool J_SMEM = {"true" if j_smem else "false"};
-    static constexpr bool IS_TAB = false;
+    static constexpr bool IS_TAB = false;{tc_members}
     __device__ static __forceinline__ unsigned ext_kind(int e) {{ return c_ext_kind[e]; }}
     __device__ static __forceinline__ unsigned ext_massive(int e) {{ return c_ext_massive[e]; }}
     __device__ static __forceinline__ unsigned line_plus(int l) {{ return c_line_plus[l]; }}

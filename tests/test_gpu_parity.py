@@ -230,3 +230,33 @@ def test_full_size_sampled_parity(orc, name, prec):
     else:
         assert np.median(rel) <= LOW_MEDIAN and rel.max() <= LOW_MAX
     assert np.all(np.isfinite(out)) and np.all(out > 0)
+
+
+def test_mixed_uses_tensor_core_colour_sum(orc):
+    """gg -> t t~ g g mixed: the colour sum runs on BF16 tensor cores (hi/lo
+    split, FP32 accumulation).  Its results differ bitwise from the FP32 scalar
+    colour sum but both agree with the FP64 oracle within the FP32 tolerances;
+    per-helicity contributions add up to the event total."""
+    name = "gg_ttxgg"
+    w = WORKLOADS[name]
+    mom = oracle_events(orc, name, 300)
+    ref = orc.me2(name, mom, mt=MT, alpha=w.alpha)
+    d = torch.from_numpy(mom).cuda()
+    out = {}
+    for prec in ("fp32", "mixed"):
+        h = me.workload_handle(name, prec)
+        me.me_filter_helicities(h, d)
+        ngood = len(me.me_good_helicities(h))
+        me2 = torch.empty(len(mom), dtype=torch.float64, device="cuda")
+        hel = torch.empty((len(mom), ngood), dtype=torch.float64, device="cuda")
+        me.me_sigmakin_hel(h, d, me2, hel)
+        plain = me.me_sigmakin(h, d)
+        torch.cuda.synchronize()
+        assert torch.equal(plain, me2)
+        assert np.allclose(hel.sum(1).cpu().numpy(), me2.cpu().numpy(), rtol=1e-12, atol=0)
+        out[prec] = me2.cpu().numpy()
+        h.close()
+    assert not np.array_equal(out["fp32"], out["mixed"])
+    for prec in ("fp32", "mixed"):
+        rel = np.abs(out[prec] / ref - 1)
+        assert np.median(rel) <= LOW_MEDIAN and rel.max() <= LOW_MAX, (prec, np.median(rel), rel.max())
