@@ -29,7 +29,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
               "-Xptxas", "-v", "-I", INCLUDE, "-I", CSRC]
 
-STATIC_SOURCES = ["me_abi.cu", "rambo.cu"]
+STATIC_SOURCES = ["me_abi.cu", "rambo.cu", "serve.cu"]
 # processes compiled into the library
 PROCESSES = ("ee_mumu", "gg_ttx", "gg_ttxg", "gg_ttxgg")
 

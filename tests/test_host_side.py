@@ -74,8 +74,8 @@ def test_generator_flop_counts_positive():
 
 
 # ---------------------------------------------------------------- C ABI
-def _declared_symbols():
-    src = open(os.path.join(ROOT, "include", "me.h")).read()
+def _declared_symbols(header="me.h"):
+    src = open(os.path.join(ROOT, "include", header)).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
     names = re.findall(r"^\s*(?:const\s+)?[\w\s\*]+?\b(\w+)\s*\(", src, flags=re.M)
     return sorted(set(n for n in names if n not in ("if", "while", "switch")))
@@ -94,9 +94,15 @@ def lib():
 def test_library_exports_every_declared_symbol(lib):
     import paper_2507_21039_gb300 as me
 
-    declared = _declared_symbols()
+    from paper_2507_21039_gb300 import serving
+
+    headers = sorted(f for f in os.listdir(os.path.join(ROOT, "include")) if f.endswith(".h"))
+    assert headers == ["me.h", "me_serve.h"]
+    declared = _declared_symbols("me.h")
     assert set(declared) == set(me.EXPORTS), declared
-    for name in declared:
+    declared_srv = _declared_symbols("me_serve.h")
+    assert set(declared_srv) == set(serving.SERVE_EXPORTS), declared_srv
+    for name in declared + declared_srv:
         assert hasattr(lib, name), name
 
 
