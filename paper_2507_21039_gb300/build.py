@@ -31,7 +31,7 @@ NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-r
 
 STATIC_SOURCES = ["me_abi.cu", "rambo.cu", "serve.cu"]
 # processes compiled into the library
-PROCESSES = ("ee_mumu", "gg_ttx", "gg_ttxg", "gg_ttxgg")
+PROCESSES = ("ee_mumu", "gg_ttx", "gg_ttxg", "gg_ttxgg", "gg_ttxggg")
 
 
 def nvcc() -> str:

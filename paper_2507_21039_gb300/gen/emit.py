@@ -13,11 +13,14 @@ import struct
 
 from .colour import colour_matrix
 from .plan import Plan, build_plan
+from .interp import AMP_KINDS, ROUTINES, build_interp
 from .tabplan import build_tabplan
 
 EXT_KINDS = {"VIN": 0, "VOUT": 1, "FO_U": 2, "FO_V": 3, "FI_U": 4, "FI_V": 5}
 # processes evaluated with the helicity-recycled table kernel (me_kernel_tab.cuh)
 TAB_PROCESSES = {"gg_ttxg": 32, "gg_ttxgg": 64}   # process -> threads per event
+# processes evaluated with the staged descriptor kernel (me_kernel_interp.cuh)
+INTERP_PROCESSES = {"gg_ttxggg": (128, 16)}        # process -> (threads per event, amplitudes per stage)
 
 
 def _ext_table(process: str):
@@ -170,14 +173,20 @@ def emit_process(process: str) -> tuple[str, dict]:
         cbody.append("  s = fma(a.re, zr, fma(a.im, zi, s));")
         cbody.append("}")
 
-    tab_src, TP = ("", None)
+    tab_src, TP, IP = ("", None, None)
     if process in TAB_PROCESSES:
         tab_src, TP = emit_tab_struct(process, TAB_PROCESSES[process], ncol, nlines, cbody)
-    kernel_struct = "ProcTab" if TP else "Proc"
-    launch_fn = "launch_tab" if TP else "launch_scalar"
+    elif process in INTERP_PROCESSES:
+        nt_i, sa = INTERP_PROCESSES[process]
+        tab_src, IP = emit_interp_struct(process, nt_i, sa, num)
+        body, cbody = [], []   # the straight-line chain is not used for this process
+    kernel_struct = "ProcTab" if TP else ("ProcInterp" if IP else "Proc")
+    launch_fn = "launch_tab" if TP else ("launch_interp" if IP else "launch_scalar")
+    nhel_all = 1 << npar
     if TP:
-        nhel_all = 1 << npar
         flops_hel = TP.amplitude_flops_per_helicity() + -(-TP.table_flops() // nhel_all)
+    elif IP:
+        flops_hel = IP.tab.amplitude_flops_per_helicity() + -(-IP.table_flops // nhel_all)
     else:
         flops_hel = P.flops_per_helicity()
     tc_members, tc_array = "", ""
@@ -196,6 +205,7 @@ def emit_process(process: str) -> tuple[str, dict]:
 #include "me_kernel.cuh"
 #include "me_colour_tc.cuh"
 #include "me_kernel_tab.cuh"
+#include "me_kernel_interp.cuh"
 
 namespace me {{
 namespace {ns} {{
@@ -211,7 +221,7 @@ struct Proc {{
     static constexpr int NPAR = {npar}, NCOL = {ncol}, NLINES = {nlines}, THREADS = {threads};
     static constexpr int CDEN = {den};
     static constexpr bool J_SMEM = {"true" if j_smem else "false"};
-    static constexpr bool IS_TAB = false;{tc_members}
+    static constexpr bool IS_TAB = false, IS_INTERP = false;{tc_members}
     __device__ static __forceinline__ unsigned ext_kind(int e) {{ return c_ext_kind[e]; }}
     __device__ static __forceinline__ unsigned ext_massive(int e) {{ return c_ext_massive[e]; }}
     __device__ static __forceinline__ unsigned line_plus(int l) {{ return c_line_plus[l]; }}
@@ -352,7 +362,7 @@ struct ProcTab : Proc {{
     // register budget: FP32 <= 128 per thread (occupancy bound by shared memory
     // anyway), FP64 <= 255 (its tables are twice as large)
     static constexpr int MIN_CTAS_F = {max(1, 65536 // (nt * 128))}, MIN_CTAS_D = {max(1, 65536 // (nt * 255))};
-    static constexpr bool IS_TAB = true;
+    static constexpr bool IS_TAB = true, IS_INTERP = false;
     static constexpr long long TABLE_FLOPS = {TP.table_flops()}LL, AMP_FLOPS = {TP.amplitude_flops_per_helicity()}LL;
 
     template <class T>
@@ -371,6 +381,84 @@ struct ProcTab : Proc {{
     }}
 }};
 """, TP
+
+
+def emit_interp_struct(process: str, nt: int, stage_amps: int, num):
+    """ProcInterp: staged table tasks, amplitude descriptors, colour terms."""
+    I = build_interp(process, stage_amps)
+    T = I.tab
+    P = T.plan
+    npar = P.npar
+    ops = P.ops
+    tasks, rounds, stages, amps, terms, stage_term = [], [], [], [], [], []
+    for st in I.stages:
+        r0 = len(rounds)
+        for ri, (kind, tl) in enumerate(st.rounds):
+            rounds.append((len(tasks), len(tl), ROUTINES.index(kind), 1 if ri in st.barriers else 0))
+            for out, ins, ln in tl:
+                ins = list(ins) + [0] * (3 - len(ins))
+                tasks.append((out, ins[0], ins[1], ins[2], ln[0], ln[1], ln[2]))
+        a0 = len(amps)
+        stage_term.append(len(terms))
+        sup_index = {S: i for i, S in enumerate(I.supports)}
+        for ai in st.amps:
+            aop, coefs = P.amps[ai]
+            op = ops[aop]
+            bases, sups = [], []
+            for x in op.args:
+                base = I.slot[x] if (ops[x].out != "A" and not ops[x].kind.startswith("ext_")) else 2 * ops[x].ext
+                bases.append(base)
+                sups.append(sup_index[T.support[x]])
+            while len(bases) < 4:
+                bases.append(0)
+                sups.append(0)
+            la, lb = (op.mom if op.kind == "VVV1_0" else (0, 0))
+            assert len(coefs) < 256 and all(c in ((0, 1), (0, -1)) for _, c in coefs)
+            amps.append((bases, sups, AMP_KINDS.index(op.kind), la, lb, len(coefs)))
+            for col, c in coefs:
+                terms.append(col | (0x8000 if c == (0, -1) else 0))
+        stages.append((r0, len(rounds), a0, len(amps)))
+    masks = []
+    for S in I.supports:
+        m = 0
+        for p in S:
+            m |= 1 << (npar - 1 - p)
+        masks.append(m)
+    n = len(num)
+    cnum2 = [num[i][j] * (1 if i == j else 2) if j >= i else 0 for i in range(n) for j in range(n)]
+
+    def arr(name, ctype, rows, fmt, per_line=6):
+        body = ",\n    ".join(", ".join(fmt(x) for x in rows[i:i + per_line]) for i in range(0, len(rows), per_line))
+        return f"__device__ const {ctype} {name}[{max(len(rows), 1)}] = {{\n    {body if rows else '0'}\n}};\n"
+
+    src = ""
+    src += arr("c_itasks", "TabTask", tasks, lambda t: "{%d, %d, %d, %d, %d, %d, %d, 0, 0}" % t, 4)
+    src += arr("c_rounds", "IRound", rounds, lambda r: "{%du, %d, %d, %d}" % r, 8)
+    src += arr("c_stages", "IStage", stages, lambda r: "{%d, %d, %d, %d}" % r, 8)
+    src += arr("c_amps", "IAmp", amps, lambda a: "{{%d, %d, %d, %d}, {%d, %d, %d, %d}, %d, %d, %d, %d}" % (
+        *a[0], *a[1], a[2], a[3], a[4], a[5]), 3)
+    src += arr("c_terms", "unsigned short", terms, lambda x: "%d" % x, 16)
+    src += arr("c_stage_term", "int", stage_term, lambda x: "%d" % x, 16)
+    src += arr("c_supmask", "unsigned short", masks, lambda x: "%d" % x, 16)
+    src += arr("c_cnum2", "short", cnum2, lambda x: "%d" % x, 24)
+    src += f"""
+// staged evaluation: {len(I.stages)} stages of <= {stage_amps} amplitudes, table peak {I.table_size} entries,
+// {len(tasks)} table tasks ({I.table_flops} flops per event), {len(terms)} colour terms
+struct ProcInterp : Proc {{
+    static constexpr int NT = {nt}, TAB = {I.table_size}, NSUP = {len(I.supports)}, NSTAGE = {len(I.stages)};
+    static constexpr bool IS_TAB = false, IS_INTERP = true;
+    static constexpr long long TABLE_FLOPS = {I.table_flops}LL, AMP_FLOPS = {T.amplitude_flops_per_helicity()}LL;
+    __device__ static __forceinline__ const TabTask* tasks() {{ return c_itasks; }}
+    __device__ static __forceinline__ IRound round(int r) {{ return c_rounds[r]; }}
+    __device__ static __forceinline__ IStage stage(int s) {{ return c_stages[s]; }}
+    __device__ static __forceinline__ IAmp amp(int a) {{ return c_amps[a]; }}
+    __device__ static __forceinline__ unsigned short term(int t) {{ return __ldg(c_terms + t); }}
+    __device__ static __forceinline__ int stage_term_begin(int s) {{ return c_stage_term[s]; }}
+    __device__ static __forceinline__ unsigned support_mask(int s) {{ return c_supmask[s]; }}
+    __device__ static __forceinline__ int cnum2(int i, int j) {{ return __ldg(c_cnum2 + i * NCOL + j); }}
+}};
+"""
+    return src, I
 
 
 PROCESSES = ("ee_mumu", "gg_ttx", "gg_ttxg", "gg_ttxgg", "gg_ttxggg")

@@ -1,0 +1,167 @@
+"""Staged, descriptor-driven evaluation for the largest process (gg -> t t~ ggg).
+
+The helicity-recycled tables of tabplan.py hold every off-shell object for
+every configuration of its support; for 7 external particles that is 12750
+wavefunctions per event, far beyond shared memory.  Here the amplitudes are
+ordered greedily (each next amplitude needs the fewest new table entries) and
+cut into stages.  A stage first computes the objects its amplitudes need that
+are not yet in the table (cooperatively, level by level), then every thread
+evaluates the stage's amplitudes for its own helicity.  A table object lives
+from the stage that computes it to the last stage that reads it; its slots are
+then reused (first-fit allocator), so the table only has to hold the peak live
+set.  The amplitude phase is a loop over compact descriptors (kind, operands,
+line momenta, colour terms) rather than straight-line code, which keeps the
+kernel small for 1890 amplitudes per helicity.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+from .plan import FLOPS
+from .tabplan import build_tabplan, compress
+
+ROUTINES = ("VVV1P0_1", "VVVV1P0_1", "VVVV3P0_1", "VVVV4P0_1", "FFV1_2", "FFV1_1", "FFV1P0_3")
+AMP_KINDS = ("FFV1_0", "VVV1_0", "VVVV1_0", "VVVV3_0", "VVVV4_0")
+
+
+@dataclass
+class Stage:
+    rounds: list = field(default_factory=list)     # (kind, [task tuples]) with a barrier between levels
+    barriers: list = field(default_factory=list)   # round indices after which a barrier is needed
+    amps: list = field(default_factory=list)       # amplitude indices (into plan.amps)
+
+
+@dataclass
+class InterpPlan:
+    tab: object
+    stages: list
+    slot: dict          # object op index -> table base (Wf units)
+    table_size: int
+    amp_order: list
+    supports: list      # distinct supports of amplitude operands
+    table_flops: int
+
+
+class _Arena:
+    """first-fit allocator over Wf slots (sizes are powers of two)"""
+
+    def __init__(self, base):
+        self.free = [(base, 1 << 30)]
+        self.peak = base
+
+    def alloc(self, n):
+        for i, (s, ln) in enumerate(self.free):
+            if ln >= n:
+                if ln == n:
+                    self.free.pop(i)
+                else:
+                    self.free[i] = (s + n, ln - n)
+                self.peak = max(self.peak, s + n)
+                return s
+        raise RuntimeError("arena exhausted")
+
+    def release(self, s, n):
+        self.free.append((s, n))
+        self.free.sort()
+        merged = []
+        for a, ln in self.free:
+            if merged and merged[-1][0] + merged[-1][1] == a:
+                merged[-1] = (merged[-1][0], merged[-1][1] + ln)
+            else:
+                merged.append((a, ln))
+        self.free = merged
+
+
+def build_interp(process: str, stage_amps: int = 48) -> InterpPlan:
+    T = build_tabplan(process)
+    P = T.plan
+    ops = P.ops
+    is_obj = lambda i: ops[i].out != "A" and not ops[i].kind.startswith("ext_")
+    size = {i: 1 << len(T.support[i]) for i in range(len(ops)) if is_obj(i)}
+
+    def closure(i, acc):
+        if i in acc or not is_obj(i):
+            return
+        for a in ops[i].args:
+            closure(a, acc)
+        acc.add(i)
+
+    amp_deps = []
+    for ai, _ in P.amps:
+        s = set()
+        for a in ops[ai].args:
+            closure(a, s)
+        amp_deps.append(s)
+
+    # greedy order: next amplitude = fewest new table entries (ties: plan order)
+    live, order, remaining = set(), [], set(range(len(P.amps)))
+    while remaining:
+        best = min(remaining, key=lambda i: (sum(size[o] for o in amp_deps[i] - live), i))
+        order.append(best)
+        remaining.remove(best)
+        live |= amp_deps[best]
+
+    # stages and lifetimes
+    stage_of_amp = {}
+    stages = []
+    for k in range(0, len(order), stage_amps):
+        stages.append(Stage(amps=order[k:k + stage_amps]))
+        for a in order[k:k + stage_amps]:
+            stage_of_amp[a] = len(stages) - 1
+    first, last = {}, {}
+    computed = set()
+    for si, st in enumerate(stages):
+        need = set()
+        for a in st.amps:
+            need |= amp_deps[a]
+        new = need - computed
+        for o in new:
+            first[o] = si
+        computed |= new
+        for o in need:
+            last[o] = max(last.get(o, -1), si)
+        st.new = new
+    # objects read only while computing others in a later stage stay live until then
+    for si, st in enumerate(stages):
+        for o in st.new:
+            for a in ops[o].args:
+                if is_obj(a):
+                    last[a] = max(last[a], si)
+
+    arena = _Arena(2 * P.npar)
+    slot = {}
+    for si, st in enumerate(stages):
+        # allocate this stage's new objects (in dependency order), release dead ones after
+        for o in sorted(st.new):
+            slot[o] = arena.alloc(size[o])
+        level = {}
+        for o in sorted(st.new):  # op indices are topologically ordered
+            level[o] = 1 + max([level.get(a, 0) for a in ops[o].args if a in st.new] or [0])
+        bykey = {}
+        for o in sorted(st.new):
+            bykey.setdefault((level[o], ops[o].kind), []).append(o)
+        prev = None
+        for (lv, kind) in sorted(bykey):
+            if prev is not None and lv != prev:
+                st.barriers.append(len(st.rounds) - 1)
+            prev = lv
+            tasks = []
+            for o in bykey[(lv, kind)]:
+                S = T.support[o]
+                op = ops[o]
+                for v in range(size[o]):
+                    bits = {p: (v >> j) & 1 for j, p in enumerate(S)}
+                    ins = []
+                    for a in op.args:
+                        base = slot[a] if is_obj(a) else 2 * ops[a].ext
+                        ins.append(base + compress(bits, T.support[a]))
+                    ln = (op.mom[0], op.mom[1], op.line) if kind == "VVV1P0_1" else (0, 0, op.line)
+                    tasks.append((slot[o] + v, tuple(ins), ln))
+            st.rounds.append((kind, tasks))
+        for o in list(slot):
+            if o in last and last[o] == si:
+                arena.release(slot[o], size[o])
+                last[o] = -99  # released
+    supports = sorted({T.support[a] for ai, _ in P.amps for a in ops[ai].args}, key=lambda s: (len(s), s))
+    tflops = sum(FLOPS[k] * len(t) for st in stages for k, t in st.rounds)
+    return InterpPlan(T, stages, slot, arena.peak, order, supports, tflops)

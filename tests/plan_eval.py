@@ -113,3 +113,80 @@ def _v4(name, A, B, C):
     if name == "VVVV3":
         return dot(A, B) * C - dot(B, C) * A
     return dot(A, B) * C - dot(A, C) * B
+
+
+def evaluate_staged(orc, I, p, h, mt):
+    """Run a staged interpreter schedule (gen/interp.py) in numpy: a slot table
+    shared by all helicity variants, filled stage by stage, with slots reused
+    after their last reader -- the layout the CUDA kernel executes."""
+    T = I.tab
+    P = T.plan
+    npar = P.npar
+    lam = [1 if (h >> (npar - 1 - i)) & 1 else -1 for i in range(npar)]
+    incoming = [i < 2 for i in range(npar)]
+    out_p = np.array([(-p[i] if incoming[i] else p[i]) for i in range(npar)])
+    lines = []
+    for ln in P.lines:
+        if ln.kind == "g":
+            q = sum(out_p[P.gluon_ext[g]] for g in ln.gluons)
+            lines.append((q, 1.0 / dot(q, q) if len(ln.gluons) > 1 else 0.0))
+        else:
+            q = p[2] + sum((out_p[P.gluon_ext[g]] for g in ln.gluons), np.zeros(4))
+            lines.append((q, 1.0 / (dot(q, q) - mt * mt)))
+    table = {}
+    for e in range(npar):
+        for b, l in ((0, -1), (1, 1)):
+            if e in (0, 1):
+                table[2 * e + b] = orc.polvec(p[e], l)
+            elif e == 2:
+                table[2 * e + b] = orc.bar(orc.spinor_u(p[e], mt, l))
+            elif e == 3:
+                table[2 * e + b] = orc.spinor_v(p[e], mt, l)
+            else:
+                table[2 * e + b] = np.conj(orc.polvec(p[e], l))
+    bits = {q: (1 if lam[q] > 0 else 0) for q in range(npar)}
+
+    def var(S):
+        return sum(bits[q] << j for j, q in enumerate(S))
+
+    J = np.zeros(P.ncol, dtype=complex)
+    ops = P.ops
+    for st in I.stages:
+        for kind, tasks in st.rounds:
+            for out, ins, ln in tasks:
+                a = [table[i] for i in ins]
+                if kind == "VVV1P0_1":
+                    PA, PB = lines[ln[0]][0], lines[ln[1]][0]
+                    k1, k2, k3 = -PA, -PB, PA + PB
+                    v = dot(a[0], a[1]) * (k1 - k2) + a[1] * dot(k2 - k3, a[0]) + a[0] * dot(k3 - k1, a[1])
+                    table[out] = lines[ln[2]][1] * v
+                elif kind.startswith("VVVV"):
+                    table[out] = lines[ln[2]][1] * _v4(kind[:5], a[0], a[1], a[2])
+                elif kind == "FFV1_2":
+                    q, inv = lines[ln[2]]
+                    table[out] = inv * (a[0] @ slash(a[1]) @ (slash(q) + mt * np.eye(4)))
+                elif kind == "FFV1_1":
+                    q, inv = lines[ln[2]]
+                    table[out] = inv * ((slash(q) + mt * np.eye(4)) @ slash(a[0]) @ a[1])
+                else:
+                    inv = lines[ln[2]][1]
+                    table[out] = inv * np.array([a[0] @ G[mu] @ a[1] for mu in range(4)])
+        for ai in st.amps:
+            aop, terms = P.amps[ai]
+            op = ops[aop]
+            w = []
+            for x in op.args:
+                base = I.slot[x] if (ops[x].out != "A" and not ops[x].kind.startswith("ext_")) else 2 * ops[x].ext
+                w.append(table[base + var(T.support[x])])
+            if op.kind == "FFV1_0":
+                x = w[0] @ slash(w[1]) @ w[2]
+            elif op.kind == "VVV1_0":
+                PA, PB = lines[op.mom[0]][0], lines[op.mom[1]][0]
+                k1, k2, k3 = -PA, -PB, PA + PB
+                x = dot(w[0], w[1]) * dot(k1 - k2, w[2]) + dot(w[1], w[2]) * dot(k2 - k3, w[0]) + \
+                    dot(w[2], w[0]) * dot(k3 - k1, w[1])
+            else:
+                x = dot(_v4(op.kind[:5], w[0], w[1], w[2]), w[3])
+            for col, c in terms:
+                J[col] += complex(c[0], c[1]) * x
+    return J

@@ -15,7 +15,7 @@ pytestmark = pytest.mark.gpu
 import paper_2507_21039_gb300 as me  # noqa: E402
 from paper_2507_21039_gb300.workloads import DR_MIN, MT, PT_MIN, WORKLOADS  # noqa: E402
 
-BUILT = ("ee_mumu", "gg_ttx", "gg_ttxg", "gg_ttxgg")
+BUILT = ("ee_mumu", "gg_ttx", "gg_ttxg", "gg_ttxgg", "gg_ttxggg")
 FP64_TOL = 1e-12
 LOW_MEDIAN, LOW_MAX = 1e-5, 1e-3
 
@@ -46,7 +46,7 @@ def gpu_me2(name, prec, mom, filter_mom=None):
     return res
 
 
-SIZES = {"ee_mumu": 1001, "gg_ttx": 1001, "gg_ttxg": 1003, "gg_ttxgg": 517}
+SIZES = {"ee_mumu": 1001, "gg_ttx": 1001, "gg_ttxg": 1003, "gg_ttxgg": 517, "gg_ttxggg": 67}
 
 
 @pytest.mark.parametrize("name", BUILT)
@@ -60,7 +60,7 @@ def test_fp64_parity(orc, name):
 
 
 @pytest.mark.parametrize("prec", ["fp32", "mixed"])
-@pytest.mark.parametrize("name", ["gg_ttx", "gg_ttxg", "gg_ttxgg"])
+@pytest.mark.parametrize("name", ["gg_ttx", "gg_ttxg", "gg_ttxgg", "gg_ttxggg"])
 def test_low_precision_parity(orc, name, prec):
     n = SIZES[name]
     mom = oracle_events(orc, name, n)
@@ -73,7 +73,7 @@ def test_low_precision_parity(orc, name, prec):
 @pytest.mark.parametrize("name", BUILT)
 def test_per_helicity_parity_and_filter(orc, name):
     w = WORKLOADS[name]
-    mom = oracle_events(orc, name, 67)
+    mom = oracle_events(orc, name, 67 if name != "gg_ttxggg" else 19)
     ref, ref_hel = orc.me2(name, mom, mt=MT, alpha=w.alpha, per_helicity=True)
     h = me.workload_handle(name, "fp64")
     d = torch.from_numpy(mom).cuda()
@@ -107,7 +107,7 @@ def test_expected_helicity_counts(orc):
     assert counts["gg_ttx"] == 12
 
 
-@pytest.mark.parametrize("name", ["gg_ttx", "gg_ttxg", "gg_ttxgg"])
+@pytest.mark.parametrize("name", ["gg_ttx", "gg_ttxg", "gg_ttxgg", "gg_ttxggg"])
 def test_gauge_invariance_on_gpu(orc, name):
     """Ward identity: a gluon polarisation replaced by its momentum gives zero."""
     mom = oracle_events(orc, name, 33)
@@ -212,7 +212,8 @@ def test_rambo_full_size_sampled(orc):
         assert np.abs(g[i] - mom[0]).max() < 1e-9 * w.sqrt_s
 
 
-@pytest.mark.parametrize("name,prec", [("gg_ttxgg", "mixed"), ("gg_ttxgg", "fp64"), ("gg_ttx", "fp64")])
+@pytest.mark.parametrize("name,prec", [("gg_ttxgg", "mixed"), ("gg_ttxgg", "fp64"), ("gg_ttx", "fp64"),
+                                       ("gg_ttxggg", "mixed")])
 def test_full_size_sampled_parity(orc, name, prec):
     """BASELINE-size batch in the benchmark's launch configuration; sampled
     events checked one by one against the oracle."""
@@ -222,7 +223,7 @@ def test_full_size_sampled_parity(orc, name, prec):
     d = torch.from_numpy(mom).cuda()
     out = me.me_sigmakin(h, d).cpu().numpy()
     h.close()
-    idx = np.unique(np.r_[0, w.nevt - 1, np.random.default_rng(11).integers(0, w.nevt, 96)])
+    idx = np.unique(np.r_[0, w.nevt - 1, np.random.default_rng(11).integers(0, w.nevt, 96 if name != "gg_ttxggg" else 30)])
     ref = orc.me2(name, mom[idx], mt=MT, alpha=w.alpha)
     rel = np.abs(out[idx] / ref - 1)
     if prec == "fp64":

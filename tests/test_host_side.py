@@ -139,3 +139,22 @@ def test_abi_validation_without_device(lib):
     out = (ctypes.c_double * 16)()
     assert lib.rambo_sample(1, 0, 1, 1000.0, heavy, 4, None, out, None, None, None) == me.ME_EINVAL
     lib.me_free(None)
+
+
+@pytest.mark.parametrize("process,stage", [("gg_ttxgg", 16), ("gg_ttxggg", 16)])
+def test_staged_schedule_reproduces_oracle(orc, process, stage):
+    """The staged schedule for the descriptor kernel (slot reuse after each
+    object's last reader, variant indexing) gives the oracle's partial amplitudes."""
+    from paper_2507_21039_gb300.gen.interp import build_interp
+    from plan_eval import evaluate_staged
+
+    I = build_interp(process, stage)
+    w = WORKLOADS[process]
+    mom, _, _ = orc.rambo(w.seed, w.sqrt_s, w.masses_final, 3, 1, w.cut_mask, 20.0, 0.4)
+    p = mom[0]
+    npar = I.tab.plan.npar
+    scale = max(np.abs(orc.partial_amps(process, p, h)).max() for h in range(0, 1 << npar, 9))
+    for h in (0b0110101 & ((1 << npar) - 1), (1 << npar) - 1 - 6):
+        J = evaluate_staged(orc, I, p, h, MT)
+        A = orc.partial_amps(process, p, h)
+        assert np.abs(J - A).max() < 1e-12 * scale
