@@ -29,6 +29,12 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "|M|^2 events/s gg->t tbar gg (mixed vs FP64, 1 GB300); serving p50/p99 latency"
+# dominant kernel of the mixed-precision step, per workload
+KERNELS = {"ee_mumu": "me_kernel_scalar<ee_mumu, float>", "gg_ttx": "me_kernel_scalar<gg_ttx, float>",
+           "gg_ttxg": "me_kernel_tab<gg_ttxg, float>", "gg_ttxgg": "me_kernel_tab<gg_ttxgg, float>",
+           "gg_ttxggg": "me_kernel_interp<gg_ttxggg, float>"}
+PROCESS_LABEL = {"ee_mumu": "e+ e- -> mu+ mu-", "gg_ttx": "g g -> t t~", "gg_ttxg": "g g -> t t~ g",
+                 "gg_ttxgg": "g g -> t t~ g g", "gg_ttxggg": "g g -> t t~ g g g"}
 FP32_LANES_PER_SM = 128     # FP32 FMA lanes per SM (4 SMSPs x 32)
 N_SM = 152
 
@@ -304,13 +310,14 @@ def run_ours(args):
     achieved = flops / (me_ms / 1e3) / 1e12
     roofline = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
                 "frac": achieved / fp32_peak, "traffic": None,
-                "kernel": "me_kernel_tab<gg_ttxgg, float>",
+                "kernel": KERNELS[name],
                 "peak_source": f"derived: {N_SM} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 flops x "
                                f"{sm_max:.0f} MHz ({peak_src} sm_max_mhz)",
                 "flops_per_event": chain_f + colour_f, "me_kernel_ms": me_ms}
     # DRAM bytes of one launch from the committed ncu summary, if it was taken on
     # this kernel version (same generator flop count); null otherwise
-    traffic_file = os.path.join(ROOT, "profiles", "me_kernel_tab_gg_ttxgg_f32.traffic.txt")
+    slug = KERNELS[name].replace("<", "_").replace(">", "").replace(", float", "_f32").replace(" ", "")
+    traffic_file = os.path.join(ROOT, "profiles", f"{slug}.traffic.txt")
     if os.path.exists(traffic_file):
         kv = {}
         with open(traffic_file) as f:
@@ -325,10 +332,13 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": "events/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * elapsed_max / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": name, "process": "g g -> t t~ g g", "global_batch": n * world,
+        "config": {"workload": name, "process": PROCESS_LABEL[name], "global_batch": n * world,
                    "events_per_gpu": n, "sqrt_s": w.sqrt_s, "seed": w.seed, "precision": "mixed",
                    "cuts": "gluon pT > 20 GeV, pairwise dR > 0.4", "good_helicities": ngood,
-                   "l2": "inputs larger than L2 (momenta 201 MB per step)",
+                   "l2": (f"inputs larger than L2 (momenta {n * w.npar * 32 / 1e6:.0f} MB per step)"
+                          if n * w.npar * 32 > 129e6 else
+                          f"momenta {n * w.npar * 32 / 1e6:.0f} MB per step, smaller than L2; no flush "
+                          "(the kernel is bound by arithmetic, not memory)"),
                    "step": "rambo_sample (device) + me_sigmakin", "parallelism": f"replicas x{world}"},
         "fp64": {"value": value64, "unit": "events/s", "ms_per_step": 1e3 * el64 / args.fp64_steps,
                  "me_kernel_ms": statistics.mean(kern64)},

@@ -20,7 +20,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
-BUILD = os.path.join(HERE, "_build")
+BUILD = os.environ.get("ME_BUILD_DIR") or os.path.join(HERE, "_build")
 GEN = os.path.join(BUILD, "gen")
 OBJ = os.path.join(BUILD, "obj")
 LIB = os.path.join(BUILD, "libme.so")
@@ -99,7 +99,7 @@ def _compile(src: str, obj: str) -> tuple[str, str]:
 def build(force: bool = False, verbose: bool = False, jobs: int | None = None) -> str:
     os.makedirs(OBJ, exist_ok=True)
     stamp = os.path.join(BUILD, "stamp")
-    dig = _digest(_inputs()) + ",".join(PROCESSES)
+    dig = _digest(_inputs()) + ",".join(PROCESSES) + os.environ.get("ME_GEN_KERNEL", "")
     if not force and os.path.exists(LIB) and os.path.exists(stamp) and open(stamp).read() == dig:
         return LIB
     gen_srcs = generate()

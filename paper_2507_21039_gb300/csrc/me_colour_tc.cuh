@@ -123,3 +123,92 @@ __device__ __forceinline__ float colour_tc_warp(const cx<float> (&J)[NCOL], unsi
 }
 
 }  // namespace me
+
+namespace me {
+
+// Tensor-core colour quadratic form for J held in shared memory as
+// jsm[c * NT + thread] (FP32 complex).  Per warp: rows = its 32 threads' Re J
+// (half 0) or Im J (half 1); A fragments are built straight from jsm (BF16 hi/lo
+// split), Y = A N accumulates in FP32 over the K steps of each n-tile, and each
+// fragment entry Y[row][n] is immediately multiplied by J_row[n] from jsm.
+// Returns this thread's own J^+ N J (rows are summed within quads, then handed
+// to their owners through `rowv`, NT floats of shared memory).
+template <int NCOL, int NT, bool NSPLIT>
+__device__ __forceinline__ float colour_tc_smem(const cx<float>* __restrict__ jsm, const uint2* __restrict__ bfrag,
+                                                float* __restrict__ rowv, int tid)
+{
+    using S = TcShape<NCOL>;
+    const int lane = tid & 31, wbase = tid & ~31;
+    const int g = lane >> 2, t = lane & 3;
+    const float* jf = reinterpret_cast<const float*>(jsm);
+    float own = 0.0f;
+#pragma unroll 1
+    for (int half = 0; half < 2; ++half) {
+        float rsum[2][2] = {{0.0f, 0.0f}, {0.0f, 0.0f}};  // [mt][row g / g+8]
+#pragma unroll 1
+        for (int mt = 0; mt < 2; ++mt) {
+            const int l0 = wbase + 16 * mt + g, l1 = l0 + 8;  // threads owning rows g and g+8
+            uint32_t ahi[S::KS][4], alo[S::KS][4];
+#pragma unroll
+            for (int ks = 0; ks < S::KS; ++ks) {
+                const int c0 = 16 * ks + 2 * t;
+                float v[8];
+                const int cols[4] = {c0, c0 + 1, c0 + 8, c0 + 9};
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    v[q] = cols[q] < NCOL ? jf[2 * (cols[q] * NT + l0) + half] : 0.0f;
+                    v[4 + q] = cols[q] < NCOL ? jf[2 * (cols[q] * NT + l1) + half] : 0.0f;
+                }
+                split2(v[0], v[1], ahi[ks][0], alo[ks][0]);  // row g,   k = c0, c0+1
+                split2(v[4], v[5], ahi[ks][1], alo[ks][1]);  // row g+8, k = c0, c0+1
+                split2(v[2], v[3], ahi[ks][2], alo[ks][2]);  // row g,   k = c0+8, c0+9
+                split2(v[6], v[7], ahi[ks][3], alo[ks][3]);  // row g+8, k = c0+8, c0+9
+            }
+#pragma unroll 1
+            for (int nt = 0; nt < S::NT8; ++nt) {
+                float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll
+                for (int ks = 0; ks < S::KS; ++ks) {
+                    const uint2 b = __ldg(bfrag + (ks * S::NT8 + nt) * 32 + lane);
+                    mma_bf16(acc, ahi[ks][0], ahi[ks][1], ahi[ks][2], ahi[ks][3], b.x, b.y);
+                    mma_bf16(acc, alo[ks][0], alo[ks][1], alo[ks][2], alo[ks][3], b.x, b.y);
+                    if constexpr (NSPLIT) {
+                        const uint2 bl = __ldg(bfrag + (S::KS * S::NT8 + ks * S::NT8 + nt) * 32 + lane);
+                        mma_bf16(acc, ahi[ks][0], ahi[ks][1], ahi[ks][2], ahi[ks][3], bl.x, bl.y);
+                    }
+                }
+                const int n0 = 8 * nt + 2 * t;
+                if (n0 < NCOL) {
+                    rsum[mt][0] = fmaf(acc[0], jf[2 * (n0 * NT + l0) + half], rsum[mt][0]);
+                    rsum[mt][1] = fmaf(acc[2], jf[2 * (n0 * NT + l1) + half], rsum[mt][1]);
+                }
+                if (n0 + 1 < NCOL) {
+                    rsum[mt][0] = fmaf(acc[1], jf[2 * ((n0 + 1) * NT + l0) + half], rsum[mt][0]);
+                    rsum[mt][1] = fmaf(acc[3], jf[2 * ((n0 + 1) * NT + l1) + half], rsum[mt][1]);
+                }
+            }
+        }
+        // row totals: sum the 4 threads of each quad, then hand each row to its owner
+#pragma unroll
+        for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+            for (int r = 0; r < 2; ++r) {
+                float x = rsum[mt][r];
+                x += __shfl_xor_sync(0xffffffffu, x, 1);
+                x += __shfl_xor_sync(0xffffffffu, x, 2);
+                rsum[mt][r] = x;
+            }
+        if (t == 0) {
+            rowv[wbase + g] = rsum[0][0];
+            rowv[wbase + g + 8] = rsum[0][1];
+            rowv[wbase + 16 + g] = rsum[1][0];
+            rowv[wbase + 24 + g] = rsum[1][1];
+        }
+        __syncwarp();
+        own += rowv[tid];
+        __syncwarp();
+    }
+    return own;
+}
+
+}  // namespace me

@@ -60,8 +60,9 @@ __device__ __forceinline__ void run_task(const TabRef<T, TAB>& tab, const Ln<T>*
     tab.st(k.out, o);
 }
 
-template <class P, class T>
-__global__ void __launch_bounds__(P::NT, 1) me_kernel_interp(LaunchArgs a, cx<T>* __restrict__ jglobal)
+// TC: colour sum on BF16 tensor cores (T = float); otherwise scalar in T
+template <class P, class T, bool TC>
+__global__ void __launch_bounds__(P::NT) me_kernel_interp(LaunchArgs a, cx<T>* __restrict__ jglobal)
 {
     using L = InterpLayout<P, T>;
     extern __shared__ __align__(16) unsigned char smem[];
@@ -74,6 +75,7 @@ __global__ void __launch_bounds__(P::NT, 1) me_kernel_interp(LaunchArgs a, cx<T>
     cx<T>* jp = L::J_IN_SMEM ? reinterpret_cast<cx<T>*>(smem + L::jsm) + threadIdx.x
                              : jglobal + (size_t)blockIdx.x * NCOL * NT + threadIdx.x;
     __shared__ double red[NT / 32];
+    __shared__ float rowv[NT];
     const int tid = threadIdx.x;
     const bool act = tid < a.nlist;
     const int h = a.hel_list[act ? tid : 0];
@@ -132,18 +134,23 @@ __global__ void __launch_bounds__(P::NT, 1) me_kernel_interp(LaunchArgs a, cx<T>
             }
             __syncthreads();  // stage done: its dead table slots are reused by the next stage
         }
-        // colour quadratic form sum_ij N_ij Re(conj J_i J_j), scalar in T
+        // colour quadratic form sum_ij N_ij Re(conj J_i J_j)
         T v = T(0);
-        for (int i = 0; i < NCOL; ++i) {
-            const cx<T> ji = jp[i * NT];
-            T zr = T(0), zi = T(0);
-            for (int j = i; j < NCOL; ++j) {
-                const T n = (T)P::cnum2(i, j);
-                const cx<T> jj = jp[j * NT];
-                zr = fma(n, jj.re, zr);
-                zi = fma(n, jj.im, zi);
+        if constexpr (TC) {
+            v = colour_tc_smem<NCOL, NT, P::NSPLIT>(reinterpret_cast<const cx<float>*>(smem + L::jsm), P::bfrag(),
+                                                    rowv, tid);
+        } else {
+            for (int i = 0; i < NCOL; ++i) {
+                const cx<T> ji = jp[i * NT];
+                T zr = T(0), zi = T(0);
+                for (int j = i; j < NCOL; ++j) {
+                    const T n = (T)P::cnum2(i, j);
+                    const cx<T> jj = jp[j * NT];
+                    zr = fma(n, jj.re, zr);
+                    zi = fma(n, jj.im, zi);
+                }
+                v = fma(ji.re, zr, fma(ji.im, zi, v));
             }
-            v = fma(ji.re, zr, fma(ji.im, zi, v));
         }
         double acc = 0.0;
         if (act) {
@@ -162,24 +169,31 @@ __global__ void __launch_bounds__(P::NT, 1) me_kernel_interp(LaunchArgs a, cx<T>
     }
 }
 
-template <class P, class T> cudaError_t launch_interp(const LaunchArgs& a)
+template <class P, class T, bool TC = false> cudaError_t launch_interp(const LaunchArgs& a)
 {
     using L = InterpLayout<P, T>;
+    static_assert(!TC || sizeof(T) == 4, "tensor-core colour sum is the mixed-precision path");
     static_assert(L::bytes <= 232448, "interpreter shared memory exceeds 227 KB");
     if (a.nlist > P::NT) return cudaErrorInvalidValue;
     static size_t granted = 0;
-    cudaError_t e = ensure_smem(me_kernel_interp<P, T>, L::bytes, granted);
+    cudaError_t e = ensure_smem(me_kernel_interp<P, T, TC>, L::bytes, granted);
     if (e != cudaSuccess) return e;
-    int dev = 0, nsm = 0;
+    int dev = 0, nsm = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    const long long grid = a.nevt < nsm ? a.nevt : nsm;  // one resident CTA per SM, persistent over events
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, me_kernel_interp<P, T, TC>, P::NT, L::bytes) != cudaSuccess ||
+        per_sm < 1) {
+        cudaGetLastError();
+        per_sm = 1;
+    }
+    const long long slots = (long long)nsm * per_sm;  // resident CTAs, persistent over events
+    const long long grid = a.nevt < slots ? a.nevt : slots;
     cx<T>* jg = nullptr;
     if constexpr (!L::J_IN_SMEM) {
         e = cudaMallocAsync(&jg, sizeof(cx<T>) * (size_t)grid * P::NCOL * P::NT, a.stream);
         if (e != cudaSuccess) return e;
     }
-    me_kernel_interp<P, T><<<(unsigned)grid, P::NT, L::bytes, a.stream>>>(a, jg);
+    me_kernel_interp<P, T, TC><<<(unsigned)grid, P::NT, L::bytes, a.stream>>>(a, jg);
     e = cudaGetLastError();
     if (jg) cudaFreeAsync(jg, a.stream);
     return e;

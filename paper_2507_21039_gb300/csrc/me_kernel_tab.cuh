@@ -185,12 +185,13 @@ template <class P, class T, bool TC = false> cudaError_t launch_tab(const Launch
 
 // Mixed precision: FP32 chain; colour sum on BF16 tensor cores for 24 or more
 // colour flows when every thread holds one helicity, FP32 scalar otherwise.
-template <class P, class T> cudaError_t launch_interp(const LaunchArgs& a);
+template <class P, class T, bool TC> cudaError_t launch_interp(const LaunchArgs& a);
 
 template <class P> cudaError_t launch_mixed(const LaunchArgs& a)
 {
     if constexpr (P::IS_INTERP) {
-        return launch_interp<P, float>(a);
+        if constexpr (P::NCOL >= 24) return launch_interp<P, float, true>(a);
+        else return launch_interp<P, float, false>(a);
     } else if constexpr (P::IS_TAB) {
         if constexpr (P::NCOL >= 24) {
             if (a.nlist <= P::NT) return launch_tab<P, float, true>(a);

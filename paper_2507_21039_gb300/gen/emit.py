@@ -23,6 +23,26 @@ TAB_PROCESSES = {"gg_ttxg": 32, "gg_ttxgg": 64}   # process -> threads per event
 INTERP_PROCESSES = {"gg_ttxggg": (128, 16)}        # process -> (threads per event, amplitudes per stage)
 
 
+def _apply_kernel_overrides():
+    """Build option ME_GEN_KERNEL="proc=interp:NT:STAGE,proc=tab:NT,..." selects
+    the kernel family of a process (used to compare kernel designs)."""
+    import os
+
+    spec = os.environ.get("ME_GEN_KERNEL", "")
+    for item in filter(None, (x.strip() for x in spec.split(","))):
+        proc, what = item.split("=")
+        parts = what.split(":")
+        TAB_PROCESSES.pop(proc, None)
+        INTERP_PROCESSES.pop(proc, None)
+        if parts[0] == "interp":
+            INTERP_PROCESSES[proc] = (int(parts[1]), int(parts[2]))
+        elif parts[0] == "tab":
+            TAB_PROCESSES[proc] = int(parts[1])
+
+
+_apply_kernel_overrides()
+
+
 def _ext_table(process: str):
     if process == "ee_mumu":
         # e-(in) u, e+(in) vbar, mu-(out) ubar, mu+(out) v; massless
@@ -247,8 +267,8 @@ struct Proc {{
 static cudaError_t launch(int precision, const LaunchArgs& a)
 {{
     switch (precision) {{
-    case PREC_FP64: return {launch_fn}<{kernel_struct}, double>(a);
-    case PREC_FP32: return {launch_fn}<{kernel_struct}, float>(a);
+    case PREC_FP64: return {launch_fn}<{kernel_struct}, double{", false" if IP else ""}>(a);
+    case PREC_FP32: return {launch_fn}<{kernel_struct}, float{", false" if IP else ""}>(a);
     case PREC_MIXED: return launch_mixed<{kernel_struct}>(a);
     default: return cudaErrorInvalidValue;
     }}
