@@ -96,35 +96,50 @@ template <class P, class T> __host__ __device__ constexpr size_t tab_smem_bytes(
 
 // TC: colour sum on the tensor cores (T = float, NCOL >= 24, one helicity per
 // thread: nlist <= NT); otherwise the scalar quadratic form in precision T.
+// EPC events share a CTA (NT threads each, own shared-memory region); CTA-wide
+// barriers keep their warps at the same point of the amplitude code, so they
+// share instruction-cache lines and overlap each other's long-latency FP64 work.
+template <class P, class T> __host__ __device__ constexpr int tab_epc() { return sizeof(T) == 8 ? P::EPC_D : P::EPC_F; }
+
 template <class P, class T, bool TC>
-__global__ void __launch_bounds__(P::NT, sizeof(T) == 8 ? P::MIN_CTAS_D : P::MIN_CTAS_F) me_kernel_tab(LaunchArgs a)
+__global__ void __launch_bounds__(P::NT * tab_epc<P, T>(), sizeof(T) == 8 ? P::MIN_CTAS_D : P::MIN_CTAS_F)
+    me_kernel_tab(LaunchArgs a)
 {
-    extern __shared__ __align__(16) unsigned char smem[];
-    constexpr int NPAR = P::NPAR, NL = P::NLINES, NT = P::NT;
+    extern __shared__ __align__(16) unsigned char smem_all[];
+    constexpr int NPAR = P::NPAR, NL = P::NLINES, NT = P::NT, EPC = tab_epc<P, T>();
+    const int grp = threadIdx.x / NT;      // event slot of this thread within the CTA
+    const int tid = threadIdx.x - grp * NT;
+    unsigned char* smem = smem_all + grp * tab_smem_bytes<P, T>();
     double* smom = reinterpret_cast<double*>(smem);
     Ln<T>* sln = reinterpret_cast<Ln<T>*>(smem + tab_line_offset<P, T>());
     const TabRef<T, P::TAB> tab{reinterpret_cast<uint4*>(smem + tab_table_offset<P, T>())};
-    __shared__ double red[NT / 32];
-    const int tid = threadIdx.x;
+    __shared__ double red[EPC][NT / 32 > 0 ? NT / 32 : 1];
 
-    for (long long e = blockIdx.x; e < a.nevt; e += gridDim.x) {
+    for (long long e0 = (long long)blockIdx.x * EPC; e0 < a.nevt; e0 += (long long)gridDim.x * EPC) {
+        const long long e = e0 + grp;
+        const bool live = e < a.nevt;      // a ragged last CTA still takes part in every barrier
         // (a1) momenta
-        const double* g = a.mom + e * NPAR * 4;
-        if ((reinterpret_cast<uintptr_t>(g) & 15) == 0) {
-            if (tid < NPAR * 2)
-                reinterpret_cast<double2*>(smom)[tid] = __ldg(reinterpret_cast<const double2*>(g) + tid);
-        } else {
-            for (int i = tid; i < NPAR * 4; i += NT) smom[i] = __ldg(g + i);
+        if (live) {
+            const double* g = a.mom + e * NPAR * 4;
+            if ((reinterpret_cast<uintptr_t>(g) & 15) == 0) {
+                if (tid < NPAR * 2)
+                    reinterpret_cast<double2*>(smom)[tid] = __ldg(reinterpret_cast<const double2*>(g) + tid);
+            } else {
+                for (int i = tid; i < NPAR * 4; i += NT) smom[i] = __ldg(g + i);
+            }
         }
         __syncthreads();
-        // (a2, a3 denominators) FP64 per-event data; external wavefunctions are
-        // the first 2*NPAR table entries
-        for (int it = tid; it < 2 * NPAR + NL; it += NT) {
-            if (it < 2 * NPAR) tab.st(it, ext_wavefunction<P, T>(smom, it, a.mt, a.gauge_ext));
-            else sln[it - 2 * NPAR] = line_data<P, T>(smom, it - 2 * NPAR, a.mt);
+        // (a2, a3 denominators) per-event data; external wavefunctions are the
+        // first 2*NPAR table entries
+        if (live) {
+            for (int it = tid; it < 2 * NPAR + NL; it += NT) {
+                if (it < 2 * NPAR) tab.st(it, ext_wavefunction<P, T>(smom, it, a.mt, a.gauge_ext));
+                else sln[it - 2 * NPAR] = line_data<P, T>(smom, it - 2 * NPAR, a.mt);
+            }
         }
         __syncthreads();
         // (a3) off-shell objects for every helicity configuration of their support
+        // (a dead slot computes on whatever its shared memory holds; nothing is stored)
         P::template tables<T>(tab, sln, (T)a.mt, tid);
         __syncthreads();
         // (a4-a6) amplitudes per good helicity, colour sum, FP64 accumulation.
@@ -134,8 +149,8 @@ __global__ void __launch_bounds__(P::NT, sizeof(T) == 8 ? P::MIN_CTAS_D : P::MIN
         double acc = 0.0;
         for (int base = 0; base < a.nlist; base += NT) {
             const int i = base + tid;
-            const bool act = i < a.nlist;
-            const int h = a.hel_list[act ? i : 0];
+            const bool act = live && i < a.nlist;
+            const int h = a.hel_list[i < a.nlist ? i : 0];
             cx<T> J[P::NCOL];
 #pragma unroll
             for (int c = 0; c < P::NCOL; ++c) J[c] = {T(0), T(0)};
@@ -155,31 +170,33 @@ __global__ void __launch_bounds__(P::NT, sizeof(T) == 8 ? P::MIN_CTAS_D : P::MIN
         }
         for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
         if constexpr (NT > 32) {
-            if ((tid & 31) == 0) red[tid >> 5] = acc;
+            if ((tid & 31) == 0) red[grp][tid >> 5] = acc;
             __syncthreads();
-            if (tid == 0) {
+            if (tid == 0 && live) {
                 double s = 0.0;
-                for (int w = 0; w < NT / 32; ++w) s += red[w];
+                for (int w = 0; w < NT / 32; ++w) s += red[grp][w];
                 a.me2[e] = s * a.norm;
             }
         } else {
-            if (tid == 0) a.me2[e] = acc * a.norm;
+            if (tid == 0 && live) a.me2[e] = acc * a.norm;
         }
-        __syncthreads();  // shared memory is reused by the next event
+        __syncthreads();  // shared memory is reused by the next events
     }
 }
 
 template <class P, class T, bool TC = false> cudaError_t launch_tab(const LaunchArgs& a)
 {
-    constexpr size_t smem = tab_smem_bytes<P, T>();
+    constexpr int EPC = tab_epc<P, T>();
+    constexpr size_t smem = tab_smem_bytes<P, T>() * EPC;
     if constexpr (TC)
         static_assert((P::NT / 32) * TcShape<P::NCOL>::WARP_BYTES <= P::TAB * sizeof(Wf<T>),
                       "tensor-core staging must fit in the table region");
     static size_t granted = 0;
     cudaError_t e = ensure_smem(me_kernel_tab<P, T, TC>, smem, granted);
     if (e != cudaSuccess) return e;
-    const long long grid = a.nevt < 0x7fffffffLL ? a.nevt : 0x7fffffffLL;
-    me_kernel_tab<P, T, TC><<<(unsigned)grid, P::NT, smem, a.stream>>>(a);
+    const long long ctas = (a.nevt + EPC - 1) / EPC;
+    const long long grid = ctas < 0x7fffffffLL ? ctas : 0x7fffffffLL;
+    me_kernel_tab<P, T, TC><<<(unsigned)grid, P::NT * EPC, smem, a.stream>>>(a);
     return cudaGetLastError();
 }
 

@@ -18,7 +18,8 @@ from .tabplan import build_tabplan
 
 EXT_KINDS = {"VIN": 0, "VOUT": 1, "FO_U": 2, "FO_V": 3, "FI_U": 4, "FI_V": 5}
 # processes evaluated with the helicity-recycled table kernel (me_kernel_tab.cuh)
-TAB_PROCESSES = {"gg_ttxg": 32, "gg_ttxgg": 64}   # process -> threads per event
+# process -> (threads per event, events per CTA in FP32 / mixed, in FP64)
+TAB_PROCESSES = {"gg_ttxg": (32, 1, 1), "gg_ttxgg": (64, 1, 2)}
 # processes evaluated with the staged descriptor kernel (me_kernel_interp.cuh)
 INTERP_PROCESSES = {"gg_ttxggg": (128, 16)}        # process -> (threads per event, amplitudes per stage)
 
@@ -37,7 +38,8 @@ def _apply_kernel_overrides():
         if parts[0] == "interp":
             INTERP_PROCESSES[proc] = (int(parts[1]), int(parts[2]))
         elif parts[0] == "tab":
-            TAB_PROCESSES[proc] = int(parts[1])
+            TAB_PROCESSES[proc] = (int(parts[1]), int(parts[2]) if len(parts) > 2 else 1,
+                                   int(parts[3]) if len(parts) > 3 else 1)
 
 
 _apply_kernel_overrides()
@@ -195,7 +197,8 @@ def emit_process(process: str) -> tuple[str, dict]:
 
     tab_src, TP, IP = ("", None, None)
     if process in TAB_PROCESSES:
-        tab_src, TP = emit_tab_struct(process, TAB_PROCESSES[process], ncol, nlines, cbody)
+        nt_t, epc_f, epc_d = TAB_PROCESSES[process]
+        tab_src, TP = emit_tab_struct(process, nt_t, epc_f, epc_d, ncol, nlines, cbody)
     elif process in INTERP_PROCESSES:
         nt_i, sa = INTERP_PROCESSES[process]
         tab_src, IP = emit_interp_struct(process, nt_i, sa, num)
@@ -321,7 +324,7 @@ def _table_call(kind, k="k"):
     return f"Wf<T> o; {c} tab.st({k}.out, o);"
 
 
-def emit_tab_struct(process: str, nt: int, ncol: int, nlines: int, colour_body: list):
+def emit_tab_struct(process: str, nt: int, epc_f: int, epc_d: int, ncol: int, nlines: int, colour_body: list):
     """ProcTab: task table, level-by-level table rounds, per-helicity amplitudes."""
     TP = build_tabplan(process)
     P = TP.plan
@@ -379,9 +382,12 @@ __device__ const TabTask c_tasks[{max(len(tasks), 1)}] = {{
 // {TP.table_flops()} table flops per event, {TP.amplitude_flops_per_helicity()} amplitude flops per helicity
 struct ProcTab : Proc {{
     static constexpr int NT = {nt}, TAB = {TP.size};
+    // events per CTA (own shared-memory region each; CTA barriers keep their
+    // warps at the same point of the code), in FP32 / mixed and in FP64
+    static constexpr int EPC_F = {epc_f}, EPC_D = {epc_d};
     // register budget: FP32 <= 128 per thread (occupancy bound by shared memory
     // anyway), FP64 <= 255 (its tables are twice as large)
-    static constexpr int MIN_CTAS_F = {max(1, 65536 // (nt * 128))}, MIN_CTAS_D = {max(1, 65536 // (nt * 255))};
+    static constexpr int MIN_CTAS_F = {max(1, 65536 // (nt * epc_f * 128))}, MIN_CTAS_D = {max(1, 65536 // (nt * epc_d * 255))};
     static constexpr bool IS_TAB = true, IS_INTERP = false;
     static constexpr long long TABLE_FLOPS = {TP.table_flops()}LL, AMP_FLOPS = {TP.amplitude_flops_per_helicity()}LL;
 
