@@ -30,8 +30,11 @@ NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-r
               "-Xptxas", "-v", "-I", INCLUDE, "-I", CSRC]
 
 STATIC_SOURCES = ["me_abi.cu", "rambo.cu", "serve.cu"]
-# processes compiled into the library
-PROCESSES = ("ee_mumu", "gg_ttx", "gg_ttxg", "gg_ttxgg", "gg_ttxggg")
+# processes compiled into the library (build option ME_BUILD_PROCESSES: a
+# comma-separated subset, for quicker builds of kernel variants)
+ALL_PROCESSES = ("ee_mumu", "gg_ttx", "gg_ttxg", "gg_ttxgg", "gg_ttxggg")
+PROCESSES = tuple(p for p in os.environ.get("ME_BUILD_PROCESSES", ",".join(ALL_PROCESSES)).split(",")
+                  if p in ALL_PROCESSES) or ALL_PROCESSES
 
 
 def nvcc() -> str:
@@ -88,8 +91,14 @@ def generate(processes=None) -> list:
     return srcs
 
 
+def _extra_flags() -> list:
+    """Build option ME_NVCC_EXTRA: additional preprocessor definitions (-DNAME=V),
+    used to compare kernel tuning parameters."""
+    return [f for f in os.environ.get("ME_NVCC_EXTRA", "").split() if f.startswith("-D")]
+
+
 def _compile(src: str, obj: str) -> tuple[str, str]:
-    cmd = [nvcc()] + ARCH + NVCC_FLAGS + ["-c", src, "-o", obj]
+    cmd = [nvcc()] + ARCH + NVCC_FLAGS + _extra_flags() + ["-c", src, "-o", obj]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"nvcc failed for {src}:\n{r.stderr[-4000:]}")
@@ -99,7 +108,7 @@ def _compile(src: str, obj: str) -> tuple[str, str]:
 def build(force: bool = False, verbose: bool = False, jobs: int | None = None) -> str:
     os.makedirs(OBJ, exist_ok=True)
     stamp = os.path.join(BUILD, "stamp")
-    dig = _digest(_inputs()) + ",".join(PROCESSES) + os.environ.get("ME_GEN_KERNEL", "")
+    dig = _digest(_inputs()) + ",".join(PROCESSES) + os.environ.get("ME_GEN_KERNEL", "") + " ".join(_extra_flags())
     if not force and os.path.exists(LIB) and os.path.exists(stamp) and open(stamp).read() == dig:
         return LIB
     gen_srcs = generate()

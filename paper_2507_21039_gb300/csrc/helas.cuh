@@ -14,6 +14,8 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "f32x2.cuh"
+
 namespace me {
 
 template <class T> struct cx { T re, im; };
@@ -64,9 +66,38 @@ template <class T> __device__ __forceinline__ Blk<T> sblk(const Wf<T>& V)
     Blk<T> b;
     b.s00 = V.c[0] - V.c[3];
     b.s11 = V.c[0] + V.c[3];
-    b.s01 = {-V.c[1].re - V.c[2].im, -V.c[1].im + V.c[2].re};   // -V1 + i V2
-    b.s10 = {-V.c[1].re + V.c[2].im, -V.c[1].im - V.c[2].re};   // -V1 - i V2
+    b.s01 = {-(V.c[1].re + V.c[2].im), V.c[2].re - V.c[1].im};   // -V1 + i V2
+    b.s10 = {V.c[2].im - V.c[1].re, -(V.c[1].im + V.c[2].re)};   // -V1 - i V2
     return b;
+}
+
+// Packed-FP32x2 forms of the complex helpers: products are grouped into
+// positive and negative parts joined by one subtraction, because the packed
+// instruction set has no negated-operand form (the operations per lane are the
+// same products and sums, in a different order).
+__device__ __forceinline__ cx<f2> operator*(cx<f2> a, cx<f2> b)
+{
+    return {a.re * b.re - a.im * b.im, fma(a.re, b.im, a.im * b.re)};
+}
+__device__ __forceinline__ cx<f2> cfma(cx<f2> a, cx<f2> b, cx<f2> c)
+{
+    return {fma(a.re, b.re, c.re) - a.im * b.im, fma(a.re, b.im, fma(a.im, b.re, c.im))};
+}
+__device__ __forceinline__ cx<f2> mdot(const Wf<f2>& a, const Wf<f2>& b)
+{
+    const cx<f2>*x = a.c, *y = b.c;
+    const f2 pr = fma(x[3].im, y[3].im, fma(x[2].im, y[2].im, fma(x[1].im, y[1].im, x[0].re * y[0].re)));
+    const f2 nr = fma(x[3].re, y[3].re, fma(x[2].re, y[2].re, fma(x[1].re, y[1].re, x[0].im * y[0].im)));
+    const f2 pi = fma(x[0].re, y[0].im, x[0].im * y[0].re);
+    const f2 ni = fma(x[3].re, y[3].im, fma(x[3].im, y[3].re, fma(x[2].re, y[2].im,
+                  fma(x[2].im, y[2].re, fma(x[1].re, y[1].im, x[1].im * y[1].re)))));
+    return {pr - nr, pi - ni};
+}
+__device__ __forceinline__ cx<f2> rdot(const f2* k, const Wf<f2>& a)
+{
+    const f2 nr = fma(k[3], a.c[3].re, fma(k[2], a.c[2].re, k[1] * a.c[1].re));
+    const f2 ni = fma(k[3], a.c[3].im, fma(k[2], a.c[2].im, k[1] * a.c[1].im));
+    return {k[0] * a.c[0].re - nr, k[0] * a.c[0].im - ni};
 }
 
 // ---------------------------------------------------------------------------
@@ -96,8 +127,8 @@ __device__ __forceinline__ cx<T> VVV1_0(const Wf<T>& A, const T* PA, const Wf<T>
 #pragma unroll
     for (int m = 0; m < 4; ++m) {
         d12[m] = PB[m] - PA[m];
-        d23[m] = -PA[m] - 2 * PB[m];
-        d31[m] = 2 * PA[m] + PB[m];
+        d23[m] = -fma(T(2), PB[m], PA[m]);
+        d31[m] = fma(T(2), PA[m], PB[m]);
     }
     cx<T> ab = mdot(A, B), bq = mdot(B, Q), qa = mdot(Q, A);
     return ab * rdot(d12, Q) + bq * rdot(d23, A) + qa * rdot(d31, B);
@@ -131,8 +162,8 @@ __device__ __forceinline__ void VVV1P0_1(const Wf<T>& A, const T* PA, const Wf<T
 #pragma unroll
     for (int m = 0; m < 4; ++m) {
         d12[m] = PB[m] - PA[m];
-        d23[m] = -PA[m] - 2 * PB[m];
-        d31[m] = 2 * PA[m] + PB[m];
+        d23[m] = -fma(T(2), PB[m], PA[m]);
+        d31[m] = fma(T(2), PA[m], PB[m]);
     }
     cx<T> ab = inv * mdot(A, B), a = inv * rdot(d23, A), b = inv * rdot(d31, B);
 #pragma unroll
@@ -222,6 +253,111 @@ __device__ __forceinline__ void FFV1_1(const Wf<T>& V, const Wf<T>& Fi, const Ln
     out.c[1] = inv * yl1;
     out.c[2] = inv * yr0;
     out.c[3] = inv * yr1;
+}
+
+// ---------------------------------------------------------------------------
+// amputated vertices (no propagator) and two-operand contractions.  A final
+// vertex with one operand's index left open; contracting it with that operand
+// gives the amplitude of the direct vertex routine (same products, grouped
+// differently), e.g. FFV1_0(Fo, V, Fi) = DOTV(FFV1A_3(Fo, Fi), V)
+// = DOTF(FFV1A_2(Fo, V), Fi) = DOTF(Fo, FFV1A_1(V, Fi)).
+// ---------------------------------------------------------------------------
+// spinor contraction (row) . (column), no metric
+template <class T> __device__ __forceinline__ cx<T> sdot(const Wf<T>& a, const Wf<T>& b)
+{
+    cx<T> s = a.c[0] * b.c[0];
+    s = cfma(a.c[1], b.c[1], s);
+    s = cfma(a.c[2], b.c[2], s);
+    s = cfma(a.c[3], b.c[3], s);
+    return s;
+}
+__device__ __forceinline__ cx<f2> sdot(const Wf<f2>& a, const Wf<f2>& b)
+{
+    const cx<f2>*x = a.c, *y = b.c;
+    const f2 pr = fma(x[3].re, y[3].re, fma(x[2].re, y[2].re, fma(x[1].re, y[1].re, x[0].re * y[0].re)));
+    const f2 nr = fma(x[3].im, y[3].im, fma(x[2].im, y[2].im, fma(x[1].im, y[1].im, x[0].im * y[0].im)));
+    const f2 im = fma(x[3].re, y[3].im, fma(x[3].im, y[3].re, fma(x[2].re, y[2].im, fma(x[2].im, y[2].re,
+                  fma(x[1].re, y[1].im, fma(x[1].im, y[1].re, fma(x[0].re, y[0].im, x[0].im * y[0].re)))))));
+    return {pr - nr, im};
+}
+template <class T> __device__ __forceinline__ cx<T> DOTV(const Wf<T>& a, const Wf<T>& b) { return mdot(a, b); }
+template <class T> __device__ __forceinline__ cx<T> DOTF(const Wf<T>& a, const Wf<T>& b) { return sdot(a, b); }
+
+// K^mu = Fo gamma^mu Fi
+template <class T> __device__ __forceinline__ void FFV1A_3(const Wf<T>& Fo, const Wf<T>& Fi, Wf<T>& out)
+{
+    const cx<T>*o = Fo.c, *i = Fi.c;
+    cx<T> a = o[0] * i[2], b = o[1] * i[3], c = o[2] * i[0], d = o[3] * i[1];
+    cx<T> e = o[0] * i[3], f = o[1] * i[2], g = o[2] * i[1], h = o[3] * i[0];
+    const cx<T> s2 = f + g - e - h;            // K2 = i * s2
+    out.c[0] = a + b + c + d;
+    out.c[1] = e + f - g - h;
+    out.c[2] = {-s2.im, s2.re};
+    out.c[3] = a - b - c + d;
+}
+// row spinor Fo gamma.V
+template <class T> __device__ __forceinline__ void FFV1A_2(const Wf<T>& Fo, const Wf<T>& V, Wf<T>& out)
+{
+    Blk<T> b = sblk(V);
+    out.c[0] = Fo.c[2] * b.s11 - Fo.c[3] * b.s10;
+    out.c[1] = Fo.c[3] * b.s00 - Fo.c[2] * b.s01;
+    out.c[2] = cfma(Fo.c[1], b.s10, Fo.c[0] * b.s00);
+    out.c[3] = cfma(Fo.c[1], b.s11, Fo.c[0] * b.s01);
+}
+// column spinor gamma.V Fi
+template <class T> __device__ __forceinline__ void FFV1A_1(const Wf<T>& V, const Wf<T>& Fi, Wf<T>& out)
+{
+    Blk<T> b = sblk(V);
+    out.c[0] = cfma(b.s01, Fi.c[3], b.s00 * Fi.c[2]);
+    out.c[1] = cfma(b.s11, Fi.c[3], b.s10 * Fi.c[2]);
+    out.c[2] = b.s11 * Fi.c[0] - b.s01 * Fi.c[1];
+    out.c[3] = b.s00 * Fi.c[1] - b.s10 * Fi.c[0];
+}
+// three-gluon vertex V^{mnr}(k1, k2, k3) A_m B_n Q_r (k1 = -PA, k2 = -PB,
+// k3 = PA + PB) with one leg open: OPEN = 3 (Q; inputs A, B), 1 (A; inputs B,
+// Q), 2 (B; inputs A, Q).  PA, PB are the momenta of legs A and B.
+template <int OPEN, class T>
+__device__ __forceinline__ void VVV1A(const Wf<T>& X, const Wf<T>& Y, const T* PA, const T* PB, Wf<T>& out)
+{
+    T d12[4], d23[4], d31[4];
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+        d12[m] = PB[m] - PA[m];
+        d23[m] = -fma(T(2), PB[m], PA[m]);
+        d31[m] = fma(T(2), PA[m], PB[m]);
+    }
+    if constexpr (OPEN == 3) {         // X = A, Y = B: (A.B) d12 + B (d23.A) + A (d31.B)
+        const cx<T> ab = mdot(X, Y), a = rdot(d23, X), b = rdot(d31, Y);
+#pragma unroll
+        for (int m = 0; m < 4; ++m) out.c[m] = cfma(Y.c[m], a, cfma(X.c[m], b, d12[m] * ab));
+    } else if constexpr (OPEN == 1) {  // X = B, Y = Q: B (d12.Q) + (B.Q) d23 + Q (d31.B)
+        const cx<T> bq = mdot(X, Y), q = rdot(d12, Y), b = rdot(d31, X);
+#pragma unroll
+        for (int m = 0; m < 4; ++m) out.c[m] = cfma(X.c[m], q, cfma(Y.c[m], b, d23[m] * bq));
+    } else {                           // X = A, Y = Q: A (d12.Q) + Q (d23.A) + (Q.A) d31
+        const cx<T> qa = mdot(Y, X), q = rdot(d12, Y), a = rdot(d23, X);
+#pragma unroll
+        for (int m = 0; m < 4; ++m) out.c[m] = cfma(X.c[m], q, cfma(Y.c[m], a, d31[m] * qa));
+    }
+}
+// four-gluon structures with the fourth leg open (VVVVnP0_1 without propagator)
+template <class T> __device__ __forceinline__ void VVVV1A(const Wf<T>& A, const Wf<T>& B, const Wf<T>& C, Wf<T>& out)
+{
+    const cx<T> x = mdot(A, C), y = mdot(B, C);
+#pragma unroll
+    for (int m = 0; m < 4; ++m) out.c[m] = x * B.c[m] - y * A.c[m];
+}
+template <class T> __device__ __forceinline__ void VVVV3A(const Wf<T>& A, const Wf<T>& B, const Wf<T>& C, Wf<T>& out)
+{
+    const cx<T> x = mdot(A, B), y = mdot(B, C);
+#pragma unroll
+    for (int m = 0; m < 4; ++m) out.c[m] = x * C.c[m] - y * A.c[m];
+}
+template <class T> __device__ __forceinline__ void VVVV4A(const Wf<T>& A, const Wf<T>& B, const Wf<T>& C, Wf<T>& out)
+{
+    const cx<T> x = mdot(A, B), y = mdot(A, C);
+#pragma unroll
+    for (int m = 0; m < 4; ++m) out.c[m] = x * C.c[m] - y * B.c[m];
 }
 
 // J_c += (R + i I) a for a Gaussian-integer colour/phase coefficient

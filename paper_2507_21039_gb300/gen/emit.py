@@ -18,8 +18,13 @@ from .tabplan import build_tabplan
 
 EXT_KINDS = {"VIN": 0, "VOUT": 1, "FO_U": 2, "FO_V": 3, "FI_U": 4, "FI_V": 5}
 # processes evaluated with the helicity-recycled table kernel (me_kernel_tab.cuh)
-# process -> (threads per event, events per CTA in FP32 / mixed, in FP64)
-TAB_PROCESSES = {"gg_ttxg": (32, 1, 1), "gg_ttxgg": (64, 1, 2)}
+# process -> (threads per event, events (event pairs) per CTA in FP32 / mixed,
+#             events per CTA in FP64, FP32 / mixed as packed FP32x2 event pairs,
+#             amplitudes as contractions of amputated vertex objects,
+#             amplitudes per stage (0: one resident table),
+#             warp fence every n amplitudes in FP32, FP32x2, FP64)
+# (measured on GB300 over stage sizes, events per CTA and fence intervals)
+TAB_PROCESSES = {"gg_ttxg": (32, 1, 1, 0, 1, 0, 1, 6, 4), "gg_ttxgg": (64, 2, 2, 0, 1, 64, 4, 6, 4)}
 # processes evaluated with the staged descriptor kernel (me_kernel_interp.cuh)
 INTERP_PROCESSES = {"gg_ttxggg": (128, 16)}        # process -> (threads per event, amplitudes per stage)
 
@@ -38,8 +43,8 @@ def _apply_kernel_overrides():
         if parts[0] == "interp":
             INTERP_PROCESSES[proc] = (int(parts[1]), int(parts[2]))
         elif parts[0] == "tab":
-            TAB_PROCESSES[proc] = (int(parts[1]), int(parts[2]) if len(parts) > 2 else 1,
-                                   int(parts[3]) if len(parts) > 3 else 1)
+            dflt = (0, 1, 1, 0, 1, 0, 1, 6, 4)
+            TAB_PROCESSES[proc] = tuple(int(parts[i + 1]) if len(parts) > i + 1 else dflt[i] for i in range(9))
 
 
 _apply_kernel_overrides()
@@ -197,8 +202,7 @@ def emit_process(process: str) -> tuple[str, dict]:
 
     tab_src, TP, IP = ("", None, None)
     if process in TAB_PROCESSES:
-        nt_t, epc_f, epc_d = TAB_PROCESSES[process]
-        tab_src, TP = emit_tab_struct(process, nt_t, epc_f, epc_d, ncol, nlines, cbody)
+        tab_src, TP, tab_flops = emit_tab_struct(process, *TAB_PROCESSES[process], ncol, nlines, cbody)
     elif process in INTERP_PROCESSES:
         nt_i, sa = INTERP_PROCESSES[process]
         tab_src, IP = emit_interp_struct(process, nt_i, sa, num)
@@ -207,7 +211,7 @@ def emit_process(process: str) -> tuple[str, dict]:
     launch_fn = "launch_tab" if TP else ("launch_interp" if IP else "launch_scalar")
     nhel_all = 1 << npar
     if TP:
-        flops_hel = TP.amplitude_flops_per_helicity() + -(-TP.table_flops() // nhel_all)
+        flops_hel = TP.amplitude_flops_per_helicity() + -(-tab_flops // nhel_all)
     elif IP:
         flops_hel = IP.tab.amplitude_flops_per_helicity() + -(-IP.table_flops // nhel_all)
     else:
@@ -313,100 +317,178 @@ def _support_name(S):
 def _table_call(kind, k="k"):
     if kind == "VVV1P0_1":
         c = f"VVV1P0_1<T>(tab.ld({k}.in0), ln[{k}.la].p, tab.ld({k}.in1), ln[{k}.lb].p, ln[{k}.lo].inv, o);"
-    elif kind.endswith("P0_1"):
+    elif kind.startswith("VVVV") and kind.endswith("P0_1"):
         c = f"{kind}<T>(tab.ld({k}.in0), tab.ld({k}.in1), tab.ld({k}.in2), ln[{k}.lo].inv, o);"
     elif kind in ("FFV1_2", "FFV1_1"):
         c = f"{kind}<T>(tab.ld({k}.in0), tab.ld({k}.in1), ln[{k}.lo], mt, o);"
     elif kind == "FFV1P0_3":
         c = f"FFV1P0_3<T>(tab.ld({k}.in0), tab.ld({k}.in1), ln[{k}.lo].inv, o);"
+    elif kind in ("FFV1A_3", "FFV1A_2", "FFV1A_1"):
+        c = f"{kind}<T>(tab.ld({k}.in0), tab.ld({k}.in1), o);"
+    elif kind.startswith("VVV1A_"):
+        c = f"VVV1A<{kind[-1]}, T>(tab.ld({k}.in0), tab.ld({k}.in1), ln[{k}.la].p, ln[{k}.lb].p, o);"
+    elif kind in ("VVVV1A", "VVVV3A", "VVVV4A"):
+        c = f"{kind}<T>(tab.ld({k}.in0), tab.ld({k}.in1), tab.ld({k}.in2), o);"
     else:
         raise ValueError(kind)
     return f"Wf<T> o; {c} tab.st({k}.out, o);"
 
 
-def emit_tab_struct(process: str, nt: int, epc_f: int, epc_d: int, ncol: int, nlines: int, colour_body: list):
-    """ProcTab: task table, level-by-level table rounds, per-helicity amplitudes."""
-    TP = build_tabplan(process)
-    P = TP.plan
-    npar = P.npar
-    tasks = []
-    rounds_code = []
-    prev_level = None
-    for r in TP.rounds:
-        if prev_level is not None and r.level != prev_level:
-            rounds_code.append("__syncthreads();")
-        prev_level = r.level
-        start = len(tasks)
-        for t in r.tasks:
-            ins = list(t.ins) + [0] * (3 - len(t.ins))
-            la, lb, lo = (x if x >= 0 else 0 for x in t.lines)
-            tasks.append((t.out, ins[0], ins[1], ins[2], la, lb, lo))
-        n = len(r.tasks)
-        rounds_code.append(f"for (int t = tid; t < {n}; t += NT) {{ const TabTask k = ld_task(c_tasks + {start} + t); "
-                           f"{_table_call(r.kind)} }}  // level {r.level}: {r.kind}")
-    # amplitude code
-    used = set()
-    acode = []
-    for n_amp, (ai, terms) in enumerate(P.amps):
-        op = P.ops[ai]
-        args = []
-        for a in op.args:
-            S = TP.support[a]
-            used.add(S)
-            args.append(f"tab.ld({TP.base[a]} + {_support_name(S)})")
-        if op.kind == "FFV1_0":
-            call = f"FFV1_0<T>({args[0]}, {args[1]}, {args[2]})"
-        elif op.kind == "VVV1_0":
-            la, lb = op.mom
-            call = f"VVV1_0<T>({args[0]}, ln[{la}].p, {args[1]}, ln[{lb}].p, {args[2]})"
-        else:
-            call = f"{op.kind}<T>({args[0]}, {args[1]}, {args[2]}, {args[3]})"
-        acode.append(f"{{ const cx<T> x = {call};")
-        for col, c in terms:
-            acode.append(f"  jacc<{c[0]}, {c[1]}, T>(J[{col}], x);")
-        acode.append("}")
-        acode.append(f"ME_FENCE(T, {n_amp});")
+def _amp_call(P, ai, addr):
+    """code evaluating amplitude op ai; addr(x) -> table address expression of operand x"""
+    op = P.ops[ai]
+    args = [f"tab.ld({addr(a)})" for a in op.args]
+    if op.kind in ("FFV1_0", "DOTV", "DOTF"):
+        return f"{op.kind}<T>({', '.join(args)})"
+    if op.kind == "VVV1_0":
+        la, lb = op.mom
+        return f"VVV1_0<T>({args[0]}, ln[{la}].p, {args[1]}, ln[{lb}].p, {args[2]})"
+    return f"{op.kind}<T>({args[0]}, {args[1]}, {args[2]}, {args[3]})"
+
+
+def _amp_block(P, ai, terms, addr, n_amp):
+    out = [f"{{ const cx<T> x = {_amp_call(P, ai, addr)};"]
+    for col, c in terms:
+        out.append(f"  jacc<{c[0]}, {c[1]}, T>(J[{col}], x);")
+    out.append("}")
+    out.append(f"ME_FENCE(T, {n_amp});")
+    return out
+
+
+def _variant_code(npar, supports):
     bits = [f"const int b{p} = (h >> {npar - 1 - p}) & 1;" for p in range(npar)]
     sups = []
-    for S in sorted(used, key=lambda x: (len(x), x)):
+    for S in sorted(supports, key=lambda x: (len(x), x)):
         expr = " | ".join(f"(b{p} << {j})" if j else f"b{p}" for j, p in enumerate(S))
         sups.append(f"const int {_support_name(S)} = {expr};")
+    return bits + sups
+
+
+def emit_tab_struct(process: str, nt: int, epc_f: int, epc_d: int, pair: int, amputated: int, stage: int,
+                    fence_f: int, fence_p: int, fence_d: int, ncol: int, nlines: int, colour_body: list):
+    """ProcTab: task table, table rounds and per-helicity amplitudes.
+
+    stage == 0: one resident table (every object, all levels), then the
+    amplitudes of each helicity (`tables` + `amps`).  stage > 0: the staged
+    schedule of gen/interp.py as straight-line code (`staged`): per stage, the
+    table rounds of the objects that become live, then the stage's amplitudes,
+    slots reused after each object's last reader; one helicity per thread."""
+    tasks = []
+
+    def round_code(kind, tl, level_note):
+        start = len(tasks)
+        for out, ins, ln in tl:
+            ins = list(ins) + [0] * (3 - len(ins))
+            tasks.append((out, ins[0], ins[1], ins[2], *(max(x, 0) for x in ln)))
+        return (f"for (int t = tid; t < {len(tl)}; t += NT) {{ const TabTask k = ld_task(c_tasks + {start} + t); "
+                f"{_table_call(kind)} }}  // {level_note}{kind}")
+
+    if stage == 0:
+        TP = build_tabplan(process, bool(amputated))
+        P = TP.plan
+        npar = P.npar
+        size, table_flops = TP.size, TP.table_flops()
+        rounds_code, prev = [], None
+        for r in TP.rounds:
+            if prev is not None and r.level != prev:
+                rounds_code.append("__syncthreads();")
+            prev = r.level
+            rounds_code.append(round_code(r.kind, [(t.out, t.ins, t.lines) for t in r.tasks], f"level {r.level}: "))
+        addr = lambda a: f"{TP.base[a]} + {_support_name(TP.support[a])}"
+        acode = []
+        for n_amp, (ai, terms) in enumerate(P.amps):
+            acode += _amp_block(P, ai, terms, addr, n_amp)
+        used = {TP.support[a] for ai, _ in P.amps for a in P.ops[ai].args}
+        body = f"""
+    static constexpr bool STAGED = false;
+    template <class T>
+    __device__ static __forceinline__ void tables(const TabRef<T, TAB>& tab, const Ln<T>* __restrict__ ln, T mt, int tid)
+    {{
+        (void)mt;
+{NL.join("        " + x for x in rounds_code)}
+    }}
+
+    template <class T, class JT>
+    __device__ static __forceinline__ void amps(const TabRef<T, TAB>& tab, int h, const Ln<T>* __restrict__ ln, JT& J)
+    {{
+{NL.join("        " + x for x in _variant_code(npar, used))}
+{NL.join("        " + x for x in acode)}
+    }}"""
+    else:
+        I = build_interp(process, stage, bool(amputated))
+        TP = I.tab
+        P = TP.plan
+        npar = P.npar
+        if nt < (1 << npar):
+            raise ValueError("the staged table kernel takes every helicity in one pass: NT >= 2^npar")
+        size, table_flops = I.table_size, I.table_flops
+        ops = P.ops
+        is_obj = lambda x: ops[x].out != "A" and not ops[x].kind.startswith("ext_")
+        addr = lambda a: f"{I.slot[a] if is_obj(a) else 2 * ops[a].ext} + {_support_name(TP.support[a])}"
+        code, n_amp = [], 0
+        for si, st in enumerate(I.stages):
+            code.append(f"// stage {si}: {sum(len(t) for _, t in st.rounds)} table tasks, {len(st.amps)} amplitudes")
+            for ri, (kind, tl) in enumerate(st.rounds):
+                code.append(round_code(kind, tl, ""))
+                if ri in st.barriers:
+                    code.append("__syncthreads();")
+            code.append("__syncthreads();")
+            for ai in st.amps:
+                aop, terms = P.amps[ai]
+                code += _amp_block(P, aop, terms, addr, n_amp)
+                n_amp += 1
+            code.append("__syncthreads();  // the stage's dead slots are reused by the next one")
+        used = {TP.support[a] for ai, _ in P.amps for a in ops[ai].args}
+        body = f"""
+    static constexpr bool STAGED = true;
+    // every stage in order; all threads of the CTA call it (CTA barriers inside)
+    template <class T, class JT>
+    __device__ static __forceinline__ void staged(const TabRef<T, TAB>& tab, const Ln<T>* __restrict__ ln, T mt, int tid,
+                                                  int h, JT& J)
+    {{
+        (void)mt;
+{NL.join("        " + x for x in _variant_code(npar, used))}
+{NL.join("        " + x for x in code)}
+    }}"""
+
     task_init = ",\n    ".join("{%d, %d, %d, %d, %d, %d, %d, 0, 0}" % t for t in tasks)
-    nl = "\n"
-    return f"""
+    # event-pair kernel: CTAs per SM that its shared memory admits (momenta,
+    # packed line data of 40 bytes, packed table entries of 64 bytes; 1 KB
+    # reserved per CTA), but never a register budget below ~232 per thread
+    # (the packed colour-flow vector alone takes 4 * NCOL registers)
+    pair_bytes = ((2 * npar * 32 + nlines * 40 + 15) // 16 * 16 + size * 64) * epc_f
+    min_ctas_p = max(1, min(16, (228 * 1024) // (pair_bytes + 1024), 65536 // (nt * epc_f * 232)))
+    desc = (f"{'staged (' + str(stage) + ' amplitudes per stage)' if stage else 'resident'}"
+            f"{', amputated vertex objects' if amputated else ''}")
+    src = f"""
 __device__ const TabTask c_tasks[{max(len(tasks), 1)}] = {{
     {task_init if tasks else "{0, 0, 0, 0, 0, 0, 0, 0, 0}"}
 }};
 
-// helicity-recycled evaluation: {TP.size} table entries, {len(tasks)} table tasks,
-// {TP.table_flops()} table flops per event, {TP.amplitude_flops_per_helicity()} amplitude flops per helicity
+// helicity-recycled evaluation, {desc}: {size} table entries, {len(tasks)} table tasks,
+// {table_flops} table flops per event, {TP.amplitude_flops_per_helicity()} amplitude flops per helicity
 struct ProcTab : Proc {{
-    static constexpr int NT = {nt}, TAB = {TP.size};
+    static constexpr int NT = {nt}, TAB = {size};
     // events per CTA (own shared-memory region each; CTA barriers keep their
     // warps at the same point of the code), in FP32 / mixed and in FP64
     static constexpr int EPC_F = {epc_f}, EPC_D = {epc_d};
     // register budget: FP32 <= 128 per thread (occupancy bound by shared memory
     // anyway), FP64 <= 255 (its tables are twice as large)
     static constexpr int MIN_CTAS_F = {max(1, 65536 // (nt * epc_f * 128))}, MIN_CTAS_D = {max(1, 65536 // (nt * epc_d * 255))};
+    // FP32 / mixed as packed FP32x2 event pairs (me_kernel_pair), EPC_F pairs per CTA
+    static constexpr bool PAIR_F = {"true" if pair else "false"};
+    static constexpr int PPC = {epc_f}, MIN_CTAS_P = {min_ctas_p};
     static constexpr bool IS_TAB = true, IS_INTERP = false;
-    static constexpr long long TABLE_FLOPS = {TP.table_flops()}LL, AMP_FLOPS = {TP.amplitude_flops_per_helicity()}LL;
-
-    template <class T>
-    __device__ static __forceinline__ void tables(const TabRef<T, TAB>& tab, const Ln<T>* __restrict__ ln, T mt, int tid)
-    {{
-        (void)mt;
-{nl.join("        " + x for x in rounds_code)}
-    }}
-
-    template <class T, class JT>
-    __device__ static __forceinline__ void amps(const TabRef<T, TAB>& tab, int h, const Ln<T>* __restrict__ ln, JT& J)
-    {{
-{nl.join("        " + x for x in bits)}
-{nl.join("        " + x for x in sups)}
-{nl.join("        " + x for x in acode)}
-    }}
+    static constexpr long long TABLE_FLOPS = {table_flops}LL, AMP_FLOPS = {TP.amplitude_flops_per_helicity()}LL;
+    // warp fence every n amplitudes (FP32, packed FP32x2, FP64)
+    static constexpr int FENCE_F = {fence_f}, FENCE_P = {fence_p}, FENCE_D = {fence_d};
+{body}
 }};
-""", TP
+"""
+    return src, TP, table_flops
+
+
+NL = "\n"
 
 
 def emit_interp_struct(process: str, nt: int, stage_amps: int, num):

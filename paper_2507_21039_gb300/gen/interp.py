@@ -72,8 +72,8 @@ class _Arena:
         self.free = merged
 
 
-def build_interp(process: str, stage_amps: int = 48) -> InterpPlan:
-    T = build_tabplan(process)
+def build_interp(process: str, stage_amps: int = 48, amputated: bool = False) -> InterpPlan:
+    T = build_tabplan(process, amputated)
     P = T.plan
     ops = P.ops
     is_obj = lambda i: ops[i].out != "A" and not ops[i].kind.startswith("ext_")
@@ -155,7 +155,8 @@ def build_interp(process: str, stage_amps: int = 48) -> InterpPlan:
                     for a in op.args:
                         base = slot[a] if is_obj(a) else 2 * ops[a].ext
                         ins.append(base + compress(bits, T.support[a]))
-                    ln = (op.mom[0], op.mom[1], op.line) if kind == "VVV1P0_1" else (0, 0, op.line)
+                    vvv = kind == "VVV1P0_1" or kind.startswith("VVV1A")
+                    ln = (op.mom[0], op.mom[1], max(op.line, 0)) if vvv else (0, 0, max(op.line, 0))
                     tasks.append((slot[o] + v, tuple(ins), ln))
             st.rounds.append((kind, tasks))
         for o in list(slot):

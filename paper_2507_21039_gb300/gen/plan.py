@@ -39,6 +39,11 @@ FLOPS = {
     "FFV1_0": 72,
     "VVV1_0": 90,
     "VVVV1_0": 70, "VVVV3_0": 70, "VVVV4_0": 70,
+    # amputated vertices (no propagator) and two-operand contractions, see amputate()
+    "FFV1A_3": 64, "FFV1A_2": 64, "FFV1A_1": 64,
+    "VVV1A_1": 116, "VVV1A_2": 116, "VVV1A_3": 116,
+    "VVVV1A": 78, "VVVV3A": 78, "VVVV4A": 78,
+    "DOTV": 30, "DOTF": 30,
 }
 V4NAMES = ("VVVV1", "VVVV3", "VVVV4")
 
@@ -228,3 +233,71 @@ def _plan_ee() -> Plan:
     P.amps = [(5, ((0, (0, 1)),))]
     P.ndiagrams = 1
     return P
+
+
+# ---------------------------------------------------------------------------
+# amputated form: every amplitude as a two-operand contraction
+# ---------------------------------------------------------------------------
+# A final vertex is a multilinear form of its operands.  Leaving one operand's
+# index open gives an "amputated" vertex object (no propagator) whose
+# contraction with that operand is the amplitude:
+#   FFV1_0(Fo, V, Fi) = K.V        K^mu = Fo gamma^mu Fi         (FFV1A_3, DOTV)
+#                     = R Fi       R    = Fo gamma.V  (row)      (FFV1A_2, DOTF)
+#                     = Fo C       C    = gamma.V Fi  (column)   (FFV1A_1, DOTF)
+#   VVV1_0(A, B, Q)   = W.Q, W.A, W.B with the open leg Q, A, B  (VVV1A_3/1/2, DOTV)
+#   VVVVn_0(A,B,C,Q)  = W.Q        W = VVVVnP0_1(A, B, C) without propagator
+# The vertex objects depend on the helicities of their operands only, so the
+# table kernel evaluates them once per configuration of that support; per
+# helicity only the contraction (30 flops) remains.  Products and sums are the
+# same as in the direct vertex, grouped differently.
+_SPLITS = {
+    # kind -> [(open operand position, vertex kind, vertex operand positions, out)]
+    "FFV1_0": [(1, "FFV1A_3", (0, 2), "V"), (2, "FFV1A_2", (0, 1), "Fo"), (0, "FFV1A_1", (1, 2), "Fi")],
+    "VVV1_0": [(2, "VVV1A_3", (0, 1), "V"), (0, "VVV1A_1", (1, 2), "V"), (1, "VVV1A_2", (0, 2), "V")],
+    "VVVV1_0": [(3, "VVVV1A", (0, 1, 2), "V")],
+    "VVVV3_0": [(3, "VVVV3A", (0, 1, 2), "V")],
+    "VVVV4_0": [(3, "VVVV4A", (0, 1, 2), "V")],
+}
+
+
+def amputate(P: Plan, support: dict) -> Plan:
+    """Rewrite every amplitude of P as a contraction of an amputated vertex
+    object with the remaining operand.  `support` maps op index -> tuple of
+    external particles.  For each amplitude the split that adds the fewest new
+    table variants (2^|support| of a vertex not yet created) is taken; vertex
+    objects are shared between amplitudes."""
+    Q = Plan(P.process, P.npar, P.gluon_ext, P.gluon_incoming, P.ncol, [], list(P.lines), [], P.ndiagrams)
+    # keep every object of P (the direct amplitude ops go), indices renumbered
+    new = {}
+    for i, op in enumerate(P.ops):
+        if op.out != "A":
+            new[i] = len(Q.ops)
+            Q.ops.append(Op(op.kind, tuple(new[a] for a in op.args), op.line, op.mom, op.ext, op.out))
+    sup_of = {new[i]: support[i] for i in new}
+    made = {}
+    for ai, terms in P.amps:
+        op = P.ops[ai]
+        best = None
+        for open_pos, vkind, vpos, out in _SPLITS[op.kind]:
+            vargs = tuple(new[op.args[i]] for i in vpos)
+            key = (vkind, vargs, op.mom)
+            sup = set()
+            for a in vargs:
+                sup |= set(sup_of[a])
+            cost = 0 if key in made else (1 << len(sup)) * FLOPS[vkind]
+            cand = (cost, len(sup), key, open_pos, out)
+            if best is None or cand[:2] < best[:2]:
+                best = cand
+        _, _, key, open_pos, out = best
+        if key not in made:
+            vkind, vargs, mom = key
+            Q.ops.append(Op(vkind, vargs, -1, mom if vkind.startswith("VVV1A") else (), out=out))
+            made[key] = len(Q.ops) - 1
+        x = made[key]
+        other = new[op.args[open_pos]]
+        dk = "DOTF" if out in ("Fo", "Fi") else "DOTV"
+        # DOTF takes (row, column)
+        args = (x, other) if out == "Fo" else ((other, x) if out == "Fi" else (x, other))
+        Q.ops.append(Op(dk, args, -1, out="A"))
+        Q.amps.append((len(Q.ops) - 1, terms))
+    return Q

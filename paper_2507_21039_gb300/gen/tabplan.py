@@ -22,7 +22,7 @@ from __future__ import annotations
 
 from dataclasses import dataclass, field
 
-from .plan import FLOPS, Plan, build_plan
+from .plan import FLOPS, Plan, amputate, build_plan
 
 
 @dataclass
@@ -81,10 +81,16 @@ def compress(full_bits: dict, support) -> int:
     return sum(full_bits[p] << j for j, p in enumerate(support))
 
 
-def build_tabplan(process: str) -> TabPlan:
+def build_tabplan(process: str, amputated: bool = False) -> TabPlan:
+    """amputated: every amplitude becomes a contraction of two table objects
+    (plan.amputate), the vertex objects joining the table."""
     P = build_plan(process)
     memo = {}
     sup = {i: _support(P, i, memo) for i in range(len(P.ops))}
+    if amputated:
+        P = amputate(P, sup)
+        memo = {}
+        sup = {i: _support(P, i, memo) for i in range(len(P.ops))}
     base = {}
     for i, op in enumerate(P.ops):
         if op.kind.startswith("ext_"):
@@ -109,7 +115,7 @@ def build_tabplan(process: str) -> TabPlan:
         for v in range(1 << len(S)):
             bits = {p: (v >> j) & 1 for j, p in enumerate(S)}
             ins = tuple(base[a] + compress(bits, sup[a]) for a in op.args)
-            if op.kind == "VVV1P0_1":
+            if op.kind == "VVV1P0_1" or op.kind.startswith("VVV1A"):
                 ln = (op.mom[0], op.mom[1], op.line)
             else:
                 ln = (-1, -1, op.line)

@@ -15,6 +15,7 @@ for _mu in range(4):
     _g[2:, :2] = _s[_mu] if _mu == 0 else -_s[_mu]
     G.append(_g)
 METRIC = np.array([1.0, -1.0, -1.0, -1.0])
+AMPUTATED_VERTICES = ("FFV1A_3", "FFV1A_2", "FFV1A_1", "VVV1A_1", "VVV1A_2", "VVV1A_3", "VVVV1A", "VVVV3A", "VVVV4A")
 
 
 def dot(a, b):
@@ -23,6 +24,41 @@ def dot(a, b):
 
 def slash(v):
     return G[0] * v[0] - G[1] * v[1] - G[2] * v[2] - G[3] * v[3]
+
+
+def _vvv_open(kind, a, PA, PB):
+    """three-gluon vertex V^{mnr}(k1, k2, k3) A_m B_n Q_r, k1 = -PA, k2 = -PB,
+    k3 = PA + PB, with one leg left open (upper index).  kind VVV1A_3: open Q,
+    inputs (A, B); VVV1A_1: open A, inputs (B, Q); VVV1A_2: open B, inputs (A, Q)."""
+    k1, k2, k3 = -PA, -PB, PA + PB
+    d12, d23, d31 = k1 - k2, k2 - k3, k3 - k1
+    if kind == "VVV1A_3":
+        A, B = a
+        return dot(A, B) * d12 + B * dot(d23, A) + A * dot(d31, B)
+    if kind == "VVV1A_1":
+        B, Q = a
+        return B * dot(d12, Q) + dot(B, Q) * d23 + Q * dot(d31, B)
+    A, Q = a
+    return A * dot(d12, Q) + Q * dot(d23, A) + dot(Q, A) * d31
+
+
+def _amputated(kind, a, lines, op_mom):
+    """amputated vertices (no propagator) and the two-operand contractions"""
+    if kind == "FFV1A_3":
+        return np.array([a[0] @ G[mu] @ a[1] for mu in range(4)])
+    if kind == "FFV1A_2":
+        return a[0] @ slash(a[1])
+    if kind == "FFV1A_1":
+        return slash(a[0]) @ a[1]
+    if kind.startswith("VVV1A"):
+        return _vvv_open(kind, a, lines[op_mom[0]][0], lines[op_mom[1]][0])
+    if kind.startswith("VVVV") and kind.endswith("A"):
+        return _v4(kind[:5], a[0], a[1], a[2])
+    if kind == "DOTV":
+        return dot(a[0], a[1])
+    if kind == "DOTF":
+        return a[0] @ a[1]
+    return None
 
 
 def evaluate(orc, plan, p, h, mt):
@@ -99,7 +135,10 @@ def evaluate(orc, plan, p, h, mt):
             A, B, C, Q = a
             vals.append(dot(_v4(k[:5], A, B, C), Q))
         else:
-            raise ValueError(k)
+            v = _amputated(k, a, lines, op.mom)
+            if v is None:
+                raise ValueError(k)
+            vals.append(v)
     J = np.zeros(plan.ncol, dtype=complex)
     for ai, terms in plan.amps:
         for col, c in terms:
@@ -160,6 +199,8 @@ def evaluate_staged(orc, I, p, h, mt):
                     k1, k2, k3 = -PA, -PB, PA + PB
                     v = dot(a[0], a[1]) * (k1 - k2) + a[1] * dot(k2 - k3, a[0]) + a[0] * dot(k3 - k1, a[1])
                     table[out] = lines[ln[2]][1] * v
+                elif kind in AMPUTATED_VERTICES:
+                    table[out] = _amputated(kind, a, lines, (ln[0], ln[1]))
                 elif kind.startswith("VVVV"):
                     table[out] = lines[ln[2]][1] * _v4(kind[:5], a[0], a[1], a[2])
                 elif kind == "FFV1_2":
@@ -178,7 +219,9 @@ def evaluate_staged(orc, I, p, h, mt):
             for x in op.args:
                 base = I.slot[x] if (ops[x].out != "A" and not ops[x].kind.startswith("ext_")) else 2 * ops[x].ext
                 w.append(table[base + var(T.support[x])])
-            if op.kind == "FFV1_0":
+            if op.kind in ("DOTV", "DOTF"):
+                x = _amputated(op.kind, w, lines, op.mom)
+            elif op.kind == "FFV1_0":
                 x = w[0] @ slash(w[1]) @ w[2]
             elif op.kind == "VVV1_0":
                 PA, PB = lines[op.mom[0]][0], lines[op.mom[1]][0]

@@ -109,16 +109,24 @@ def test_expected_helicity_counts(orc):
 
 @pytest.mark.parametrize("name", ["gg_ttx", "gg_ttxg", "gg_ttxgg", "gg_ttxggg"])
 def test_gauge_invariance_on_gpu(orc, name):
-    """Ward identity: a gluon polarisation replaced by its momentum gives zero."""
+    """Ward identity: a gluon polarisation replaced by its momentum gives zero.
+
+    In floating point the residual amplitude is rounding of diagrams that each
+    scale with the gluon energy E_g (the momentum replaces a unit polarisation),
+    so |M_k|^2 / (|M|^2 E_g^2) is bounded by (C u)^2, u the unit roundoff and C
+    the cancellation between diagrams; C = 1000 is used.  A wrong vertex or
+    sign gives a ratio of order one."""
     mom = oracle_events(orc, name, 33)
     d = torch.from_numpy(mom).cuda()
-    for prec, tol in (("fp64", 1e-18), ("fp32", 1e-6)):
+    for prec, u in (("fp64", 2.0 ** -53), ("fp32", 2.0 ** -24)):
+        tol = (1000 * u) ** 2
         h = me.workload_handle(name, prec)
         base = me.me_sigmakin(h, d).cpu().numpy()
         for g in [0, 1] + list(range(4, WORKLOADS[name].npar)):
             me.me_set_option(h, me.ME_OPT_GAUGE_CHECK, g)
             z = me.me_sigmakin(h, d).cpu().numpy()
-            assert np.abs(z / base).max() < tol, (prec, g, np.abs(z / base).max())
+            ratio = np.abs(z / base) / mom[:, g, 0] ** 2
+            assert ratio.max() < tol, (prec, g, ratio.max(), tol)
         me.me_set_option(h, me.ME_OPT_GAUGE_CHECK, -1)
         again = me.me_sigmakin(h, d).cpu().numpy()
         assert np.array_equal(again, base)

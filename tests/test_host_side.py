@@ -66,6 +66,30 @@ def test_generator_plan_reproduces_oracle_partial_amplitudes(orc, process):
             assert np.abs(J - A).max() < 1e-12 * scale
 
 
+@pytest.mark.parametrize("process", ["gg_ttx", "gg_ttxg", "gg_ttxgg", "gg_ttxggg"])
+def test_amputated_plan_reproduces_oracle_partial_amplitudes(orc, process):
+    """Every amplitude rewritten as the contraction of an amputated vertex
+    object (no propagator) with the remaining operand gives the oracle's
+    colour-ordered partial amplitudes."""
+    from paper_2507_21039_gb300.gen.plan import amputate
+    from paper_2507_21039_gb300.gen.tabplan import _support
+
+    P = build_plan(process)
+    memo = {}
+    Q = amputate(P, {i: _support(P, i, memo) for i in range(len(P.ops))})
+    assert len(Q.amps) == len(P.amps)
+    assert all(Q.ops[a].kind in ("DOTV", "DOTF") for a, _ in Q.amps)
+    w = WORKLOADS[process]
+    mom, _, _ = orc.rambo(w.seed, w.sqrt_s, w.masses_final, 4, 1, w.cut_mask, 20.0, 0.4)
+    p = mom[0]
+    scale = max(np.abs(orc.partial_amps(process, p, h)).max() for h in range(0, 1 << P.npar, 7))
+    rng = np.random.default_rng(11)
+    for h in rng.integers(0, 1 << P.npar, size=3 if process != "gg_ttxggg" else 1):
+        J = evaluate(orc, Q, p, int(h), MT)
+        A = orc.partial_amps(process, p, int(h))
+        assert np.abs(J - A).max() < 1e-12 * scale
+
+
 def test_generator_flop_counts_positive():
     for p in ("ee_mumu", "gg_ttx", "gg_ttxg", "gg_ttxgg", "gg_ttxggg"):
         P = build_plan(p)
@@ -141,14 +165,16 @@ def test_abi_validation_without_device(lib):
     lib.me_free(None)
 
 
-@pytest.mark.parametrize("process,stage", [("gg_ttxgg", 16), ("gg_ttxggg", 16)])
-def test_staged_schedule_reproduces_oracle(orc, process, stage):
-    """The staged schedule for the descriptor kernel (slot reuse after each
-    object's last reader, variant indexing) gives the oracle's partial amplitudes."""
+@pytest.mark.parametrize("process,stage,amputated", [("gg_ttxgg", 16, False), ("gg_ttxggg", 16, False),
+                                                     ("gg_ttxg", 4, True), ("gg_ttxgg", 16, True)])
+def test_staged_schedule_reproduces_oracle(orc, process, stage, amputated):
+    """The staged schedules (slot reuse after each object's last reader,
+    variant indexing; with or without amputated vertex objects) give the
+    oracle's partial amplitudes."""
     from paper_2507_21039_gb300.gen.interp import build_interp
     from plan_eval import evaluate_staged
 
-    I = build_interp(process, stage)
+    I = build_interp(process, stage, amputated)
     w = WORKLOADS[process]
     mom, _, _ = orc.rambo(w.seed, w.sqrt_s, w.masses_final, 3, 1, w.cut_mask, 20.0, 0.4)
     p = mom[0]
