@@ -80,11 +80,11 @@ __global__ void __launch_bounds__(P::NT) me_kernel_interp(LaunchArgs a, cx<T>* _
     const bool act = tid < a.nlist;
     const int h = a.hel_list[act ? tid : 0];
     // compressed variant index of every operand support for this helicity
-    // (support particles in ascending order = helicity bits from high to low)
+    // (support particles in descending order = helicity bits from low to high)
     for (int s = 0; s < P::NSUP; ++s) {
         const unsigned m = P::support_mask(s);
         unsigned v = 0, j = 0;
-        for (int b = NPAR - 1; b >= 0; --b)
+        for (int b = 0; b < NPAR; ++b)
             if ((m >> b) & 1) v |= ((h >> b) & 1) << j++;
         vsup[s * NT + tid] = (unsigned char)v;
     }

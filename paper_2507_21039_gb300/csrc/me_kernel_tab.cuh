@@ -83,6 +83,10 @@ __device__ __forceinline__ TabTask ld_task(const TabTask* p)
 // Tables are stored as planes of 16-byte chunks: chunk c of entry i lives at
 // c * TAB + i.  Lanes that read consecutive variants then touch consecutive
 // banks (a plain array of 32- or 64-byte entries makes 2- or 4-way conflicts).
+// A 16-byte load of a warp is served in phases of 8 lanes, which differ in the
+// three lowest helicity bits; the generator numbers an object's variants with
+// the highest-numbered support particle (lowest helicity bit) first, so those
+// lanes read at most 8 consecutive entries.
 template <class T> struct Chunks { static constexpr int N = (int)(sizeof(Wf<T>) / 16); };
 
 template <class T, int TAB> struct TabRef {

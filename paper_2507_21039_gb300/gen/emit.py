@@ -456,7 +456,7 @@ def emit_tab_struct(process: str, nt: int, epc_f: int, epc_d: int, pair: int, am
     # packed line data of 40 bytes, packed table entries of 64 bytes; 1 KB
     # reserved per CTA), but never a register budget below ~232 per thread
     # (the packed colour-flow vector alone takes 4 * NCOL registers)
-    pair_bytes = ((2 * npar * 32 + nlines * 40 + 15) // 16 * 16 + size * 64) * epc_f
+    pair_bytes = ((2 * npar * 32 + nlines * 40 + 15) // 16 * 16 + (size + 7) // 8 * 8 * 64) * epc_f
     min_ctas_p = max(1, min(16, (228 * 1024) // (pair_bytes + 1024), 65536 // (nt * epc_f * 232)))
     desc = (f"{'staged (' + str(stage) + ' amplitudes per stage)' if stage else 'resident'}"
             f"{', amputated vertex objects' if amputated else ''}")
@@ -468,7 +468,7 @@ __device__ const TabTask c_tasks[{max(len(tasks), 1)}] = {{
 // helicity-recycled evaluation, {desc}: {size} table entries, {len(tasks)} table tasks,
 // {table_flops} table flops per event, {TP.amplitude_flops_per_helicity()} amplitude flops per helicity
 struct ProcTab : Proc {{
-    static constexpr int NT = {nt}, TAB = {size};
+    static constexpr int NT = {nt}, TAB = {(size + 7) // 8 * 8};
     // events per CTA (own shared-memory region each; CTA barriers keep their
     // warps at the same point of the code), in FP32 / mixed and in FP64
     static constexpr int EPC_F = {epc_f}, EPC_D = {epc_d};
@@ -553,7 +553,7 @@ def emit_interp_struct(process: str, nt: int, stage_amps: int, num):
 // staged evaluation: {len(I.stages)} stages of <= {stage_amps} amplitudes, table peak {I.table_size} entries,
 // {len(tasks)} table tasks ({I.table_flops} flops per event), {len(terms)} colour terms
 struct ProcInterp : Proc {{
-    static constexpr int NT = {nt}, TAB = {I.table_size}, NSUP = {len(I.supports)}, NSTAGE = {len(I.stages)};
+    static constexpr int NT = {nt}, TAB = {(I.table_size + 7) // 8 * 8}, NSUP = {len(I.supports)}, NSTAGE = {len(I.stages)};
     static constexpr bool IS_TAB = false, IS_INTERP = true;
     static constexpr long long TABLE_FLOPS = {I.table_flops}LL, AMP_FLOPS = {T.amplitude_flops_per_helicity()}LL;
     __device__ static __forceinline__ const TabTask* tasks() {{ return c_itasks; }}

@@ -15,7 +15,11 @@ Table layout (units of one wavefunction, Wf = 4 complex numbers):
   [0, 2*npar)           external wavefunctions: particle e, helicity bit b at 2e+b
   then, per object X    2^|S_X| consecutive variants; variant index
                         v = sum_j b(p_j) << j over the support particles
-                        p_0 < p_1 < ... (b = 1 for helicity +1).
+                        p_0 > p_1 > ... (b = 1 for helicity +1): the
+                        highest-numbered particle -- the lowest helicity bit,
+                        which differs between neighbouring lanes -- is the
+                        lowest variant bit, so the lanes of one 8-lane
+                        shared-memory phase read nearby entries.
 Helicity index h: particle i has helicity +1 iff bit (npar-1-i) of h is set.
 """
 from __future__ import annotations
@@ -71,7 +75,7 @@ def _support(P: Plan, i: int, memo: dict):
         acc = set()
         for a in op.args:
             acc |= set(_support(P, a, memo))
-        s = tuple(sorted(acc))
+        s = tuple(sorted(acc, reverse=True))
     memo[i] = s
     return s
 
