@@ -30,8 +30,12 @@ struct __align__(16) IAmp {
     unsigned char kind, la, lb, nterm;
 };
 
-enum IRoutine : unsigned char { R_VVV1P0_1 = 0, R_VVVV1P0_1, R_VVVV3P0_1, R_VVVV4P0_1, R_FFV1_2, R_FFV1_1, R_FFV1P0_3 };
-enum IAmpKind : unsigned char { A_FFV1_0 = 0, A_VVV1_0, A_VVVV1_0, A_VVVV3_0, A_VVVV4_0 };
+// codes in the generator's order (gen/interp.py ROUTINES, AMP_KINDS)
+enum IRoutine : unsigned char {
+    R_VVV1P0_1 = 0, R_VVVV1P0_1, R_VVVV3P0_1, R_VVVV4P0_1, R_FFV1_2, R_FFV1_1, R_FFV1P0_3,
+    R_FFV1A_3, R_FFV1A_2, R_FFV1A_1, R_VVV1A_1, R_VVV1A_2, R_VVV1A_3, R_VVVV1A, R_VVVV3A, R_VVVV4A
+};
+enum IAmpKind : unsigned char { A_FFV1_0 = 0, A_VVV1_0, A_VVVV1_0, A_VVVV3_0, A_VVVV4_0, A_DOTV, A_DOTF };
 
 template <class P, class T> struct InterpLayout {
     static constexpr size_t mom = 0;
@@ -55,7 +59,16 @@ __device__ __forceinline__ void run_task(const TabRef<T, TAB>& tab, const Ln<T>*
     case R_VVVV4P0_1: VVVV4P0_1<T>(tab.ld(k.in0), tab.ld(k.in1), tab.ld(k.in2), ln[k.lo].inv, o); break;
     case R_FFV1_2: FFV1_2<T>(tab.ld(k.in0), tab.ld(k.in1), ln[k.lo], mt, o); break;
     case R_FFV1_1: FFV1_1<T>(tab.ld(k.in0), tab.ld(k.in1), ln[k.lo], mt, o); break;
-    default: FFV1P0_3<T>(tab.ld(k.in0), tab.ld(k.in1), ln[k.lo].inv, o); break;
+    case R_FFV1P0_3: FFV1P0_3<T>(tab.ld(k.in0), tab.ld(k.in1), ln[k.lo].inv, o); break;
+    case R_FFV1A_3: FFV1A_3<T>(tab.ld(k.in0), tab.ld(k.in1), o); break;
+    case R_FFV1A_2: FFV1A_2<T>(tab.ld(k.in0), tab.ld(k.in1), o); break;
+    case R_FFV1A_1: FFV1A_1<T>(tab.ld(k.in0), tab.ld(k.in1), o); break;
+    case R_VVV1A_1: VVV1A<1, T>(tab.ld(k.in0), tab.ld(k.in1), ln[k.la].p, ln[k.lb].p, o); break;
+    case R_VVV1A_2: VVV1A<2, T>(tab.ld(k.in0), tab.ld(k.in1), ln[k.la].p, ln[k.lb].p, o); break;
+    case R_VVV1A_3: VVV1A<3, T>(tab.ld(k.in0), tab.ld(k.in1), ln[k.la].p, ln[k.lb].p, o); break;
+    case R_VVVV1A: VVVV1A<T>(tab.ld(k.in0), tab.ld(k.in1), tab.ld(k.in2), o); break;
+    case R_VVVV3A: VVVV3A<T>(tab.ld(k.in0), tab.ld(k.in1), tab.ld(k.in2), o); break;
+    default: VVVV4A<T>(tab.ld(k.in0), tab.ld(k.in1), tab.ld(k.in2), o); break;
     }
     tab.st(k.out, o);
 }
@@ -113,16 +126,22 @@ __global__ void __launch_bounds__(P::NT) me_kernel_interp(LaunchArgs a, cx<T>* _
                 const IAmp d = P::amp(ai);
                 const Wf<T> w0 = tab.ld(d.op[0] + vsup[d.sup[0] * NT + tid]);
                 const Wf<T> w1 = tab.ld(d.op[1] + vsup[d.sup[1] * NT + tid]);
-                const Wf<T> w2 = tab.ld(d.op[2] + vsup[d.sup[2] * NT + tid]);
                 cx<T> x;
-                switch (d.kind) {
-                case A_FFV1_0: x = FFV1_0<T>(w0, w1, w2); break;
-                case A_VVV1_0: x = VVV1_0<T>(w0, sln[d.la].p, w1, sln[d.lb].p, w2); break;
-                default: {
-                    const Wf<T> w3 = tab.ld(d.op[3] + vsup[d.sup[3] * NT + tid]);
-                    x = d.kind == A_VVVV1_0 ? VVVV1_0<T>(w0, w1, w2, w3)
-                      : d.kind == A_VVVV3_0 ? VVVV3_0<T>(w0, w1, w2, w3) : VVVV4_0<T>(w0, w1, w2, w3);
-                }
+                if (d.kind == A_DOTV) {         // amputated: two-operand contractions
+                    x = DOTV<T>(w0, w1);
+                } else if (d.kind == A_DOTF) {
+                    x = DOTF<T>(w0, w1);
+                } else {
+                    const Wf<T> w2 = tab.ld(d.op[2] + vsup[d.sup[2] * NT + tid]);
+                    switch (d.kind) {
+                    case A_FFV1_0: x = FFV1_0<T>(w0, w1, w2); break;
+                    case A_VVV1_0: x = VVV1_0<T>(w0, sln[d.la].p, w1, sln[d.lb].p, w2); break;
+                    default: {
+                        const Wf<T> w3 = tab.ld(d.op[3] + vsup[d.sup[3] * NT + tid]);
+                        x = d.kind == A_VVVV1_0 ? VVVV1_0<T>(w0, w1, w2, w3)
+                          : d.kind == A_VVVV3_0 ? VVVV3_0<T>(w0, w1, w2, w3) : VVVV4_0<T>(w0, w1, w2, w3);
+                    }
+                    }
                 }
                 // every colour coefficient is +-i: J_c += +-i x
                 for (int k = 0; k < d.nterm; ++k, ++term) {

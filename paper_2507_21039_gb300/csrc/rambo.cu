@@ -58,25 +58,26 @@ struct Params {
     unsigned long long* nfail;
 };
 
-__device__ double eta_of(const double* p)
-{
-    const double P = sqrt(p[1] * p[1] + p[2] * p[2] + p[3] * p[3]);
-    return 0.5 * log((P + p[3]) / (P - p[3]));
-}
-
+// generation cuts on the final particles selected by cutmask: pT > ptmin for
+// each, Delta R = sqrt(Delta eta^2 + Delta phi^2) > drmin for each pair.  The
+// pseudorapidity and azimuth of each particle are computed once.
 __device__ bool passes(const double (*k)[4], int n, const Params& a)
 {
     if (!a.cutmask) return true;
+    double eta[kMaxFinal], phi[kMaxFinal];
     for (int i = 0; i < n; ++i) {
         if (!((a.cutmask >> i) & 1)) continue;
         if (!(sqrt(k[i][1] * k[i][1] + k[i][2] * k[i][2]) > a.ptmin)) return false;
+        const double P = sqrt(k[i][1] * k[i][1] + k[i][2] * k[i][2] + k[i][3] * k[i][3]);
+        eta[i] = 0.5 * log((P + k[i][3]) / (P - k[i][3]));
+        phi[i] = atan2(k[i][2], k[i][1]);
     }
     for (int i = 0; i < n; ++i) {
         if (!((a.cutmask >> i) & 1)) continue;
         for (int j = i + 1; j < n; ++j) {
             if (!((a.cutmask >> j) & 1)) continue;
-            const double de = eta_of(k[i]) - eta_of(k[j]);
-            double dphi = atan2(k[i][2], k[i][1]) - atan2(k[j][2], k[j][1]);
+            const double de = eta[i] - eta[j];
+            double dphi = phi[i] - phi[j];
             while (dphi > M_PI) dphi -= 2.0 * M_PI;
             while (dphi < -M_PI) dphi += 2.0 * M_PI;
             if (!(sqrt(de * de + dphi * dphi) > a.drmin)) return false;
@@ -97,9 +98,11 @@ __device__ bool rambo_point(const Params& a, long long ev, int attempt, double (
         const double s = sqrt(1.0 - c * c);
         const double f = 2.0 * M_PI * u01(r.x[1]);
         const double q0 = -log(u01(r.x[2]) * u01(r.x[3]));
+        double sf, cf;
+        sincos(f, &sf, &cf);
         q[j][0] = q0;
-        q[j][1] = q0 * s * cos(f);
-        q[j][2] = q0 * s * sin(f);
+        q[j][1] = q0 * s * cf;
+        q[j][2] = q0 * s * sf;
         q[j][3] = q0 * c;
         Q0 += q[j][0];
         Q1 += q[j][1];

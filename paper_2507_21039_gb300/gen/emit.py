@@ -26,7 +26,11 @@ EXT_KINDS = {"VIN": 0, "VOUT": 1, "FO_U": 2, "FO_V": 3, "FI_U": 4, "FI_V": 5}
 # (measured on GB300 over stage sizes, events per CTA and fence intervals)
 TAB_PROCESSES = {"gg_ttxg": (32, 1, 1, 0, 1, 0, 1, 6, 4), "gg_ttxgg": (64, 2, 2, 0, 1, 64, 4, 6, 4)}
 # processes evaluated with the staged descriptor kernel (me_kernel_interp.cuh)
-INTERP_PROCESSES = {"gg_ttxggg": (128, 16)}        # process -> (threads per event, amplitudes per stage)
+# process -> (threads per event, amplitudes per stage and amputated vertex objects
+#             in FP32 / mixed, the same in FP64).  FP32 keeps J in shared memory,
+#             so its table must stay small (short stages); FP64 keeps J in a
+#             global scratch and takes the amputated schedule with longer stages.
+INTERP_PROCESSES = {"gg_ttxggg": (128, 16, 0, 16, 1)}
 
 
 def _apply_kernel_overrides():
@@ -41,7 +45,8 @@ def _apply_kernel_overrides():
         TAB_PROCESSES.pop(proc, None)
         INTERP_PROCESSES.pop(proc, None)
         if parts[0] == "interp":
-            INTERP_PROCESSES[proc] = (int(parts[1]), int(parts[2]))
+            dflt = (0, 16, 0, 16, 1)
+            INTERP_PROCESSES[proc] = tuple(int(parts[i + 1]) if len(parts) > i + 1 else dflt[i] for i in range(5))
         elif parts[0] == "tab":
             dflt = (0, 1, 1, 0, 1, 0, 1, 6, 4)
             TAB_PROCESSES[proc] = tuple(int(parts[i + 1]) if len(parts) > i + 1 else dflt[i] for i in range(9))
@@ -204,10 +209,15 @@ def emit_process(process: str) -> tuple[str, dict]:
     if process in TAB_PROCESSES:
         tab_src, TP, tab_flops = emit_tab_struct(process, *TAB_PROCESSES[process], ncol, nlines, cbody)
     elif process in INTERP_PROCESSES:
-        nt_i, sa = INTERP_PROCESSES[process]
-        tab_src, IP = emit_interp_struct(process, nt_i, sa, num)
+        nt_i, sa, amp_i, sa_d, amp_d = INTERP_PROCESSES[process]
+        tab_src, IP = emit_interp_struct(process, nt_i, sa, num, bool(amp_i))
+        if (sa_d, amp_d) != (sa, amp_i):
+            tab_src += emit_interp_struct(process, nt_i, sa_d, num, bool(amp_d), "ProcInterpD", "d_")[0]
+        else:
+            tab_src += "using ProcInterpD = ProcInterp;\n"
         body, cbody = [], []   # the straight-line chain is not used for this process
     kernel_struct = "ProcTab" if TP else ("ProcInterp" if IP else "Proc")
+    kernel_struct_d = "ProcInterpD" if IP else kernel_struct
     launch_fn = "launch_tab" if TP else ("launch_interp" if IP else "launch_scalar")
     nhel_all = 1 << npar
     if TP:
@@ -274,7 +284,7 @@ struct Proc {{
 static cudaError_t launch(int precision, const LaunchArgs& a)
 {{
     switch (precision) {{
-    case PREC_FP64: return {launch_fn}<{kernel_struct}, double{", false" if IP else ""}>(a);
+    case PREC_FP64: return {launch_fn}<{kernel_struct_d}, double{", false" if IP else ""}>(a);
     case PREC_FP32: return {launch_fn}<{kernel_struct}, float{", false" if IP else ""}>(a);
     case PREC_MIXED: return launch_mixed<{kernel_struct}>(a);
     default: return cudaErrorInvalidValue;
@@ -491,9 +501,11 @@ struct ProcTab : Proc {{
 NL = "\n"
 
 
-def emit_interp_struct(process: str, nt: int, stage_amps: int, num):
-    """ProcInterp: staged table tasks, amplitude descriptors, colour terms."""
-    I = build_interp(process, stage_amps)
+def emit_interp_struct(process: str, nt: int, stage_amps: int, num, amputated: bool = False,
+                       name: str = "ProcInterp", prefix: str = ""):
+    """ProcInterp: staged table tasks, amplitude descriptors, colour terms
+    (arrays named with `prefix`, struct `name`)."""
+    I = build_interp(process, stage_amps, amputated)
     T = I.tab
     P = T.plan
     npar = P.npar
@@ -521,7 +533,7 @@ def emit_interp_struct(process: str, nt: int, stage_amps: int, num):
                 bases.append(0)
                 sups.append(0)
             la, lb = (op.mom if op.kind == "VVV1_0" else (0, 0))
-            assert len(coefs) < 256 and all(c in ((0, 1), (0, -1)) for _, c in coefs)
+            assert len(op.args) <= 4 and len(coefs) < 256 and all(c in ((0, 1), (0, -1)) for _, c in coefs)
             amps.append((bases, sups, AMP_KINDS.index(op.kind), la, lb, len(coefs)))
             for col, c in coefs:
                 terms.append(col | (0x8000 if c == (0, -1) else 0))
@@ -535,9 +547,9 @@ def emit_interp_struct(process: str, nt: int, stage_amps: int, num):
     n = len(num)
     cnum2 = [num[i][j] * (1 if i == j else 2) if j >= i else 0 for i in range(n) for j in range(n)]
 
-    def arr(name, ctype, rows, fmt, per_line=6):
+    def arr(aname, ctype, rows, fmt, per_line=6):
         body = ",\n    ".join(", ".join(fmt(x) for x in rows[i:i + per_line]) for i in range(0, len(rows), per_line))
-        return f"__device__ const {ctype} {name}[{max(len(rows), 1)}] = {{\n    {body if rows else '0'}\n}};\n"
+        return f"__device__ const {ctype} {prefix}{aname}[{max(len(rows), 1)}] = {{\n    {body if rows else '0'}\n}};\n"
 
     src = ""
     src += arr("c_itasks", "TabTask", tasks, lambda t: "{%d, %d, %d, %d, %d, %d, %d, 0, 0}" % t, 4)
@@ -550,20 +562,20 @@ def emit_interp_struct(process: str, nt: int, stage_amps: int, num):
     src += arr("c_supmask", "unsigned short", masks, lambda x: "%d" % x, 16)
     src += arr("c_cnum2", "short", cnum2, lambda x: "%d" % x, 24)
     src += f"""
-// staged evaluation: {len(I.stages)} stages of <= {stage_amps} amplitudes, table peak {I.table_size} entries,
+// staged evaluation{' with amputated vertex objects' if amputated else ''}: {len(I.stages)} stages of <= {stage_amps} amplitudes, table peak {I.table_size} entries,
 // {len(tasks)} table tasks ({I.table_flops} flops per event), {len(terms)} colour terms
-struct ProcInterp : Proc {{
+struct {name} : Proc {{
     static constexpr int NT = {nt}, TAB = {(I.table_size + 7) // 8 * 8}, NSUP = {len(I.supports)}, NSTAGE = {len(I.stages)};
     static constexpr bool IS_TAB = false, IS_INTERP = true;
     static constexpr long long TABLE_FLOPS = {I.table_flops}LL, AMP_FLOPS = {T.amplitude_flops_per_helicity()}LL;
-    __device__ static __forceinline__ const TabTask* tasks() {{ return c_itasks; }}
-    __device__ static __forceinline__ IRound round(int r) {{ return c_rounds[r]; }}
-    __device__ static __forceinline__ IStage stage(int s) {{ return c_stages[s]; }}
-    __device__ static __forceinline__ IAmp amp(int a) {{ return c_amps[a]; }}
-    __device__ static __forceinline__ unsigned short term(int t) {{ return __ldg(c_terms + t); }}
-    __device__ static __forceinline__ int stage_term_begin(int s) {{ return c_stage_term[s]; }}
-    __device__ static __forceinline__ unsigned support_mask(int s) {{ return c_supmask[s]; }}
-    __device__ static __forceinline__ int cnum2(int i, int j) {{ return __ldg(c_cnum2 + i * NCOL + j); }}
+    __device__ static __forceinline__ const TabTask* tasks() {{ return {prefix}c_itasks; }}
+    __device__ static __forceinline__ IRound round(int r) {{ return {prefix}c_rounds[r]; }}
+    __device__ static __forceinline__ IStage stage(int s) {{ return {prefix}c_stages[s]; }}
+    __device__ static __forceinline__ IAmp amp(int a) {{ return {prefix}c_amps[a]; }}
+    __device__ static __forceinline__ unsigned short term(int t) {{ return __ldg({prefix}c_terms + t); }}
+    __device__ static __forceinline__ int stage_term_begin(int s) {{ return {prefix}c_stage_term[s]; }}
+    __device__ static __forceinline__ unsigned support_mask(int s) {{ return {prefix}c_supmask[s]; }}
+    __device__ static __forceinline__ int cnum2(int i, int j) {{ return __ldg({prefix}c_cnum2 + i * NCOL + j); }}
 }};
 """
     return src, I

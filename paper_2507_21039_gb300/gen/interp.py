@@ -20,8 +20,10 @@ from dataclasses import dataclass, field
 from .plan import FLOPS
 from .tabplan import build_tabplan, compress
 
-ROUTINES = ("VVV1P0_1", "VVVV1P0_1", "VVVV3P0_1", "VVVV4P0_1", "FFV1_2", "FFV1_1", "FFV1P0_3")
-AMP_KINDS = ("FFV1_0", "VVV1_0", "VVVV1_0", "VVVV3_0", "VVVV4_0")
+# descriptor codes of the table routines and amplitude kinds (me_kernel_interp.cuh)
+ROUTINES = ("VVV1P0_1", "VVVV1P0_1", "VVVV3P0_1", "VVVV4P0_1", "FFV1_2", "FFV1_1", "FFV1P0_3",
+            "FFV1A_3", "FFV1A_2", "FFV1A_1", "VVV1A_1", "VVV1A_2", "VVV1A_3", "VVVV1A", "VVVV3A", "VVVV4A")
+AMP_KINDS = ("FFV1_0", "VVV1_0", "VVVV1_0", "VVVV3_0", "VVVV4_0", "DOTV", "DOTF")
 
 
 @dataclass

@@ -223,7 +223,7 @@ def test_rambo_full_size_sampled(orc):
 @pytest.mark.parametrize("name,prec", [("gg_ttxgg", "mixed"), ("gg_ttxgg", "fp64"), ("gg_ttx", "fp64"),
                                        ("gg_ttxggg", "mixed")])
 def test_full_size_sampled_parity(orc, name, prec):
-    """BASELINE-size batch in the benchmark's launch configuration; sampled
+    """Full-size batch in the benchmark's launch configuration; sampled
     events checked one by one against the oracle."""
     w = WORKLOADS[name]
     mom, _, _ = orc.rambo(w.seed, w.sqrt_s, w.masses_final, 0, w.nevt, w.cut_mask, PT_MIN, DR_MIN)

@@ -90,6 +90,18 @@ def test_amputated_plan_reproduces_oracle_partial_amplitudes(orc, process):
         assert np.abs(J - A).max() < 1e-12 * scale
 
 
+def test_interpreter_descriptor_codes_match_kernel():
+    """The generator's routine / amplitude codes are the kernel's enum order."""
+    from paper_2507_21039_gb300.gen.interp import AMP_KINDS, ROUTINES
+
+    src = open(os.path.join(ROOT, "paper_2507_21039_gb300", "csrc", "me_kernel_interp.cuh")).read()
+    body = lambda name: re.search(r"enum " + name + r" : unsigned char \{(.*?)\};", src, re.S).group(1)
+    routines = [x.strip().split("=")[0].strip()[2:] for x in body("IRoutine").split(",") if x.strip()]
+    kinds = [x.strip().split("=")[0].strip()[2:] for x in body("IAmpKind").split(",") if x.strip()]
+    assert routines == list(ROUTINES)
+    assert kinds == list(AMP_KINDS)
+
+
 def test_generator_flop_counts_positive():
     for p in ("ee_mumu", "gg_ttx", "gg_ttxg", "gg_ttxgg", "gg_ttxggg"):
         P = build_plan(p)
@@ -166,7 +178,8 @@ def test_abi_validation_without_device(lib):
 
 
 @pytest.mark.parametrize("process,stage,amputated", [("gg_ttxgg", 16, False), ("gg_ttxggg", 16, False),
-                                                     ("gg_ttxg", 4, True), ("gg_ttxgg", 16, True)])
+                                                     ("gg_ttxg", 4, True), ("gg_ttxgg", 16, True),
+                                                     ("gg_ttxggg", 16, True)])
 def test_staged_schedule_reproduces_oracle(orc, process, stage, amputated):
     """The staged schedules (slot reuse after each object's last reader,
     variant indexing; with or without amputated vertex objects) give the
