@@ -1,6 +1,7 @@
 // C ABI of libme (declared in include/me.h): handles, pointer-kind detection,
 // host staging, helicity filtering (arXiv:2507.21039 Sec. 3.1 "non-vanishing
 // helicities"), dispatch to the generated per-process kernels.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -29,6 +30,12 @@ struct me_handle {
     int require_filter;
     int check_finite;
     int gauge_ext;
+    // host-buffer pipeline: two streams (created on first use) and the events
+    // that order them after / before the caller's stream
+    std::mutex pipe_mutex;
+    cudaStream_t pipe[2];
+    cudaEvent_t fork, join[2];
+    bool pipe_ready;
 };
 
 namespace {
@@ -255,6 +262,13 @@ void me_free(me_handle* h)
     if (!h) return;
     cudaDeviceSynchronize();
     cudaFree(h->d_hel);
+    if (h->pipe_ready) {
+        for (int i = 0; i < 2; ++i) {
+            cudaStreamDestroy(h->pipe[i]);
+            cudaEventDestroy(h->join[i]);
+        }
+        cudaEventDestroy(h->fork);
+    }
     delete h;
 }
 
@@ -324,6 +338,62 @@ int me_filter_helicities(me_handle* h, const double* momenta, int64_t nevt, int*
     return rc;
 }
 
+// Host momenta in, host |M|^2 out: the batch is processed in chunks on the
+// handle's two streams, so that the copies of one chunk overlap the evaluation
+// of the other (copy engines and SMs work at the same time).  The caller's
+// stream orders the call: its earlier work comes first, and it waits for every
+// chunk before the call returns.
+constexpr int64_t kPipeChunk = int64_t(1) << 17;
+
+static int sigmakin_host_pipelined(me_handle* h, const double* momenta, int64_t nevt, double* me2, cudaStream_t st)
+{
+    std::lock_guard<std::mutex> lock(h->pipe_mutex);
+    if (!h->pipe_ready) {
+        bool ok = cudaEventCreateWithFlags(&h->fork, cudaEventDisableTiming) == cudaSuccess;
+        for (int i = 0; i < 2 && ok; ++i)
+            ok = cudaStreamCreateWithFlags(&h->pipe[i], cudaStreamNonBlocking) == cudaSuccess &&
+                 cudaEventCreateWithFlags(&h->join[i], cudaEventDisableTiming) == cudaSuccess;
+        if (!ok) {
+            cudaGetLastError();
+            return ME_ECUDA;
+        }
+        h->pipe_ready = true;
+    }
+    const int64_t per = 4 * (int64_t)h->proc->npar;  // doubles per event
+    double *d_mom = nullptr, *d_me2 = nullptr;
+    if (cudaMallocAsync(&d_mom, sizeof(double) * per * nevt, st) != cudaSuccess) return ME_ENOMEM;
+    int rc = ME_OK;
+    if (cudaMallocAsync(&d_me2, sizeof(double) * nevt, st) != cudaSuccess) rc = ME_ENOMEM;
+    if (rc == ME_OK && cudaEventRecord(h->fork, st) != cudaSuccess) rc = ME_ECUDA;
+    for (int i = 0; i < 2 && rc == ME_OK; ++i)
+        if (cudaStreamWaitEvent(h->pipe[i], h->fork, 0) != cudaSuccess) rc = ME_ECUDA;
+    const int64_t chunk = std::max(kPipeChunk, (nevt + 7) / 8);
+    for (int64_t c0 = 0, k = 0; c0 < nevt && rc == ME_OK; c0 += chunk, ++k) {
+        const int64_t n = std::min(chunk, nevt - c0);
+        cudaStream_t s = h->pipe[k & 1];
+        if (cudaMemcpyAsync(d_mom + c0 * per, momenta + c0 * per, sizeof(double) * per * n, cudaMemcpyHostToDevice,
+                            s) != cudaSuccess) {
+            rc = ME_ECUDA;
+            break;
+        }
+        rc = launch_me(h, h->precision, d_mom + c0 * per, n, d_me2 + c0, nullptr, h->d_hel, h->ngood, s);
+        if (rc == ME_OK &&
+            cudaMemcpyAsync(me2 + c0, d_me2 + c0, sizeof(double) * n, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+            rc = ME_ECUDA;
+    }
+    // join both streams into the caller's before the buffers are released
+    for (int i = 0; i < 2; ++i) {
+        if (cudaEventRecord(h->join[i], h->pipe[i]) != cudaSuccess || cudaStreamWaitEvent(st, h->join[i], 0) != cudaSuccess) {
+            cudaStreamSynchronize(h->pipe[i]);
+            if (rc == ME_OK) rc = ME_ECUDA;
+        }
+    }
+    if (d_mom) cudaFreeAsync(d_mom, st);
+    if (d_me2) cudaFreeAsync(d_me2, st);
+    if (cudaStreamSynchronize(st) != cudaSuccess && rc == ME_OK) rc = ME_ECUDA;
+    return rc;
+}
+
 static int sigmakin_impl(me_handle* h, const double* momenta, int64_t nevt, double* me2, double* hel_out,
                          cudaStream_t st)
 {
@@ -346,7 +416,8 @@ static int sigmakin_impl(me_handle* h, const double* momenta, int64_t nevt, doub
         }
         return launch_me(h, h->precision, momenta, nevt, me2, hel_out, h->d_hel, h->ngood, st);
     }
-    // host buffers: stage through stream-ordered device memory, then wait
+    if (!dm && !dr && !h->check_finite && nevt >= 2 * kPipeChunk) return sigmakin_host_pipelined(h, momenta, nevt, me2, st);
+    // other host buffers: stage through stream-ordered device memory, then wait
     double *d_mom = nullptr, *d_me2 = nullptr;
     int rc = ME_OK;
     if (!dm) {

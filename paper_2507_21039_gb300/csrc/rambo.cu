@@ -6,6 +6,7 @@
 // Random numbers: Philox4x64-10 (Salmon, Moraes, Dror, Shaw, SC'11), key
 // (seed, 0), counter (event, attempt, final-particle index, 0); one block
 // yields the four uniforms of one final-state particle, u = ((x >> 11) + 1/2) 2^-53.
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 
@@ -15,6 +16,7 @@ namespace {
 
 constexpr int kMaxFinal = 6;
 constexpr int kMaxAttempts = 1000;
+constexpr int64_t kPipeChunk = int64_t(1) << 17;  // events per chunk of the host-output pipeline
 
 struct U4 { uint64_t x[4]; };
 
@@ -250,16 +252,62 @@ extern "C" int rambo_sample(uint64_t seed, int64_t ev0, int64_t nevt, double sqr
     a.mom = dev_m ? momenta_out : d_m;
     a.wt = weights_out ? (dev_w ? weights_out : d_w) : nullptr;
     a.nfail = d_fail;
-    if (rc == ME_OK) {
-        const int th = 128;
+    const int th = 128;
+    if (rc == ME_OK && !dev_m && nevt >= 2 * kPipeChunk) {
+        // host output: chunks on two streams, so that the copy of one chunk
+        // overlaps the sampling of the next; ordered after the caller's stream
+        // and joined back into it
+        cudaStream_t s2[2] = {nullptr, nullptr};
+        cudaEvent_t fork = nullptr, join[2] = {nullptr, nullptr};
+        bool ok = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming) == cudaSuccess &&
+                  cudaEventRecord(fork, st) == cudaSuccess;
+        for (int i = 0; i < 2 && ok; ++i)
+            ok = cudaStreamCreateWithFlags(&s2[i], cudaStreamNonBlocking) == cudaSuccess &&
+                 cudaEventCreateWithFlags(&join[i], cudaEventDisableTiming) == cudaSuccess &&
+                 cudaStreamWaitEvent(s2[i], fork, 0) == cudaSuccess;
+        const int64_t chunk = std::max(kPipeChunk, (nevt + 7) / 8);
+        const size_t per = sizeof(double) * 4 * npar;
+        for (int64_t c0 = 0, k = 0; c0 < nevt && ok; c0 += chunk, ++k) {
+            const int64_t n = std::min(chunk, nevt - c0);
+            Params b = a;
+            b.ev0 = a.ev0 + c0;
+            b.nevt = n;
+            b.mom = a.mom + c0 * 4 * npar;
+            b.wt = a.wt ? a.wt + c0 : nullptr;
+            rambo_kernel<<<(unsigned)((n + th - 1) / th), th, 0, s2[k & 1]>>>(b);
+            ok = cudaGetLastError() == cudaSuccess &&
+                 cudaMemcpyAsync(reinterpret_cast<char*>(momenta_out) + c0 * per, b.mom, per * n, cudaMemcpyDeviceToHost,
+                                 s2[k & 1]) == cudaSuccess;
+            if (ok && d_w)
+                ok = cudaMemcpyAsync(weights_out + c0, b.wt, sizeof(double) * n, cudaMemcpyDeviceToHost, s2[k & 1]) ==
+                     cudaSuccess;
+        }
+        for (int i = 0; i < 2; ++i) {
+            if (!s2[i]) continue;
+            if (!join[i] || cudaEventRecord(join[i], s2[i]) != cudaSuccess || cudaStreamWaitEvent(st, join[i], 0) != cudaSuccess) {
+                cudaStreamSynchronize(s2[i]);
+                ok = false;
+            }
+        }
+        for (int i = 0; i < 2; ++i) {
+            if (s2[i]) cudaStreamDestroy(s2[i]);
+            if (join[i]) cudaEventDestroy(join[i]);
+        }
+        if (fork) cudaEventDestroy(fork);
+        if (!ok) {
+            cudaGetLastError();
+            rc = ME_ECUDA;
+        }
+    } else if (rc == ME_OK) {
         rambo_kernel<<<(unsigned)((nevt + th - 1) / th), th, 0, st>>>(a);
         if (cudaGetLastError() != cudaSuccess) rc = ME_ECUDA;
+        if (rc == ME_OK && !dev_m && cudaMemcpyAsync(momenta_out, d_m, mbytes, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+            rc = ME_ECUDA;
+        if (rc == ME_OK && d_w &&
+            cudaMemcpyAsync(weights_out, d_w, sizeof(double) * nevt, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+            rc = ME_ECUDA;
     }
     unsigned long long nfail = 0;
-    if (rc == ME_OK && !dev_m && cudaMemcpyAsync(momenta_out, d_m, mbytes, cudaMemcpyDeviceToHost, st) != cudaSuccess)
-        rc = ME_ECUDA;
-    if (rc == ME_OK && d_w && cudaMemcpyAsync(weights_out, d_w, sizeof(double) * nevt, cudaMemcpyDeviceToHost, st) != cudaSuccess)
-        rc = ME_ECUDA;
     if (rc == ME_OK && d_fail && cudaMemcpyAsync(&nfail, d_fail, sizeof(nfail), cudaMemcpyDeviceToHost, st) != cudaSuccess)
         rc = ME_ECUDA;
     if (d_m) cudaFreeAsync(d_m, st);

@@ -241,6 +241,33 @@ def test_full_size_sampled_parity(orc, name, prec):
     assert np.all(np.isfinite(out)) and np.all(out > 0)
 
 
+@pytest.mark.parametrize("name,prec", [("gg_ttx", "fp64"), ("gg_ttxg", "mixed")])
+def test_host_buffer_pipeline_matches_device(name, prec):
+    """Host buffers of 300000 events (two full pipeline chunks and a ragged
+    tail) through rambo_sample and me_sigmakin: bitwise the device-buffer
+    results, weights included."""
+    w = WORKLOADS[name]
+    n = 300000
+    masses = [0.0, 0.0] + list(w.masses_final)
+    cuts = me.cuts_for(name)
+    d_mom = me.rambo_sample(w.seed, 7, n, w.sqrt_s, masses, cuts, check=True)
+    d_wt = torch.empty(n, dtype=torch.float64, device="cuda")
+    me.rambo_sample(w.seed, 7, n, w.sqrt_s, masses, cuts, momenta_out=d_mom, weights_out=d_wt, check=True)
+    h_mom = torch.empty((n, w.npar, 4), dtype=torch.float64, pin_memory=True)
+    h_wt = torch.empty(n, dtype=torch.float64, pin_memory=True)
+    me.rambo_sample(w.seed, 7, n, w.sqrt_s, masses, cuts, momenta_out=h_mom, weights_out=h_wt, check=True)
+    assert torch.equal(h_mom, d_mom.cpu()) and torch.equal(h_wt, d_wt.cpu())
+    h = me.workload_handle(name, prec)
+    me.me_filter_helicities(h, d_mom[:4096])
+    d_me2 = me.me_sigmakin(h, d_mom)
+    h_me2 = torch.empty(n, dtype=torch.float64, pin_memory=True)
+    me.me_sigmakin(h, h_mom, h_me2)
+    assert torch.equal(h_me2, d_me2.cpu())
+    pageable = h_mom.numpy().copy()   # pageable host memory takes the same path
+    assert np.array_equal(me.me_sigmakin(h, pageable), d_me2.cpu().numpy())
+    h.close()
+
+
 def test_mixed_uses_tensor_core_colour_sum(orc):
     """gg -> t t~ g g mixed: the colour sum runs on BF16 tensor cores (hi/lo
     split, FP32 accumulation).  Its results differ bitwise from the FP32 scalar
