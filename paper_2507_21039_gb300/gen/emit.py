@@ -384,13 +384,20 @@ def emit_tab_struct(process: str, nt: int, epc_f: int, epc_d: int, pair: int, am
     table rounds of the objects that become live, then the stage's amplitudes,
     slots reused after each object's last reader; one helicity per thread."""
     tasks = []
+    # rounds of one level run without barriers between them; each round's
+    # tasks start at the warp after the one where the previous round's ended,
+    # so that small rounds do not all land on the first warp
+    rot = [0]
 
     def round_code(kind, tl, level_note):
         start = len(tasks)
         for out, ins, ln in tl:
             ins = list(ins) + [0] * (3 - len(ins))
             tasks.append((out, ins[0], ins[1], ins[2], *(max(x, 0) for x in ln)))
-        return (f"for (int t = tid; t < {len(tl)}; t += NT) {{ const TabTask k = ld_task(c_tasks + {start} + t); "
+        off = rot[0]
+        rot[0] = (off + -(-len(tl) // 32) * 32) % nt
+        first = "tid" if off == 0 else f"(tid + {nt - off}) % NT"
+        return (f"for (int t = {first}; t < {len(tl)}; t += NT) {{ const TabTask k = ld_task(c_tasks + {start} + t); "
                 f"{_table_call(kind)} }}  // {level_note}{kind}")
 
     if stage == 0:
