@@ -56,12 +56,15 @@ extern "C" {
 #define ME_ESAMPLER (-7)      /* RAMBO: an event needed more than 1000 attempts or Newton failed */
 #define ME_ETOOLARGE (-8)     /* me_filter_helicities_noalloc: the probe batch does not fit its fixed scratch */
 
-/* precision modes (Sec. 4.1, Table 1: FP64, FP32, mixed) */
+/* precision modes (Sec. 4.1, Table 1: FP64, FP32, mixed; ME_PREC_MIXED is this library's
+   tensor-core variant, ME_PREC_MIXED64 the paper's definition) */
 #define ME_PREC_FP64 0   /* chain, colour sum and helicity sum in FP64 */
 #define ME_PREC_FP32 1   /* chain and colour sum in FP32; momenta, p^2-m^2 and helicity sum in FP64 */
 #define ME_PREC_MIXED 2  /* FP32 chain (FP64 momenta, p^2-m^2), colour sum on BF16 tensor cores
                             with hi/lo split operands and FP32 accumulation (24 and 120 flows;
                             FP32 scalar below), FP64 helicity sum */
+#define ME_PREC_MIXED64 3 /* the paper's mixed mode (Sec. 4.1, Table 1): FP64 chain, the colour-flow
+                             amplitudes cast to FP32 for the colour sum, FP64 helicity sum */
 
 typedef struct me_handle me_handle;
 

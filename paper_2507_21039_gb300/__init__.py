@@ -30,7 +30,8 @@ ME_ETOOLARGE = -8
 ME_PREC_FP64 = 0
 ME_PREC_FP32 = 1
 ME_PREC_MIXED = 2
-PRECISIONS = {"fp64": ME_PREC_FP64, "fp32": ME_PREC_FP32, "mixed": ME_PREC_MIXED}
+ME_PREC_MIXED64 = 3
+PRECISIONS = {"fp64": ME_PREC_FP64, "fp32": ME_PREC_FP32, "mixed": ME_PREC_MIXED, "mixed64": ME_PREC_MIXED64}
 
 ME_OPT_REQUIRE_FILTER = 1
 ME_OPT_CHECK_FINITE = 2

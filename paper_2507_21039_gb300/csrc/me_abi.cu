@@ -210,7 +210,7 @@ int me_init(me_handle** hp, const char* process, const double* masses, int nmass
     *hp = nullptr;
     const ProcDesc* pd = me::find_process(process);
     if (!pd) return ME_EINVAL;
-    if (precision < ME_PREC_FP64 || precision > ME_PREC_MIXED) return ME_EINVAL;
+    if (precision < ME_PREC_FP64 || precision > ME_PREC_MIXED64) return ME_EINVAL;
     const bool qcd = pd->ngluon > 0;
     double mt = qcd ? 173.0 : 0.0;
     if (nmass != 0 || masses) {

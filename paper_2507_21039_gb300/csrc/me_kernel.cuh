@@ -18,6 +18,8 @@
 //     120-flow basis), then the colour quadratic form, accumulating |M_h|^2 in
 //     FP64.
 #pragma once
+#include <type_traits>
+
 #include "helas.cuh"
 #include "me_proc.h"
 
@@ -99,8 +101,26 @@ __device__ __forceinline__ void event_setup(const double* __restrict__ p, int it
     else ln[item - 2 * P::NPAR] = line_data<P, T>(p, item - 2 * P::NPAR, mt);
 }
 
-// Scalar colour contraction and helicity sum.  T: chain/colour precision.
-template <class P, class T>
+// Colour form J^+ N J in precision C of a colour-flow vector J held in
+// precision T: with C != T the amplitudes are cast to C first (the paper's
+// mixed mode evaluates them in FP64 and the colour algebra in FP32).
+template <class P, class T, class C, class JT> __device__ __forceinline__ T colour_as(const JT& J)
+{
+    if constexpr (std::is_same<C, T>::value) {
+        return P::template colour<T>(J);
+    } else {
+        cx<C> Jc[P::NCOL];
+#pragma unroll
+        for (int c = 0; c < P::NCOL; ++c) {
+            const cx<T> j = J[c];
+            Jc[c] = {(C)j.re, (C)j.im};
+        }
+        return (T)P::template colour<C>(Jc);
+    }
+}
+
+// Scalar colour contraction and helicity sum.  T: chain precision, C: colour.
+template <class P, class T, class C = T>
 __global__ void __launch_bounds__(P::THREADS) me_kernel_scalar(LaunchArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -147,13 +167,13 @@ __global__ void __launch_bounds__(P::THREADS) me_kernel_scalar(LaunchArgs a)
                 JSmem<T, TH> J{jb};
                 for (int c = 0; c < P::NCOL; ++c) J[c] = {T(0), T(0)};
                 P::template chain<T>(ext, hel, ln, (T)a.mt, J);
-                v = P::template colour<T>(J);
+                v = colour_as<P, T, C>(J);
             } else {
                 cx<T> J[P::NCOL];
 #pragma unroll
                 for (int c = 0; c < P::NCOL; ++c) J[c] = {T(0), T(0)};
                 P::template chain<T>(ext, hel, ln, (T)a.mt, J);
-                v = P::template colour<T>(J);
+                v = colour_as<P, T, C>(J);
             }
             acc += (double)v;
             if (a.hel_out) a.hel_out[(e0 + ev) * a.nlist + i] = (double)v * a.norm;
@@ -186,16 +206,16 @@ template <class K> cudaError_t ensure_smem(K kernel, size_t bytes, size_t& grant
     return cudaSuccess;
 }
 
-template <class P, class T> cudaError_t launch_scalar(const LaunchArgs& a)
+template <class P, class T, class C = T> cudaError_t launch_scalar(const LaunchArgs& a)
 {
     const int E = P::THREADS / a.slots;
     const long long grid = (a.nevt + E - 1) / E;
     const size_t smem = scalar_smem_bytes<P, T>(E);
     static size_t granted = 0;  // per instantiation; idempotent if raced
-    cudaError_t e = ensure_smem(me_kernel_scalar<P, T>, smem, granted);
+    cudaError_t e = ensure_smem(me_kernel_scalar<P, T, C>, smem, granted);
     if (e != cudaSuccess) return e;
     if (grid > 0x7fffffffLL) return cudaErrorInvalidValue;
-    me_kernel_scalar<P, T><<<(unsigned)grid, P::THREADS, smem, a.stream>>>(a);
+    me_kernel_scalar<P, T, C><<<(unsigned)grid, P::THREADS, smem, a.stream>>>(a);
     return cudaGetLastError();
 }
 

@@ -73,8 +73,8 @@ __device__ __forceinline__ void run_task(const TabRef<T, TAB>& tab, const Ln<T>*
     tab.st(k.out, o);
 }
 
-// TC: colour sum on BF16 tensor cores (T = float); otherwise scalar in T
-template <class P, class T, bool TC>
+// TC: colour sum on BF16 tensor cores (T = float); otherwise scalar in C
+template <class P, class T, bool TC, class C = T>
 __global__ void __launch_bounds__(P::NT) me_kernel_interp(LaunchArgs a, cx<T>* __restrict__ jglobal)
 {
     using L = InterpLayout<P, T>;
@@ -159,17 +159,19 @@ __global__ void __launch_bounds__(P::NT) me_kernel_interp(LaunchArgs a, cx<T>* _
             v = colour_tc_smem<NCOL, NT, P::NSPLIT>(reinterpret_cast<const cx<float>*>(smem + L::jsm), P::bfrag(),
                                                     rowv, tid);
         } else {
+            C w = C(0);
             for (int i = 0; i < NCOL; ++i) {
                 const cx<T> ji = jp[i * NT];
-                T zr = T(0), zi = T(0);
+                C zr = C(0), zi = C(0);
                 for (int j = i; j < NCOL; ++j) {
-                    const T n = (T)P::cnum2(i, j);
+                    const C n = (C)P::cnum2(i, j);
                     const cx<T> jj = jp[j * NT];
-                    zr = fma(n, jj.re, zr);
-                    zi = fma(n, jj.im, zi);
+                    zr = fma(n, (C)jj.re, zr);
+                    zi = fma(n, (C)jj.im, zi);
                 }
-                v = fma(ji.re, zr, fma(ji.im, zi, v));
+                w = fma((C)ji.re, zr, fma((C)ji.im, zi, w));
             }
+            v = (T)w;
         }
         double acc = 0.0;
         if (act) {
@@ -188,19 +190,19 @@ __global__ void __launch_bounds__(P::NT) me_kernel_interp(LaunchArgs a, cx<T>* _
     }
 }
 
-template <class P, class T, bool TC = false> cudaError_t launch_interp(const LaunchArgs& a)
+template <class P, class T, bool TC = false, class C = T> cudaError_t launch_interp(const LaunchArgs& a)
 {
     using L = InterpLayout<P, T>;
     static_assert(!TC || sizeof(T) == 4, "tensor-core colour sum is the mixed-precision path");
     static_assert(L::bytes <= 232448, "interpreter shared memory exceeds 227 KB");
     if (a.nlist > P::NT) return cudaErrorInvalidValue;
     static size_t granted = 0;
-    cudaError_t e = ensure_smem(me_kernel_interp<P, T, TC>, L::bytes, granted);
+    cudaError_t e = ensure_smem(me_kernel_interp<P, T, TC, C>, L::bytes, granted);
     if (e != cudaSuccess) return e;
     int dev = 0, nsm = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, me_kernel_interp<P, T, TC>, P::NT, L::bytes) != cudaSuccess ||
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, me_kernel_interp<P, T, TC, C>, P::NT, L::bytes) != cudaSuccess ||
         per_sm < 1) {
         cudaGetLastError();
         per_sm = 1;
@@ -212,7 +214,7 @@ template <class P, class T, bool TC = false> cudaError_t launch_interp(const Lau
         e = cudaMallocAsync(&jg, sizeof(cx<T>) * (size_t)grid * P::NCOL * P::NT, a.stream);
         if (e != cudaSuccess) return e;
     }
-    me_kernel_interp<P, T, TC><<<(unsigned)grid, P::NT, L::bytes, a.stream>>>(a, jg);
+    me_kernel_interp<P, T, TC, C><<<(unsigned)grid, P::NT, L::bytes, a.stream>>>(a, jg);
     e = cudaGetLastError();
     if (jg) cudaFreeAsync(jg, a.stream);
     return e;

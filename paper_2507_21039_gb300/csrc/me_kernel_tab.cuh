@@ -127,7 +127,7 @@ template <class P, class T> __host__ __device__ constexpr size_t tab_smem_bytes(
 // share instruction-cache lines and overlap each other's long-latency FP64 work.
 template <class P, class T> __host__ __device__ constexpr int tab_epc() { return is_fp64<T>() ? P::EPC_D : P::EPC_F; }
 
-template <class P, class T, bool TC>
+template <class P, class T, bool TC, class C = T>
 __global__ void __launch_bounds__(P::NT * tab_epc<P, T>(), is_fp64<T>() ? P::MIN_CTAS_D : P::MIN_CTAS_F)
     me_kernel_tab(LaunchArgs a)
 {
@@ -192,7 +192,7 @@ __global__ void __launch_bounds__(P::NT * tab_epc<P, T>(), is_fp64<T>() ? P::MIN
                 unsigned char* stage = smem + tab_table_offset<P, T>() + (tid >> 5) * TcShape<P::NCOL>::WARP_BYTES;
                 v = colour_tc_warp<P::NCOL, P::NSPLIT>(J, stage, P::bfrag(), tid & 31);
             } else {
-                v = P::template colour<T>(J);
+                v = colour_as<P, T, C>(J);
             }
             if (act) {
                 acc += (double)v;
@@ -366,9 +366,9 @@ template <class P, bool TC> cudaError_t launch_pair(const LaunchArgs& a)
     return cudaGetLastError();
 }
 
-template <class P, class T, bool TC = false> cudaError_t launch_tab(const LaunchArgs& a)
+template <class P, class T, bool TC = false, class C = T> cudaError_t launch_tab(const LaunchArgs& a)
 {
-    if constexpr (!is_fp64<T>() && P::PAIR_F) {
+    if constexpr (!is_fp64<T>() && std::is_same<C, T>::value && P::PAIR_F) {
         return launch_pair<P, TC>(a);
     } else {
         constexpr int EPC = tab_epc<P, T>();
@@ -378,24 +378,24 @@ template <class P, class T, bool TC = false> cudaError_t launch_tab(const Launch
             static_assert((P::NT / 32) * TcShape<P::NCOL>::WARP_BYTES <= P::TAB * sizeof(Wf<T>),
                           "tensor-core staging must fit in the table region");
         static size_t granted = 0;
-        cudaError_t e = ensure_smem(me_kernel_tab<P, T, TC>, smem, granted);
+        cudaError_t e = ensure_smem(me_kernel_tab<P, T, TC, C>, smem, granted);
         if (e != cudaSuccess) return e;
         const long long ctas = (a.nevt + EPC - 1) / EPC;
         const long long grid = ctas < 0x7fffffffLL ? ctas : 0x7fffffffLL;
-        me_kernel_tab<P, T, TC><<<(unsigned)grid, P::NT * EPC, smem, a.stream>>>(a);
+        me_kernel_tab<P, T, TC, C><<<(unsigned)grid, P::NT * EPC, smem, a.stream>>>(a);
         return cudaGetLastError();
     }
 }
 
 // Mixed precision: FP32 chain; colour sum on BF16 tensor cores for 24 or more
 // colour flows when every thread holds one helicity, FP32 scalar otherwise.
-template <class P, class T, bool TC> cudaError_t launch_interp(const LaunchArgs& a);
+template <class P, class T, bool TC, class C> cudaError_t launch_interp(const LaunchArgs& a);
 
 template <class P> cudaError_t launch_mixed(const LaunchArgs& a)
 {
     if constexpr (P::IS_INTERP) {
-        if constexpr (P::NCOL >= 24) return launch_interp<P, float, true>(a);
-        else return launch_interp<P, float, false>(a);
+        if constexpr (P::NCOL >= 24) return launch_interp<P, float, true, float>(a);
+        else return launch_interp<P, float, false, float>(a);
     } else if constexpr (P::IS_TAB) {
         if constexpr (P::NCOL >= 24) {
             if (a.nlist <= P::NT) return launch_tab<P, float, true>(a);

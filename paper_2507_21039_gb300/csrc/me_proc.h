@@ -20,7 +20,7 @@ struct LaunchArgs {
     cudaStream_t stream;
 };
 
-enum Precision : int { PREC_FP64 = 0, PREC_FP32 = 1, PREC_MIXED = 2 };
+enum Precision : int { PREC_FP64 = 0, PREC_FP32 = 1, PREC_MIXED = 2, PREC_MIXED64 = 3 };
 
 struct ProcDesc {
     const char* name;

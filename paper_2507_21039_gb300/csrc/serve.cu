@@ -356,7 +356,7 @@ int srv_submit(srv_server* s, const char* process, int precision, const double* 
 {
     if (!s || !process || !momenta || !me2_out || !ticket) return ME_EINVAL;
     const int npar = npar_of(process);
-    if (!npar || nevt <= 0 || nevt > s->cfg.max_batch || precision < ME_PREC_FP64 || precision > ME_PREC_MIXED)
+    if (!npar || nevt <= 0 || nevt > s->cfg.max_batch || precision < ME_PREC_FP64 || precision > ME_PREC_MIXED64)
         return ME_EINVAL;
     auto r = std::make_shared<Request>();
     r->process = process;

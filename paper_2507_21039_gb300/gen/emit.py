@@ -287,6 +287,7 @@ static cudaError_t launch(int precision, const LaunchArgs& a)
     case PREC_FP64: return {launch_fn}<{kernel_struct_d}, double{", false" if IP else ""}>(a);
     case PREC_FP32: return {launch_fn}<{kernel_struct}, float{", false" if IP else ""}>(a);
     case PREC_MIXED: return launch_mixed<{kernel_struct}>(a);
+    case PREC_MIXED64: return {launch_fn}<{kernel_struct_d}, double{", false" if (IP or TP) else ""}, float>(a);
     default: return cudaErrorInvalidValue;
     }}
 }}

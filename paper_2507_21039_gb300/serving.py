@@ -180,6 +180,32 @@ def bench_point(load=0.7, nreq=300, processes=None, precision="mixed", lanes=4):
             "batches": st["batches"], "graph_updates": st["graph_updates"]}
 
 
+def sweep(loads=(0.1, 0.3, 0.5, 0.7, 0.9, 1.1), nreq=2000, processes=None, precision="mixed", lanes=4):
+    """Latency against offered load: Poisson arrivals at each `load` x the
+    measured saturation request rate, `nreq` requests per point (the same
+    seeded request stream at every point)."""
+    processes = processes or built_processes()
+    reqs, bufs = make_requests(nreq, processes)
+    srv = Server(lanes=lanes, max_batch=1 << 17)
+    points = []
+    try:
+        run_load(srv, reqs[:min(40, nreq)], bufs, 0.0, precision)  # warm-up: handles, graphs
+        sat_ev = saturation(srv, reqs, bufs, precision)
+        mean_batch = float(np.mean([n for _, n in reqs]))
+        for load in loads:
+            rate = load * sat_ev / mean_batch
+            lat, ev, wall, _ = run_load(srv, reqs, bufs, rate, precision)
+            points.append({"load": load, "rate_req_per_s": rate, "events_per_s": ev / wall,
+                           "p50_ms": float(np.percentile(lat, 50) * 1e3), "p90_ms": float(np.percentile(lat, 90) * 1e3),
+                           "p99_ms": float(np.percentile(lat, 99) * 1e3)})
+        st = srv.stats()
+    finally:
+        srv.close()
+    return {"requests_per_point": nreq, "saturation_events_per_s": sat_ev, "mean_batch": mean_batch,
+            "processes": processes, "precision": precision, "lanes": lanes, "points": points,
+            "batches": st["batches"], "graph_updates": st["graph_updates"]}
+
+
 def built_processes():
     """Processes of the serving mix that this library build contains."""
     from . import load as _load
@@ -192,3 +218,15 @@ def built_processes():
             lib.me_free(h)
             out.append(p)
     return out
+
+
+if __name__ == "__main__":
+    import argparse
+    import json
+
+    ap = argparse.ArgumentParser(description="serving latency sweep on the current CUDA device")
+    ap.add_argument("--requests", type=int, default=2000)
+    ap.add_argument("--loads", default="0.1,0.3,0.5,0.7,0.9,1.1")
+    ap.add_argument("--precision", default="mixed")
+    args = ap.parse_args()
+    print(json.dumps(sweep(tuple(float(x) for x in args.loads.split(",")), args.requests, precision=args.precision)))

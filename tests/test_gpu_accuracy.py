@@ -1,7 +1,13 @@
 """Relative-error distribution of |M|^2 per process and precision against the
 FP64 oracle (median, p99, max), the report the benchmark definition asks for.
 Bounds: FP64 <= 1e-12 per event; FP32 and mixed median <= 1e-5, max <= 1e-3.
-Set ME_ACCURACY_REPORT=<path> to write the table as JSON."""
+Set ME_ACCURACY_REPORT=<path> to write the table as JSON.
+
+The second test is the counterpart of the paper's Table 1 (significant
+digits of gg -> t t~ ggg on 8000 points per precision): digits of an event =
+-log10 of its relative error against the FP64 oracle (capped at 16); worst and
+best are the floors of the minimum and maximum.  Set ME_DIGITS_REPORT=<path>
+to write it as JSON."""
 import json
 import os
 
@@ -28,7 +34,7 @@ def test_error_distribution_per_precision(orc):
         mom, _, _ = orc.rambo(w.seed, w.sqrt_s, w.masses_final, 0, n, w.cut_mask, PT_MIN, DR_MIN)
         ref = orc.me2(name, mom, mt=MT, alpha=w.alpha)
         d = torch.from_numpy(mom).cuda()
-        for prec in w.precisions if name != "ee_mumu" else ("fp64", "fp32", "mixed"):
+        for prec in (tuple(w.precisions) if name != "ee_mumu" else ("fp64", "fp32", "mixed")) + ("mixed64",):
             h = me.workload_handle(name, prec)
             got = me.me_sigmakin(h, d).cpu().numpy()
             h.close()
@@ -44,3 +50,32 @@ def test_error_distribution_per_precision(orc):
         with open(out, "w") as f:
             json.dump(report, f, indent=1)
     print(json.dumps(report, indent=1))
+
+
+def test_significant_digits_ttggg(orc):
+    import __graft_entry__
+
+    __graft_entry__.build()
+    import paper_2507_21039_gb300 as me
+
+    name, n = "gg_ttxggg", 8000
+    w = WORKLOADS[name]
+    mom, _, _ = orc.rambo(w.seed, w.sqrt_s, w.masses_final, 0, n, w.cut_mask, PT_MIN, DR_MIN)
+    ref = orc.me2(name, mom, mt=MT, alpha=w.alpha)
+    d = torch.from_numpy(mom).cuda()
+    table = {}
+    for prec in ("fp64", "fp32", "mixed", "mixed64"):
+        h = me.workload_handle(name, prec)
+        got = me.me_sigmakin(h, d).cpu().numpy()
+        h.close()
+        digits = -np.log10(np.maximum(np.abs(got / ref - 1), 1e-16))
+        table[prec] = {"events": n, "worst": int(np.floor(digits.min())), "best": int(np.floor(digits.max())),
+                       "mean": float(digits.mean())}
+    assert table["fp64"]["mean"] >= 12 and table["fp64"]["worst"] >= 11, table["fp64"]
+    for prec in ("fp32", "mixed", "mixed64"):
+        assert table[prec]["mean"] >= 5 and table[prec]["worst"] >= 3, (prec, table[prec])
+    out = os.environ.get("ME_DIGITS_REPORT")
+    if out:
+        with open(out, "w") as f:
+            json.dump(table, f, indent=1)
+    print(json.dumps(table, indent=1))

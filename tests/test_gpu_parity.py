@@ -59,7 +59,7 @@ def test_fp64_parity(orc, name):
     assert rel.max() < FP64_TOL, (rel.max(), np.argmax(rel))
 
 
-@pytest.mark.parametrize("prec", ["fp32", "mixed"])
+@pytest.mark.parametrize("prec", ["fp32", "mixed", "mixed64"])
 @pytest.mark.parametrize("name", ["gg_ttx", "gg_ttxg", "gg_ttxgg", "gg_ttxggg"])
 def test_low_precision_parity(orc, name, prec):
     n = SIZES[name]
