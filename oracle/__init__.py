@@ -56,6 +56,8 @@ def _load():
             lib.orc_me2.restype = i
             lib.orc_partial_amps.argtypes = [i, P, d, i, i, P]
             lib.orc_partial_amps.restype = i
+            lib.orc_sde.argtypes = [i, P, d, P, i, P, P, P]
+            lib.orc_sde.restype = i
             lib.orc_colour_matrix.argtypes = [i, P]
             lib.orc_colour_matrix.restype = i
             lib.orc_me2_dressed.argtypes = [i, P, d, d, P, i, P]
@@ -148,6 +150,23 @@ def me2(process, momenta, mt=173.0, alpha=None, per_helicity=False, nthreads=0):
     if st != 0:
         raise RuntimeError("oracle me2 failed")
     return (out, hel) if per_helicity else out
+
+
+def sde(process, p_event, helicities, mt=173.0):
+    """Feynman diagrams one by one (single-diagram enhancement): for one event,
+    per diagram the sum over `helicities` of |amp_d|^2 with bare vertex factors
+    (no couplings), and each diagram's internal lines as masks over the external
+    particles (the side without the tbar), sorted.  Returns (w2, [lines])."""
+    pid = _pid(process)
+    p = np.ascontiguousarray(p_event, dtype=np.float64)
+    hels = np.ascontiguousarray(helicities, dtype=np.int32)
+    w2 = np.zeros(1300)
+    lines = np.zeros(1300 * 4, dtype=np.int32)
+    nl = np.zeros(1300, dtype=np.int32)
+    nd = _load().orc_sde(pid, _ptr(p), float(mt), _ptr(hels), len(hels), _ptr(w2), _ptr(lines), _ptr(nl))
+    if nd < 0:
+        raise RuntimeError("oracle sde failed")
+    return w2[:nd].copy(), [tuple(int(x) for x in lines[4 * d:4 * d + nl[d]]) for d in range(nd)]
 
 
 def partial_amps(process, p_event, helicity, mt=173.0, gauge_gluon=-1) -> np.ndarray:

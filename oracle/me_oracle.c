@@ -942,3 +942,275 @@ double orc_closed_ggtt(const double *p, double mt, double alpha_s)
     double g2 = 4.0 * M_PI * alpha_s;
     return g2 * g2 * (1.0 / (6 * t1 * t2) - 3.0 / 8.0) * (t1 * t1 + t2 * t2 + rho - rho * rho / (4 * t1 * t2));
 }
+
+/* ------------------------------------------------------------------ */
+/* Feynman diagrams one by one: single-diagram-enhancement weights     */
+/* ------------------------------------------------------------------ */
+/* The paper's multi-channel integration weights a phase-space channel by
+ * |amp_d|^2 / sum_d' |amp_d'|^2, amp_d the amplitude of one Feynman diagram,
+ * summed over helicities (its single-diagram enhancement).  Here every tree
+ * diagram of g g -> t tbar + n g is enumerated directly (independently of the
+ * colour-ordered recursion above) and evaluated with the bare vertex factors:
+ * no couplings and no factors of i, so amp_d is fixed up to a phase.
+ *
+ *   gluon tree: a leaf (external gluon), a three-gluon vertex with two
+ *     children, or a four-gluon vertex with three children; children are
+ *     unordered.  A four-gluon vertex has three Lorentz structures (one per
+ *     colour structure), (A.C)B-(B.C)A, (A.B)C-(B.C)A, (A.B)C-(A.C)B, each a
+ *     separate amplitude of the same diagram; |amp_d|^2 sums them.
+ *   current of a tree with leaf set S (outgoing momentum P_S): the vertex
+ *     contracted with the children's currents, times 1/P_S^2.
+ *   diagram: an ordered sequence of trees along the quark line, read from the
+ *     outgoing t (ubar) to the outgoing tbar (v), leaf sets partitioning the
+ *     gluons; amp = ubar [J1.gamma] S(q1) [J2.gamma] ... [Jm.gamma] v with
+ *     S(q) = (qslash + m) / (q^2 - m^2), q_j = p_t + sum_{i<=j} P_i.
+ *     (m = 1: the single tree meets the t tbar pair directly.)
+ * A diagram is identified by its internal lines: each line is the set of
+ * external particles on one side of it (the side without the tbar), and a
+ * tree diagram is fixed by this set of splits.  Counting a four-gluon vertex
+ * once gives 3, 16, 123, 1240 diagrams for 2..5 gluons. */
+
+#define SDE_MAXTREE 1024   /* distinct gluon trees over all subsets of 5 gluons */
+#define SDE_MAXVAR 9       /* four-gluon structure variants of one tree (<= 2 vertices) */
+#define SDE_MAXDIAG 1300
+#define SDE_MAXLINES 4
+
+typedef struct {
+    int mask;        /* leaf set (bits over gluon positions) */
+    int kind;        /* 0 leaf, 3 three-gluon, 4 four-gluon */
+    int child[3];
+    int nvar;        /* structure variants */
+    int leaf;        /* gluon position of a leaf */
+} sde_tree;
+
+typedef struct {
+    int m;                  /* trees along the quark line */
+    int tree[MAXG];
+    int nlines;
+    int lines[SDE_MAXLINES]; /* internal-line masks over external particles, sorted */
+} sde_diag;
+
+static sde_tree sde_trees[SDE_MAXTREE];
+static int sde_ntree;
+static int sde_first[1 << MAXG], sde_count[1 << MAXG]; /* trees of each leaf set (contiguous) */
+static sde_diag sde_diags[MAXG + 1][SDE_MAXDIAG];
+static int sde_ndiag[MAXG + 1];
+static int sde_k = -1; /* gluon count the tables above were built for */
+
+static int lowbit(int x) { return x & -x; }
+
+/* all trees with leaf set S, appended contiguously (children first) */
+static void sde_build_trees(int k)
+{
+    sde_ntree = 0;
+    for (int S = 1; S < (1 << k); ++S) {
+        /* subsets in increasing order: every proper subset is done before S */
+        sde_first[S] = sde_ntree;
+        if ((S & (S - 1)) == 0) {
+            sde_tree t = {S, 0, {-1, -1, -1}, 1, __builtin_ctz(S)};
+            sde_trees[sde_ntree++] = t;
+        } else {
+            int lo = lowbit(S);
+            /* three-gluon vertex: {A, B}, A holds the lowest leaf */
+            for (int A = (S - 1) & S; A > 0; A = (A - 1) & S) {
+                if (!(A & lo)) continue;
+                int B = S & ~A;
+                for (int a = 0; a < sde_count[A]; ++a)
+                    for (int b = 0; b < sde_count[B]; ++b) {
+                        int ta = sde_first[A] + a, tb = sde_first[B] + b;
+                        sde_tree t = {S, 3, {ta, tb, -1}, sde_trees[ta].nvar * sde_trees[tb].nvar, -1};
+                        sde_trees[sde_ntree++] = t;
+                    }
+            }
+            /* four-gluon vertex: {A, B, C}, A holds the lowest leaf of S, B the
+             * lowest leaf of S \ A */
+            for (int A = (S - 1) & S; A > 0; A = (A - 1) & S) {
+                if (!(A & lo)) continue;
+                int R = S & ~A, lo2 = lowbit(R);
+                for (int B = (R - 1) & R; B > 0; B = (B - 1) & R) {
+                    if (!(B & lo2)) continue;
+                    int C = R & ~B;
+                    for (int a = 0; a < sde_count[A]; ++a)
+                        for (int b = 0; b < sde_count[B]; ++b)
+                            for (int c = 0; c < sde_count[C]; ++c) {
+                                int ta = sde_first[A] + a, tb = sde_first[B] + b, tc = sde_first[C] + c;
+                                sde_tree t = {S, 4, {ta, tb, tc},
+                                              3 * sde_trees[ta].nvar * sde_trees[tb].nvar * sde_trees[tc].nvar, -1};
+                                sde_trees[sde_ntree++] = t;
+                            }
+                }
+            }
+        }
+        sde_count[S] = sde_ntree - sde_first[S];
+    }
+}
+
+static int sde_ext_mask(int proc, int gmask)
+{
+    int m = 0;
+    for (int g = 0; gmask; ++g, gmask >>= 1)
+        if (gmask & 1) m |= 1 << gluon_pos(proc, g);
+    return m;
+}
+
+static void sde_tree_lines(int proc, int t, int *lines, int *n)
+{
+    const sde_tree *T = &sde_trees[t];
+    if (T->kind == 0) return;
+    lines[(*n)++] = sde_ext_mask(proc, T->mask);
+    for (int c = 0; c < (T->kind == 3 ? 2 : 3); ++c) sde_tree_lines(proc, T->child[c], lines, n);
+}
+
+static int cmp_int(const void *a, const void *b) { return *(const int *)a - *(const int *)b; }
+
+static void sde_add_diagram(int proc, int k, const int *seq, int m)
+{
+    sde_diag *D = &sde_diags[k][sde_ndiag[k]++];
+    D->m = m;
+    int n = 0, side = 1 << 2; /* the t side of a quark propagator: t and the gluons before it */
+    for (int i = 0; i < m; ++i) {
+        D->tree[i] = seq[i];
+        sde_tree_lines(proc, seq[i], D->lines, &n);
+        side |= sde_ext_mask(proc, sde_trees[seq[i]].mask);
+        if (i < m - 1) D->lines[n++] = side;
+    }
+    D->nlines = n;
+    qsort(D->lines, n, sizeof(int), cmp_int);
+}
+
+static void sde_sequences(int proc, int k, int remaining, int *seq, int m)
+{
+    if (!remaining) {
+        sde_add_diagram(proc, k, seq, m);
+        return;
+    }
+    for (int A = remaining; A > 0; A = (A - 1) & remaining)
+        for (int a = 0; a < sde_count[A]; ++a) {
+            seq[m] = sde_first[A] + a;
+            sde_sequences(proc, k, remaining & ~A, seq, m + 1);
+        }
+}
+
+static void sde_init(int proc) /* not thread-safe: the tables are rebuilt when k changes */
+{
+    int k = orc_ngluon(proc);
+    if (sde_k == k) return;
+    sde_build_trees(k);
+    sde_ndiag[k] = 0;
+    int seq[MAXG];
+    sde_sequences(proc, k, (1 << k) - 1, seq, 0);
+    sde_k = k;
+}
+
+/* current variants of tree t for the externals eps / P */
+static void sde_current(int t, cx eps[][4], double P[][4], cx cur[][SDE_MAXVAR][4], double PS[][4])
+{
+    const sde_tree *T = &sde_trees[t];
+    if (T->kind == 0) {
+        memcpy(cur[t][0], eps[T->leaf], sizeof(cx) * 4);
+        memcpy(PS[t], P[T->leaf], sizeof(double) * 4);
+        return;
+    }
+    int nc = T->kind == 3 ? 2 : 3;
+    for (int mu = 0; mu < 4; ++mu) {
+        PS[t][mu] = 0;
+        for (int c = 0; c < nc; ++c) PS[t][mu] += PS[T->child[c]][mu];
+    }
+    double inv = 1.0 / mdot(PS[t], PS[t]);
+    int v = 0;
+    if (T->kind == 3) {
+        const int a = T->child[0], b = T->child[1];
+        double ka[4], kb[4];
+        for (int mu = 0; mu < 4; ++mu) { ka[mu] = -PS[a][mu]; kb[mu] = -PS[b][mu]; }
+        for (int va = 0; va < sde_trees[a].nvar; ++va)
+            for (int vb = 0; vb < sde_trees[b].nvar; ++vb, ++v) {
+                cx o[4];
+                v3(cur[a][va], ka, cur[b][vb], kb, o);
+                for (int mu = 0; mu < 4; ++mu) cur[t][v][mu] = inv * o[mu];
+            }
+    } else {
+        const int a = T->child[0], b = T->child[1], c = T->child[2];
+        for (int va = 0; va < sde_trees[a].nvar; ++va)
+            for (int vb = 0; vb < sde_trees[b].nvar; ++vb)
+                for (int vc = 0; vc < sde_trees[c].nvar; ++vc) {
+                    const cx *A = cur[a][va], *B = cur[b][vb], *C = cur[c][vc];
+                    cx ab = cdot(A, B), ac = cdot(A, C), bc = cdot(B, C);
+                    for (int mu = 0; mu < 4; ++mu) {
+                        cur[t][v][mu] = inv * (ac * B[mu] - bc * A[mu]);
+                        cur[t][v + 1][mu] = inv * (ab * C[mu] - bc * A[mu]);
+                        cur[t][v + 2][mu] = inv * (ab * C[mu] - ac * B[mu]);
+                    }
+                    v += 3;
+                }
+    }
+}
+
+/* sum over the variants of diagram D of |amp|^2 (one helicity) */
+static double sde_diagram_w2(const sde_diag *D, cx cur[][SDE_MAXVAR][4], double PS[][4], const cx ubar[4],
+                             const double pt[4], double mt, const cx v[4])
+{
+    int nv = 1;
+    for (int i = 0; i < D->m; ++i) nv *= sde_trees[D->tree[i]].nvar;
+    double w2 = 0;
+    for (int var = 0; var < nv; ++var) {
+        int rem = var;
+        cx U[4];
+        memcpy(U, ubar, sizeof(cx) * 4);
+        double q[4] = {pt[0], pt[1], pt[2], pt[3]};
+        for (int i = 0; i < D->m; ++i) {
+            const int t = D->tree[i], nvt = sde_trees[t].nvar;
+            cx S[4][4], X[4];
+            slash_c(cur[t][rem % nvt], S);
+            rem /= nvt;
+            row_times(U, S, X);
+            if (i < D->m - 1) {
+                for (int mu = 0; mu < 4; ++mu) q[mu] += PS[t][mu];
+                cx Q[4][4];
+                slash_r(q, Q);
+                for (int r = 0; r < 4; ++r) Q[r][r] += mt;
+                row_times(X, Q, U);
+                const double den = mdot(q, q) - mt * mt;
+                for (int c = 0; c < 4; ++c) U[c] /= den;
+            } else {
+                cx a = X[0] * v[0] + X[1] * v[1] + X[2] * v[2] + X[3] * v[3];
+                w2 += creal(a * conj(a));
+            }
+        }
+    }
+    return w2;
+}
+
+/* Per-diagram sum over the given helicities of |amp_d|^2 for one event.
+ * Returns the number of diagrams; lines_out[d * 4 + i] (i < nlines_out[d])
+ * are diagram d's internal-line masks over the external particles (sorted). */
+int orc_sde(int proc, const double *p, double mt, const int *hels, int nh, double *w2_out, int *lines_out,
+            int *nlines_out)
+{
+    init_gamma();
+    if (proc == 0) { /* one diagram: the s-channel photon, line {e-, e+} */
+        double s = 0;
+        for (int i = 0; i < nh; ++i) s += ee_hel(p, hels[i]);
+        w2_out[0] = s;
+        lines_out[0] = 0x3;
+        nlines_out[0] = 1;
+        return 1;
+    }
+    if (proc < 1 || proc > 4) return -1;
+    sde_init(proc);
+    const int k = orc_ngluon(proc), nd = sde_ndiag[k];
+    static __thread cx cur[SDE_MAXTREE][SDE_MAXVAR][4];
+    static __thread double PS[SDE_MAXTREE][4];
+    for (int d = 0; d < nd; ++d) {
+        w2_out[d] = 0;
+        nlines_out[d] = sde_diags[k][d].nlines;
+        for (int i = 0; i < SDE_MAXLINES; ++i) lines_out[d * 4 + i] = i < sde_diags[k][d].nlines ? sde_diags[k][d].lines[i] : 0;
+    }
+    for (int ih = 0; ih < nh; ++ih) {
+        cx eps[MAXG][4], ubar[4], v[4];
+        double P[MAXG][4];
+        qcd_externals(proc, p, mt, hels[ih], -1, eps, P, ubar, v);
+        for (int t = 0; t < sde_ntree; ++t) sde_current(t, eps, P, cur, PS);
+        for (int d = 0; d < nd; ++d) w2_out[d] += sde_diagram_w2(&sde_diags[k][d], cur, PS, ubar, p + 8, mt, v);
+    }
+    return nd;
+}

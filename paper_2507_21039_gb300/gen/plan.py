@@ -75,6 +75,8 @@ class Plan:
     lines: list = field(default_factory=list)
     amps: list = field(default_factory=list)   # (op index, ((col, (re, im)), ...))
     ndiagrams: int = 0
+    amp_diag: list = field(default_factory=list)   # Feynman diagram of each amplitude
+    diag_lines: list = field(default_factory=list)  # internal lines of each diagram (see diagram_lines)
 
     def flops_per_helicity(self) -> int:
         f = sum(FLOPS.get(o.kind, 0) for o in self.ops)
@@ -186,6 +188,15 @@ def build_plan(process: str) -> Plan:
     pidx = D.permutation_index(k)
     terms = D.diagrams(k)
     P.ndiagrams = D.diagram_count(k)
+    # diagram ids in order of first appearance; a four-gluon vertex's colour
+    # structures are amplitudes of one diagram
+    diag_of_term, key_id = [], {}
+    for d in terms:
+        key = _term_lines(d, gluon_ext)
+        if key not in key_id:
+            key_id[key] = len(P.diag_lines)
+            P.diag_lines.append(key)
+        diag_of_term.append(key_id[key])
     # longer diagrams first: their prefixes/suffixes seed the reuse
     order = sorted(range(len(terms)), key=lambda i: (-len(terms[i]), i))
     for di in order:
@@ -212,7 +223,37 @@ def build_plan(process: str) -> Plan:
             R = suffix(d[best + 1:])
             a = add(Op("FFV1_0", (L, Jm, R), -1, out="A"))
         P.amps.append((a, tuple(coeffs)))
+        P.amp_diag.append(diag_of_term[di])
     return P
+
+
+def _term_lines(d, gluon_ext) -> tuple:
+    """Internal lines of a diagram (sequence of gluon trees along the quark line
+    from the t end): each line as the mask of external particles on its side
+    away from the t~ (gluon subtrees: their leaves; quark propagators: the t and
+    the gluons attached before them), sorted.  A tree diagram is fixed by this
+    set of splits."""
+    lines = []
+
+    def tree_lines(t):
+        if t.kind == "leaf":
+            return
+        lines.append(sum(1 << gluon_ext[g] for g in t.leaves))
+        for c in t.children:
+            tree_lines(c)
+
+    side = 1 << 2
+    for j, t in enumerate(d):
+        tree_lines(t)
+        side |= sum(1 << gluon_ext[g] for g in t.leaves)
+        if j < len(d) - 1:
+            lines.append(side)
+    return tuple(sorted(lines))
+
+
+def diagram_lines(P: Plan, d: int) -> tuple:
+    """internal lines of diagram d (masks over the external particles)"""
+    return P.diag_lines[d]
 
 
 def _plan_ee() -> Plan:
@@ -232,6 +273,8 @@ def _plan_ee() -> Plan:
     # i * i * (-i) = i
     P.amps = [(5, ((0, (0, 1)),))]
     P.ndiagrams = 1
+    P.amp_diag = [0]
+    P.diag_lines = [(0b11,)]
     return P
 
 
@@ -266,7 +309,8 @@ def amputate(P: Plan, support: dict) -> Plan:
     external particles.  For each amplitude the split that adds the fewest new
     table variants (2^|support| of a vertex not yet created) is taken; vertex
     objects are shared between amplitudes."""
-    Q = Plan(P.process, P.npar, P.gluon_ext, P.gluon_incoming, P.ncol, [], list(P.lines), [], P.ndiagrams)
+    Q = Plan(P.process, P.npar, P.gluon_ext, P.gluon_incoming, P.ncol, [], list(P.lines), [], P.ndiagrams,
+             list(P.amp_diag), list(P.diag_lines))
     # keep every object of P (the direct amplitude ops go), indices renumbered
     new = {}
     for i, op in enumerate(P.ops):

@@ -102,6 +102,23 @@ def test_interpreter_descriptor_codes_match_kernel():
     assert kinds == list(AMP_KINDS)
 
 
+@pytest.mark.parametrize("k", [2, 3, 4, 5])
+def test_generator_diagrams_are_the_oracle_diagrams(orc, k):
+    """The generator's Feynman diagrams (its amplitudes, grouped by diagram) are
+    exactly the oracle's independently enumerated ones, identified by their
+    internal lines."""
+    from paper_2507_21039_gb300.gen.plan import diagram_lines
+
+    process = {2: "gg_ttx", 3: "gg_ttxg", 4: "gg_ttxgg", 5: "gg_ttxggg"}[k]
+    P = build_plan(process)
+    gen = set(diagram_lines(P, d) for d in range(P.ndiagrams))
+    assert len(gen) == P.ndiagrams == D.diagram_count(k)
+    w = WORKLOADS[process]
+    mom, _, _ = orc.rambo(w.seed, w.sqrt_s, w.masses_final, 0, 1, w.cut_mask, 20.0, 0.4)
+    _, lines = orc.sde(process, mom[0], [0], MT)
+    assert gen == set(lines)
+
+
 def test_generator_flop_counts_positive():
     for p in ("ee_mumu", "gg_ttx", "gg_ttxg", "gg_ttxgg", "gg_ttxggg"):
         P = build_plan(p)

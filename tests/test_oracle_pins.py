@@ -475,3 +475,63 @@ def test_parke_taylor_mhv(orc, name):
     ratios = np.array(ratios)
     assert ratios.size > 0
     assert np.allclose(ratios, 2.0**k, rtol=1e-10)
+
+
+# ---------------------------------------------------------------- diagrams one by one
+@pytest.mark.parametrize("name,count", [("gg_ttx", 3), ("gg_ttxg", 16), ("gg_ttxgg", 123), ("gg_ttxggg", 1240)])
+def test_sde_diagram_counts(orc, name, count):
+    """The paper's diagram counts for g g -> t t~ + 0..3 g (a four-gluon vertex
+    counted once); every diagram is a distinct tree (distinct set of splits)
+    with at most npar - 3 internal lines, none containing the t~."""
+    p = events(orc, name, 1)[0]
+    w2, lines = orc.sde(name, p, [0], MT)
+    assert len(w2) == count and len(set(lines)) == count
+    npar = WORKLOADS[name].npar
+    for key in lines:
+        assert 1 <= len(key) <= npar - 3
+        assert all(0 < m < (1 << npar) and not (m >> 3) & 1 for m in key)
+        assert list(key) == sorted(key)
+
+
+def test_sde_ee_single_diagram_is_the_matrix_element(orc):
+    """e+ e- -> mu+ mu-: one diagram, so its helicity-summed |amp|^2 times the
+    couplings and the spin average is |M|^2 (pinned to the closed form)."""
+    mom = back_to_back(events(orc, "ee_mumu", 64), 0.0)
+    me = orc.me2("ee_mumu", mom)
+    for p, v in zip(mom, me):
+        w2, lines = orc.sde("ee_mumu", p, list(range(16)), 0.0)
+        assert lines == [(0b11,)]
+        assert abs((4 * math.pi * ALPHA_EM) ** 2 * w2[0] / 4 / v - 1) < 1e-13
+
+
+def test_sde_gg_ttx_diagrams_by_traces(orc):
+    """g g -> t t~: each diagram's helicity sum recomputed with the trace
+    technique (top and antitop spins summed as Tr[(pt + m) G (ptb - m) Gbar],
+    no spinors), gluon polarisations summed explicitly."""
+    eye = np.eye(4)
+    for p in events(orc, "gg_ttx", 8):
+        w2, lines = orc.sde("gg_ttx", p, list(range(16)), MT)
+        by = dict(zip(lines, w2))
+        assert set(by) == {(0b011,), (0b101,), (0b110,)}
+        pt, ptb = p[2], p[3]
+        Pt, Pb = slash(pt) + MT * eye, slash(ptb) - MT * eye
+
+        def spin_sum(gam):
+            gbar = G[0] @ gam.conj().T @ G[0]
+            return np.trace(Pt @ gam @ Pb @ gbar).real
+
+        ref = {(0b011,): 0.0, (0b101,): 0.0, (0b110,): 0.0}
+        for l0 in (-1, 1):
+            for l1 in (-1, 1):
+                e0, e1 = orc.polvec(p[0], l0), orc.polvec(p[1], l1)   # incoming gluons: eps
+                for first, second, pin, key in ((e0, e1, p[0], (0b101,)), (e1, e0, p[1], (0b110,))):
+                    q = pt - pin                                      # t side: t + outgoing(-p_in)
+                    gam = slash(first) @ (slash(q) + MT * eye) @ slash(second) / (mdot(q, q) - MT * MT)
+                    ref[key] += spin_sum(gam)
+                k0, k1 = p[0], p[1]                                   # momenta into the three-gluon vertex
+                k3 = -k0 - k1
+                J = (np.dot(MINK @ e0, e1) * (k0 - k1) + e1 * np.dot(MINK @ (k1 - k3), e0)
+                     + e0 * np.dot(MINK @ (k3 - k0), e1)) / mdot(k0 + k1, k0 + k1)
+                ref[(0b011,)] += spin_sum(slash(J))
+        for key in ref:
+            assert abs(by[key] / ref[key] - 1) < 1e-12, (key, by[key], ref[key])
