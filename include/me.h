@@ -134,6 +134,38 @@ int me_sigmakin_hel(me_handle* h, const double* momenta, int64_t nevt, double* m
                     void* cuda_stream);
 
 /*
+ * me_sigmakin_sde -- |M|^2 and the single-diagram-enhancement weight of one
+ * integration channel (Sec. 3.2: MadEvent's multi-channel weights, which the
+ * event-generation interface keeps): for every event
+ *     weight[e] = sum_h |amp_channel|^2 / sum_h sum_d |amp_d|^2,
+ * amp_d the amplitude of Feynman diagram d with bare vertex factors (no
+ * couplings), summed over the handle's kept helicities; the three Lorentz
+ * structures of a four-gluon vertex are amplitudes of one diagram and their
+ * |amp|^2 add.  channel: 0 <= channel < ndiag (me_info), the diagram order of
+ * me_diagram_lines.  me2 as me_sigmakin computes it, except that both mixed
+ * modes evaluate the chain in the precision that carries the weight (FP32 for
+ * ME_PREC_MIXED, FP64 for ME_PREC_MIXED64) with a scalar colour sum.
+ * momenta, me2, weight: device pointers ([nevt][npar][4], [nevt], [nevt]),
+ * owned by the caller.  Filtering as in me_sigmakin.
+ * Errors: ME_EINVAL (bad channel, host pointers), ME_ENOTFILTERED,
+ * ME_ENONFINITE, ME_ENOMEM, ME_ECUDA.
+ */
+int me_sigmakin_sde(me_handle* h, const double* momenta, int64_t nevt, int channel, double* me2, double* weight,
+                    void* cuda_stream);
+
+/*
+ * me_diagram_lines -- identity of Feynman diagram `diagram` (0 <= diagram <
+ * ndiag): its internal lines, each as a mask over the external particles
+ * (bit i = particle i in the order of the momenta) on the side of the line
+ * away from the last particle pair's antifermion (the t~; for e+e- -> mu+mu-
+ * the photon line {e-, e+}), sorted ascending.  A tree diagram is fixed by this
+ * set.  With masks == NULL only *n is set; otherwise cap must be >= *n
+ * (at most npar - 3 lines).  Host-only, no device work.
+ * Errors: ME_EINVAL.
+ */
+int me_diagram_lines(const me_handle* h, int diagram, int* masks, int cap, int* n);
+
+/*
  * me_info -- process sizes.  Any output pointer may be NULL.
  *   good_mask_words: 2 words; bit h of word h/64 set iff helicity h is kept
  *   (all set before filtering).  nhel <= 128.

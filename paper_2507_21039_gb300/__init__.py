@@ -38,9 +38,9 @@ ME_OPT_CHECK_FINITE = 2
 ME_OPT_GAUGE_CHECK = 3
 
 #: symbols declared in include/me.h
-EXPORTS = ("me_init", "me_filter_helicities", "me_filter_helicities_noalloc", "me_sigmakin", "me_sigmakin_hel", "me_info",
-           "me_good_helicities", "me_flops_per_event", "me_set_option", "me_free", "rambo_sample",
-           "me_strerror", "me_version")
+EXPORTS = ("me_init", "me_filter_helicities", "me_filter_helicities_noalloc", "me_sigmakin", "me_sigmakin_hel",
+           "me_sigmakin_sde", "me_diagram_lines", "me_info", "me_good_helicities", "me_flops_per_event",
+           "me_set_option", "me_free", "rambo_sample", "me_strerror", "me_version")
 
 _lock = threading.Lock()
 _lib = None
@@ -72,6 +72,8 @@ def load():
         lib.me_filter_helicities_noalloc.argtypes = [P, P, i64, ctypes.POINTER(i)]
         lib.me_sigmakin.argtypes = [P, P, i64, P, P]
         lib.me_sigmakin_hel.argtypes = [P, P, i64, P, P, P]
+        lib.me_sigmakin_sde.argtypes = [P, P, i64, i, P, P, P]
+        lib.me_diagram_lines.argtypes = [P, i, P, i, ctypes.POINTER(i)]
         lib.me_info.argtypes = [P, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i), P]
         lib.me_good_helicities.argtypes = [P, P, i, ctypes.POINTER(i)]
         lib.me_flops_per_event.argtypes = [P, ctypes.POINTER(d), ctypes.POINTER(d)]
@@ -83,8 +85,9 @@ def load():
         lib.me_strerror.argtypes = [i]
         lib.me_strerror.restype = ctypes.c_char_p
         lib.me_version.restype = ctypes.c_char_p
-        for name in ("me_init", "me_filter_helicities", "me_filter_helicities_noalloc", "me_sigmakin", "me_sigmakin_hel", "me_info",
-                     "me_good_helicities", "me_flops_per_event", "me_set_option", "rambo_sample"):
+        for name in ("me_init", "me_filter_helicities", "me_filter_helicities_noalloc", "me_sigmakin", "me_sigmakin_hel",
+                     "me_sigmakin_sde", "me_diagram_lines", "me_info", "me_good_helicities", "me_flops_per_event",
+                     "me_set_option", "rambo_sample"):
             getattr(lib, name).restype = i
         _lib = lib
         return lib
@@ -202,6 +205,25 @@ def me_sigmakin_hel(h: Handle, momenta, me2, hel_out, stream=None):
     _check(load().me_sigmakin_hel(h.ptr, _ptr(momenta), momenta.shape[0], _ptr(me2), _ptr(hel_out),
                                   _stream(stream)), "me_sigmakin_hel")
     return me2, hel_out
+
+
+def me_sigmakin_sde(h: Handle, momenta, channel, me2=None, weight=None, stream=None):
+    """|M|^2 and the single-diagram-enhancement weight of diagram `channel`
+    (device tensors); returns (me2, weight)."""
+    nevt = momenta.shape[0]
+    me2 = momenta.new_empty((nevt,)) if me2 is None else me2
+    weight = momenta.new_empty((nevt,)) if weight is None else weight
+    _check(load().me_sigmakin_sde(h.ptr, _ptr(momenta), nevt, int(channel), _ptr(me2), _ptr(weight),
+                                  _stream(stream)), "me_sigmakin_sde")
+    return me2, weight
+
+
+def me_diagram_lines(h: Handle, diagram) -> tuple:
+    """internal lines of a Feynman diagram as masks over the external particles"""
+    n = ctypes.c_int()
+    masks = (ctypes.c_int * 8)()
+    _check(load().me_diagram_lines(h.ptr, int(diagram), masks, 8, ctypes.byref(n)), "me_diagram_lines")
+    return tuple(masks[i] for i in range(n.value))
 
 
 def me_info(h: Handle) -> dict:

@@ -93,9 +93,9 @@ __global__ void count_nonfinite(const double* __restrict__ p, long long n, unsig
 }
 
 int launch_me(me_handle* h, int precision, const double* d_mom, int64_t nevt, double* d_me2, double* d_hel_out,
-              const short* d_list, int nlist, cudaStream_t st)
+              const short* d_list, int nlist, cudaStream_t st, double* d_sde_w = nullptr, int sde_channel = 0)
 {
-    LaunchArgs a;
+    LaunchArgs a{};
     a.mom = d_mom;
     a.nevt = nevt;
     a.me2 = d_me2;
@@ -107,6 +107,8 @@ int launch_me(me_handle* h, int precision, const double* d_mom, int64_t nevt, do
     a.mt = h->mt;
     a.gauge_ext = h->gauge_ext;
     a.stream = st;
+    a.sde_w = d_sde_w;
+    a.sde_channel = sde_channel;
     cudaError_t e = h->proc->launch(precision, a);
     return e == cudaSuccess ? ME_OK : ME_ECUDA;
 }
@@ -448,6 +450,39 @@ int me_sigmakin_hel(me_handle* h, const double* momenta, int64_t nevt, double* m
 {
     if (!hel_out) return ME_EINVAL;
     return sigmakin_impl(h, momenta, nevt, me2, hel_out, (cudaStream_t)cuda_stream);
+}
+
+int me_sigmakin_sde(me_handle* h, const double* momenta, int64_t nevt, int channel, double* me2, double* weight,
+                    void* cuda_stream)
+{
+    if (!h || nevt < 0 || channel < 0 || channel >= h->proc->ndiag) return ME_EINVAL;
+    if (nevt == 0) return ME_OK;
+    if (!momenta || !me2 || !weight || !is_device_ptr(momenta) || !is_device_ptr(me2) || !is_device_ptr(weight))
+        return ME_EINVAL;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    if (!h->filtered) {
+        if (h->require_filter) return ME_ENOTFILTERED;
+        if (cudaStreamSynchronize(st) != cudaSuccess) return ME_ECUDA;
+        int rc = me_filter_helicities(h, momenta, nevt, nullptr);
+        if (rc != ME_OK) return rc;
+    }
+    if (h->check_finite) {
+        int rc = check_finite(momenta, nevt * 4 * h->proc->npar, st);
+        if (rc != ME_OK) return rc;
+    }
+    return launch_me(h, h->precision, momenta, nevt, me2, nullptr, h->d_hel, h->ngood, st, weight, channel);
+}
+
+int me_diagram_lines(const me_handle* h, int diagram, int* masks, int cap, int* n)
+{
+    if (!h || !n || diagram < 0 || diagram >= h->proc->ndiag) return ME_EINVAL;
+    const int nl = h->proc->diag_nlines[diagram];
+    *n = nl;
+    if (masks) {
+        if (cap < nl) return ME_EINVAL;
+        for (int i = 0; i < nl; ++i) masks[i] = h->proc->diag_lines[4 * diagram + i];
+    }
+    return ME_OK;
 }
 
 }  // extern "C"

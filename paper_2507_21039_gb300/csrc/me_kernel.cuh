@@ -35,6 +35,24 @@ template <class P, class T> __host__ __device__ constexpr size_t setup_bytes(int
            (size_t)E * P::NLINES * sizeof(Ln<T>);
 }
 
+// Single-diagram enhancement (the multi-channel weight of the paper's event
+// generation): per thread, |x|^2 of every amplitude x into den and of the
+// chosen diagram's amplitudes into num, summed over the thread's helicities.
+// The generated amplitude code calls ME_SDE after each amplitude; it compiles
+// to nothing unless the kernel's SDE flag is set.
+template <class T> struct SdeAcc {
+    T num, den;
+    int chan;
+};
+#define ME_SDE(x, d)                                            \
+    do {                                                        \
+        if constexpr (SDE) {                                    \
+            const auto sde_w2 = fma((x).re, (x).re, (x).im * (x).im); \
+            sde.den += sde_w2;                                  \
+            if ((d) == sde.chan) sde.num += sde_w2;             \
+        }                                                       \
+    } while (0)
+
 // Strided shared-memory accumulator for a per-thread J (column-major over the CTA)
 template <class T, int STRIDE> struct JSmem {
     cx<T>* base;
@@ -120,7 +138,7 @@ template <class P, class T, class C, class JT> __device__ __forceinline__ T colo
 }
 
 // Scalar colour contraction and helicity sum.  T: chain precision, C: colour.
-template <class P, class T, class C = T>
+template <class P, class T, class C = T, bool SDE = false>
 __global__ void __launch_bounds__(P::THREADS) me_kernel_scalar(LaunchArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -155,34 +173,48 @@ __global__ void __launch_bounds__(P::THREADS) me_kernel_scalar(LaunchArgs a)
 
     // (a3-a6) chain, colour sum, helicity accumulation
     const int ev = threadIdx.x / S, slot = threadIdx.x - ev * S;
-    double acc = 0.0;
+    double acc = 0.0, snum = 0.0, sden = 0.0;
     if (ev < ne) {
         const Wf<T>* ext = sext + ev * NPAR * 2;
         const Ln<T>* ln = sln + ev * NL;
         for (int i = slot; i < a.nlist; i += S) {
             const int hel = a.hel_list[i];
+            SdeAcc<T> sde{T(0), T(0), a.sde_channel};
             T v;
             if constexpr (P::J_SMEM) {
                 cx<T>* jb = reinterpret_cast<cx<T>*>(smem + setup_bytes<P, T>(E)) + threadIdx.x;
                 JSmem<T, TH> J{jb};
                 for (int c = 0; c < P::NCOL; ++c) J[c] = {T(0), T(0)};
-                P::template chain<T>(ext, hel, ln, (T)a.mt, J);
+                P::template chain<T, SDE>(ext, hel, ln, (T)a.mt, J, sde);
                 v = colour_as<P, T, C>(J);
             } else {
                 cx<T> J[P::NCOL];
 #pragma unroll
                 for (int c = 0; c < P::NCOL; ++c) J[c] = {T(0), T(0)};
-                P::template chain<T>(ext, hel, ln, (T)a.mt, J);
+                P::template chain<T, SDE>(ext, hel, ln, (T)a.mt, J, sde);
                 v = colour_as<P, T, C>(J);
             }
             acc += (double)v;
+            if constexpr (SDE) {
+                snum += (double)sde.num;
+                sden += (double)sde.den;
+            }
             if (a.hel_out) a.hel_out[(e0 + ev) * a.nlist + i] = (double)v * a.norm;
         }
     }
     // (a6) helicity sum: reduce over the S lanes of each event
-    for (int off = S >> 1; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+    for (int off = S >> 1; off > 0; off >>= 1) {
+        acc += __shfl_xor_sync(0xffffffffu, acc, off);
+        if constexpr (SDE) {
+            snum += __shfl_xor_sync(0xffffffffu, snum, off);
+            sden += __shfl_xor_sync(0xffffffffu, sden, off);
+        }
+    }
     // (a7) normalisation g^{2k} / (IDEN * colour denominator)
-    if (ev < ne && slot == 0) a.me2[e0 + ev] = acc * a.norm;
+    if (ev < ne && slot == 0) {
+        a.me2[e0 + ev] = acc * a.norm;
+        if constexpr (SDE) a.sde_w[e0 + ev] = sden > 0.0 ? snum / sden : 0.0;
+    }
 }
 
 template <class P, class T> size_t scalar_smem_bytes(int E)
@@ -206,16 +238,16 @@ template <class K> cudaError_t ensure_smem(K kernel, size_t bytes, size_t& grant
     return cudaSuccess;
 }
 
-template <class P, class T, class C = T> cudaError_t launch_scalar(const LaunchArgs& a)
+template <class P, class T, class C = T, bool SDE = false> cudaError_t launch_scalar(const LaunchArgs& a)
 {
     const int E = P::THREADS / a.slots;
     const long long grid = (a.nevt + E - 1) / E;
     const size_t smem = scalar_smem_bytes<P, T>(E);
     static size_t granted = 0;  // per instantiation; idempotent if raced
-    cudaError_t e = ensure_smem(me_kernel_scalar<P, T, C>, smem, granted);
+    cudaError_t e = ensure_smem(me_kernel_scalar<P, T, C, SDE>, smem, granted);
     if (e != cudaSuccess) return e;
     if (grid > 0x7fffffffLL) return cudaErrorInvalidValue;
-    me_kernel_scalar<P, T, C><<<(unsigned)grid, P::THREADS, smem, a.stream>>>(a);
+    me_kernel_scalar<P, T, C, SDE><<<(unsigned)grid, P::THREADS, smem, a.stream>>>(a);
     return cudaGetLastError();
 }
 

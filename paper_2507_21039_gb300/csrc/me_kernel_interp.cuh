@@ -74,7 +74,7 @@ __device__ __forceinline__ void run_task(const TabRef<T, TAB>& tab, const Ln<T>*
 }
 
 // TC: colour sum on BF16 tensor cores (T = float); otherwise scalar in C
-template <class P, class T, bool TC, class C = T>
+template <class P, class T, bool TC, class C = T, bool SDE = false>
 __global__ void __launch_bounds__(P::NT) me_kernel_interp(LaunchArgs a, cx<T>* __restrict__ jglobal)
 {
     using L = InterpLayout<P, T>;
@@ -88,6 +88,7 @@ __global__ void __launch_bounds__(P::NT) me_kernel_interp(LaunchArgs a, cx<T>* _
     cx<T>* jp = L::J_IN_SMEM ? reinterpret_cast<cx<T>*>(smem + L::jsm) + threadIdx.x
                              : jglobal + (size_t)blockIdx.x * NCOL * NT + threadIdx.x;
     __shared__ double red[NT / 32];
+    __shared__ double red_sde[SDE ? 2 : 1][NT / 32];
     __shared__ float rowv[NT];
     const int tid = threadIdx.x;
     const bool act = tid < a.nlist;
@@ -113,6 +114,7 @@ __global__ void __launch_bounds__(P::NT) me_kernel_interp(LaunchArgs a, cx<T>* _
         }
         __syncthreads();
         const T mt = (T)a.mt;
+        T snum = T(0), sden = T(0);
         for (int s = 0; s < P::NSTAGE; ++s) {
             const IStage st = P::stage(s);
             for (int r = st.round_begin; r < st.round_end; ++r) {
@@ -142,6 +144,11 @@ __global__ void __launch_bounds__(P::NT) me_kernel_interp(LaunchArgs a, cx<T>* _
                           : d.kind == A_VVVV3_0 ? VVVV3_0<T>(w0, w1, w2, w3) : VVVV4_0<T>(w0, w1, w2, w3);
                     }
                     }
+                }
+                if constexpr (SDE) {  // single-diagram enhancement
+                    const T w2 = fma(x.re, x.re, x.im * x.im);
+                    sden += w2;
+                    if (P::diag(ai) == a.sde_channel) snum += w2;
                 }
                 // every colour coefficient is +-i: J_c += +-i x
                 for (int k = 0; k < d.nterm; ++k, ++term) {
@@ -173,36 +180,59 @@ __global__ void __launch_bounds__(P::NT) me_kernel_interp(LaunchArgs a, cx<T>* _
             }
             v = (T)w;
         }
-        double acc = 0.0;
+        double acc = 0.0, dn = 0.0, dd = 0.0;
         if (act) {
             acc = (double)v;
+            if constexpr (SDE) {
+                dn = (double)snum;
+                dd = (double)sden;
+            }
             if (a.hel_out) a.hel_out[e * a.nlist + tid] = (double)v * a.norm;
         }
-        for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
-        if ((tid & 31) == 0) red[tid >> 5] = acc;
+        for (int off = 16; off > 0; off >>= 1) {
+            acc += __shfl_xor_sync(0xffffffffu, acc, off);
+            if constexpr (SDE) {
+                dn += __shfl_xor_sync(0xffffffffu, dn, off);
+                dd += __shfl_xor_sync(0xffffffffu, dd, off);
+            }
+        }
+        if ((tid & 31) == 0) {
+            red[tid >> 5] = acc;
+            if constexpr (SDE) {
+                red_sde[0][tid >> 5] = dn;
+                red_sde[1][tid >> 5] = dd;
+            }
+        }
         __syncthreads();
         if (tid == 0) {
-            double s = 0.0;
-            for (int w = 0; w < NT / 32; ++w) s += red[w];
+            double s = 0.0, sn = 0.0, sd = 0.0;
+            for (int w = 0; w < NT / 32; ++w) {
+                s += red[w];
+                if constexpr (SDE) {
+                    sn += red_sde[0][w];
+                    sd += red_sde[1][w];
+                }
+            }
             a.me2[e] = s * a.norm;
+            if constexpr (SDE) a.sde_w[e] = sd > 0.0 ? sn / sd : 0.0;
         }
         __syncthreads();
     }
 }
 
-template <class P, class T, bool TC = false, class C = T> cudaError_t launch_interp(const LaunchArgs& a)
+template <class P, class T, bool TC = false, class C = T, bool SDE = false> cudaError_t launch_interp(const LaunchArgs& a)
 {
     using L = InterpLayout<P, T>;
     static_assert(!TC || sizeof(T) == 4, "tensor-core colour sum is the mixed-precision path");
     static_assert(L::bytes <= 232448, "interpreter shared memory exceeds 227 KB");
     if (a.nlist > P::NT) return cudaErrorInvalidValue;
     static size_t granted = 0;
-    cudaError_t e = ensure_smem(me_kernel_interp<P, T, TC, C>, L::bytes, granted);
+    cudaError_t e = ensure_smem(me_kernel_interp<P, T, TC, C, SDE>, L::bytes, granted);
     if (e != cudaSuccess) return e;
     int dev = 0, nsm = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, me_kernel_interp<P, T, TC, C>, P::NT, L::bytes) != cudaSuccess ||
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, me_kernel_interp<P, T, TC, C, SDE>, P::NT, L::bytes) != cudaSuccess ||
         per_sm < 1) {
         cudaGetLastError();
         per_sm = 1;
@@ -214,7 +244,7 @@ template <class P, class T, bool TC = false, class C = T> cudaError_t launch_int
         e = cudaMallocAsync(&jg, sizeof(cx<T>) * (size_t)grid * P::NCOL * P::NT, a.stream);
         if (e != cudaSuccess) return e;
     }
-    me_kernel_interp<P, T, TC, C><<<(unsigned)grid, P::NT, L::bytes, a.stream>>>(a, jg);
+    me_kernel_interp<P, T, TC, C, SDE><<<(unsigned)grid, P::NT, L::bytes, a.stream>>>(a, jg);
     e = cudaGetLastError();
     if (jg) cudaFreeAsync(jg, a.stream);
     return e;

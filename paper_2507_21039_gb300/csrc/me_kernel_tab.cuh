@@ -127,7 +127,7 @@ template <class P, class T> __host__ __device__ constexpr size_t tab_smem_bytes(
 // share instruction-cache lines and overlap each other's long-latency FP64 work.
 template <class P, class T> __host__ __device__ constexpr int tab_epc() { return is_fp64<T>() ? P::EPC_D : P::EPC_F; }
 
-template <class P, class T, bool TC, class C = T>
+template <class P, class T, bool TC, class C = T, bool SDE = false>
 __global__ void __launch_bounds__(P::NT * tab_epc<P, T>(), is_fp64<T>() ? P::MIN_CTAS_D : P::MIN_CTAS_F)
     me_kernel_tab(LaunchArgs a)
 {
@@ -140,6 +140,7 @@ __global__ void __launch_bounds__(P::NT * tab_epc<P, T>(), is_fp64<T>() ? P::MIN
     Ln<T>* sln = reinterpret_cast<Ln<T>*>(smem + tab_line_offset<P, T>());
     const TabRef<T, P::TAB> tab{reinterpret_cast<uint4*>(smem + tab_table_offset<P, T>())};
     __shared__ double red[EPC][NT / 32 > 0 ? NT / 32 : 1];
+    __shared__ double red_sde[SDE ? EPC : 1][2][NT / 32 > 0 ? NT / 32 : 1];
 
     for (long long e0 = (long long)blockIdx.x * EPC; e0 < a.nevt; e0 += (long long)gridDim.x * EPC) {
         const long long e = e0 + grp;
@@ -176,7 +177,7 @@ __global__ void __launch_bounds__(P::NT * tab_epc<P, T>(), is_fp64<T>() ? P::MIN
         // the amplitude code are always reached by every thread.  A staged
         // process computes its table objects stage by stage between its
         // amplitudes, in one pass (nlist <= NT).
-        double acc = 0.0;
+        double acc = 0.0, snum = 0.0, sden = 0.0;
         for (int base = 0; base < a.nlist; base += NT) {
             const int i = base + tid;
             const bool act = live && i < a.nlist;
@@ -184,8 +185,9 @@ __global__ void __launch_bounds__(P::NT * tab_epc<P, T>(), is_fp64<T>() ? P::MIN
             cx<T> J[P::NCOL];
 #pragma unroll
             for (int c = 0; c < P::NCOL; ++c) J[c] = {T(0), T(0)};
-            if constexpr (P::STAGED) P::template staged<T>(tab, sln, (T)a.mt, tid, h, J);
-            else P::template amps<T>(tab, h, sln, J);
+            SdeAcc<T> sde{T(0), T(0), a.sde_channel};
+            if constexpr (P::STAGED) P::template staged<T, SDE>(tab, sln, (T)a.mt, tid, h, J, sde);
+            else P::template amps<T, SDE>(tab, h, sln, J, sde);
             T v;
             if constexpr (TC) {
                 __syncthreads();  // single pass (nlist <= NT): the tables are dead, reuse them as staging
@@ -196,20 +198,46 @@ __global__ void __launch_bounds__(P::NT * tab_epc<P, T>(), is_fp64<T>() ? P::MIN
             }
             if (act) {
                 acc += (double)v;
+                if constexpr (SDE) {
+                    snum += (double)sde.num;
+                    sden += (double)sde.den;
+                }
                 if (a.hel_out) a.hel_out[e * a.nlist + i] = (double)v * a.norm;
             }
         }
-        for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+        for (int off = 16; off > 0; off >>= 1) {
+            acc += __shfl_xor_sync(0xffffffffu, acc, off);
+            if constexpr (SDE) {
+                snum += __shfl_xor_sync(0xffffffffu, snum, off);
+                sden += __shfl_xor_sync(0xffffffffu, sden, off);
+            }
+        }
         if constexpr (NT > 32) {
-            if ((tid & 31) == 0) red[grp][tid >> 5] = acc;
+            if ((tid & 31) == 0) {
+                red[grp][tid >> 5] = acc;
+                if constexpr (SDE) {
+                    red_sde[grp][0][tid >> 5] = snum;
+                    red_sde[grp][1][tid >> 5] = sden;
+                }
+            }
             __syncthreads();
             if (tid == 0 && live) {
-                double s = 0.0;
-                for (int w = 0; w < NT / 32; ++w) s += red[grp][w];
+                double s = 0.0, sn = 0.0, sd = 0.0;
+                for (int w = 0; w < NT / 32; ++w) {
+                    s += red[grp][w];
+                    if constexpr (SDE) {
+                        sn += red_sde[grp][0][w];
+                        sd += red_sde[grp][1][w];
+                    }
+                }
                 a.me2[e] = s * a.norm;
+                if constexpr (SDE) a.sde_w[e] = sd > 0.0 ? sn / sd : 0.0;
             }
         } else {
-            if (tid == 0 && live) a.me2[e] = acc * a.norm;
+            if (tid == 0 && live) {
+                a.me2[e] = acc * a.norm;
+                if constexpr (SDE) a.sde_w[e] = sden > 0.0 ? snum / sden : 0.0;
+            }
         }
         __syncthreads();  // shared memory is reused by the next events
     }
@@ -297,8 +325,9 @@ __global__ void __launch_bounds__(P::NT * P::PPC, P::MIN_CTAS_P) me_kernel_pair(
             cx<f2> J[P::NCOL];
 #pragma unroll
             for (int c = 0; c < P::NCOL; ++c) J[c] = {f2(0), f2(0)};
-            if constexpr (P::STAGED) P::template staged<f2>(tab, sln, f2((float)a.mt), tid, h, J);
-            else P::template amps<f2>(tab, h, sln, J);
+            SdeAcc<f2> sde{f2(0), f2(0), 0};   // unused: the pair kernel computes no enhancement weights
+            if constexpr (P::STAGED) P::template staged<f2, false>(tab, sln, f2((float)a.mt), tid, h, J, sde);
+            else P::template amps<f2, false>(tab, h, sln, J, sde);
             float v0, v1;
             if constexpr (TC) {
                 __syncthreads();  // single pass (nlist <= NT): the tables are dead, reuse them as staging
@@ -366,9 +395,9 @@ template <class P, bool TC> cudaError_t launch_pair(const LaunchArgs& a)
     return cudaGetLastError();
 }
 
-template <class P, class T, bool TC = false, class C = T> cudaError_t launch_tab(const LaunchArgs& a)
+template <class P, class T, bool TC = false, class C = T, bool SDE = false> cudaError_t launch_tab(const LaunchArgs& a)
 {
-    if constexpr (!is_fp64<T>() && std::is_same<C, T>::value && P::PAIR_F) {
+    if constexpr (!is_fp64<T>() && std::is_same<C, T>::value && !SDE && P::PAIR_F) {
         return launch_pair<P, TC>(a);
     } else {
         constexpr int EPC = tab_epc<P, T>();
@@ -378,24 +407,24 @@ template <class P, class T, bool TC = false, class C = T> cudaError_t launch_tab
             static_assert((P::NT / 32) * TcShape<P::NCOL>::WARP_BYTES <= P::TAB * sizeof(Wf<T>),
                           "tensor-core staging must fit in the table region");
         static size_t granted = 0;
-        cudaError_t e = ensure_smem(me_kernel_tab<P, T, TC, C>, smem, granted);
+        cudaError_t e = ensure_smem(me_kernel_tab<P, T, TC, C, SDE>, smem, granted);
         if (e != cudaSuccess) return e;
         const long long ctas = (a.nevt + EPC - 1) / EPC;
         const long long grid = ctas < 0x7fffffffLL ? ctas : 0x7fffffffLL;
-        me_kernel_tab<P, T, TC, C><<<(unsigned)grid, P::NT * EPC, smem, a.stream>>>(a);
+        me_kernel_tab<P, T, TC, C, SDE><<<(unsigned)grid, P::NT * EPC, smem, a.stream>>>(a);
         return cudaGetLastError();
     }
 }
 
 // Mixed precision: FP32 chain; colour sum on BF16 tensor cores for 24 or more
 // colour flows when every thread holds one helicity, FP32 scalar otherwise.
-template <class P, class T, bool TC, class C> cudaError_t launch_interp(const LaunchArgs& a);
+template <class P, class T, bool TC, class C, bool SDE> cudaError_t launch_interp(const LaunchArgs& a);
 
 template <class P> cudaError_t launch_mixed(const LaunchArgs& a)
 {
     if constexpr (P::IS_INTERP) {
-        if constexpr (P::NCOL >= 24) return launch_interp<P, float, true, float>(a);
-        else return launch_interp<P, float, false, float>(a);
+        if constexpr (P::NCOL >= 24) return launch_interp<P, float, true, float, false>(a);
+        else return launch_interp<P, float, false, float, false>(a);
     } else if constexpr (P::IS_TAB) {
         if constexpr (P::NCOL >= 24) {
             if (a.nlist <= P::NT) return launch_tab<P, float, true>(a);

@@ -18,6 +18,8 @@ struct LaunchArgs {
     double mt;              // top mass (0 for massless fermions)
     int gauge_ext;          // -1, or external gluon whose polarisation is replaced by its momentum
     cudaStream_t stream;
+    double* sde_w;          // optional [nevt]: single-diagram-enhancement weight of diagram sde_channel
+    int sde_channel;
 };
 
 enum Precision : int { PREC_FP64 = 0, PREC_FP32 = 1, PREC_MIXED = 2, PREC_MIXED64 = 3 };
@@ -32,6 +34,8 @@ struct ProcDesc {
     long long colour_flops_hel;
     int coupling_power;        // |M|^2 proportional to (4 pi alpha)^coupling_power
     cudaError_t (*launch)(int precision, const LaunchArgs&);
+    const int* diag_lines;     // [ndiag][4] internal-line masks of each diagram (host), 0-padded
+    const int* diag_nlines;    // [ndiag]
 };
 
 const ProcDesc* find_process(const char* name);

@@ -159,6 +159,7 @@ def emit_process(process: str) -> tuple[str, dict]:
     threads = 64 if j_smem else 128
     nlines = len(P.lines)
 
+    diag_of_op = {op: P.amp_diag[n] for n, (op, _) in enumerate(P.amps)}
     body = []
     for i, op in enumerate(P.ops):
         a = [f"w{x}" for x in op.args]
@@ -188,6 +189,7 @@ def emit_process(process: str) -> tuple[str, dict]:
             terms = dict(P.amps)[i]
             for col, c in terms:
                 body.append("  " + _coef_call(col, c, f"w{i}"))
+            body.append(f"  ME_SDE(w{i}, {diag_of_op[i]});")
 
     # colour quadratic form: sum_i Re(conj J_i z_i), z_i = N_ii J_i + sum_{j>i} 2 N_ij J_j
     cbody = []
@@ -253,6 +255,8 @@ __constant__ unsigned short c_line_plus[{nlines}] = {{{", ".join(str(x) for x in
 __constant__ unsigned short c_line_minus[{nlines}] = {{{", ".join(str(x) for x in minus)}}};
 __constant__ unsigned char c_line_kind[{nlines}] = {{{", ".join(str(x) for x in lkind)}}};
 static const int h_cnum[{ncol * ncol}] = {{{cnum_flat}}};
+static const int h_diag_lines[{4 * P.ndiagrams}] = {{{", ".join(str(x) for key in P.diag_lines for x in (list(key) + [0] * (4 - len(key))))}}};
+static const int h_diag_nlines[{P.ndiagrams}] = {{{", ".join(str(len(key)) for key in P.diag_lines)}}};
 {tc_array}
 struct Proc {{
     static constexpr int NPAR = {npar}, NCOL = {ncol}, NLINES = {nlines}, THREADS = {threads};
@@ -265,10 +269,11 @@ struct Proc {{
     __device__ static __forceinline__ unsigned line_minus(int l) {{ return c_line_minus[l]; }}
     __device__ static __forceinline__ unsigned line_kind(int l) {{ return c_line_kind[l]; }}
 
-    template <class T, class JT>
+    template <class T, bool SDE, class JT>
     __device__ static __forceinline__ void chain(const Wf<T>* __restrict__ ext, int hel, const Ln<T>* __restrict__ ln,
-                                                 T mt, JT& J)
+                                                 T mt, JT& J, SdeAcc<T>& sde)
     {{
+        (void)sde;
         (void)mt;
 {chr(10).join("        " + x for x in body)}
     }}
@@ -283,6 +288,11 @@ struct Proc {{
 {tab_src}
 static cudaError_t launch(int precision, const LaunchArgs& a)
 {{
+    if (a.sde_w) {{  // single-diagram-enhancement weights: FP64 or FP32 chain, scalar colour
+        if (precision == PREC_FP64 || precision == PREC_MIXED64)
+            return {launch_fn}<{kernel_struct_d}, double{", false" if (IP or TP) else ""}, double, true>(a);
+        return {launch_fn}<{kernel_struct}, float{", false" if (IP or TP) else ""}, float, true>(a);
+    }}
     switch (precision) {{
     case PREC_FP64: return {launch_fn}<{kernel_struct_d}, double{", false" if IP else ""}>(a);
     case PREC_FP32: return {launch_fn}<{kernel_struct}, float{", false" if IP else ""}>(a);
@@ -298,7 +308,8 @@ const ProcDesc* procdesc_{process}()
 {{
     static const ProcDesc d = {{"{process}", {npar}, {1 << npar}, {ncol}, {P.ndiagrams}, {len(P.amps)}, {k}, {nlines},
                                {threads}, {iden!r}, {den}, {ns}::h_cnum, {flops_hel}LL,
-                               {P.colour_flops_per_helicity()}LL, {cpow}, &{ns}::launch}};
+                               {P.colour_flops_per_helicity()}LL, {cpow}, &{ns}::launch, {ns}::h_diag_lines,
+                               {ns}::h_diag_nlines}};
     return &d;
 }}
 
@@ -357,10 +368,11 @@ def _amp_call(P, ai, addr):
     return f"{op.kind}<T>({args[0]}, {args[1]}, {args[2]}, {args[3]})"
 
 
-def _amp_block(P, ai, terms, addr, n_amp):
+def _amp_block(P, ai, terms, addr, n_amp, diag):
     out = [f"{{ const cx<T> x = {_amp_call(P, ai, addr)};"]
     for col, c in terms:
         out.append(f"  jacc<{c[0]}, {c[1]}, T>(J[{col}], x);")
+    out.append(f"  ME_SDE(x, {diag});")
     out.append("}")
     out.append(f"ME_FENCE(T, {n_amp});")
     return out
@@ -415,7 +427,7 @@ def emit_tab_struct(process: str, nt: int, epc_f: int, epc_d: int, pair: int, am
         addr = lambda a: f"{TP.base[a]} + {_support_name(TP.support[a])}"
         acode = []
         for n_amp, (ai, terms) in enumerate(P.amps):
-            acode += _amp_block(P, ai, terms, addr, n_amp)
+            acode += _amp_block(P, ai, terms, addr, n_amp, P.amp_diag[n_amp])
         used = {TP.support[a] for ai, _ in P.amps for a in P.ops[ai].args}
         body = f"""
     static constexpr bool STAGED = false;
@@ -426,9 +438,11 @@ def emit_tab_struct(process: str, nt: int, epc_f: int, epc_d: int, pair: int, am
 {NL.join("        " + x for x in rounds_code)}
     }}
 
-    template <class T, class JT>
-    __device__ static __forceinline__ void amps(const TabRef<T, TAB>& tab, int h, const Ln<T>* __restrict__ ln, JT& J)
+    template <class T, bool SDE, class JT>
+    __device__ static __forceinline__ void amps(const TabRef<T, TAB>& tab, int h, const Ln<T>* __restrict__ ln, JT& J,
+                                                SdeAcc<T>& sde)
     {{
+        (void)sde;
 {NL.join("        " + x for x in _variant_code(npar, used))}
 {NL.join("        " + x for x in acode)}
     }}"""
@@ -453,18 +467,19 @@ def emit_tab_struct(process: str, nt: int, epc_f: int, epc_d: int, pair: int, am
             code.append("__syncthreads();")
             for ai in st.amps:
                 aop, terms = P.amps[ai]
-                code += _amp_block(P, aop, terms, addr, n_amp)
+                code += _amp_block(P, aop, terms, addr, n_amp, P.amp_diag[ai])
                 n_amp += 1
             code.append("__syncthreads();  // the stage's dead slots are reused by the next one")
         used = {TP.support[a] for ai, _ in P.amps for a in ops[ai].args}
         body = f"""
     static constexpr bool STAGED = true;
     // every stage in order; all threads of the CTA call it (CTA barriers inside)
-    template <class T, class JT>
+    template <class T, bool SDE, class JT>
     __device__ static __forceinline__ void staged(const TabRef<T, TAB>& tab, const Ln<T>* __restrict__ ln, T mt, int tid,
-                                                  int h, JT& J)
+                                                  int h, JT& J, SdeAcc<T>& sde)
     {{
         (void)mt;
+        (void)sde;
 {NL.join("        " + x for x in _variant_code(npar, used))}
 {NL.join("        " + x for x in code)}
     }}"""
@@ -518,7 +533,7 @@ def emit_interp_struct(process: str, nt: int, stage_amps: int, num, amputated: b
     P = T.plan
     npar = P.npar
     ops = P.ops
-    tasks, rounds, stages, amps, terms, stage_term = [], [], [], [], [], []
+    tasks, rounds, stages, amps, terms, stage_term, diags = [], [], [], [], [], [], []
     for st in I.stages:
         r0 = len(rounds)
         for ri, (kind, tl) in enumerate(st.rounds):
@@ -541,6 +556,7 @@ def emit_interp_struct(process: str, nt: int, stage_amps: int, num, amputated: b
                 bases.append(0)
                 sups.append(0)
             la, lb = (op.mom if op.kind == "VVV1_0" else (0, 0))
+            diags.append(P.amp_diag[ai])
             assert len(op.args) <= 4 and len(coefs) < 256 and all(c in ((0, 1), (0, -1)) for _, c in coefs)
             amps.append((bases, sups, AMP_KINDS.index(op.kind), la, lb, len(coefs)))
             for col, c in coefs:
@@ -569,6 +585,7 @@ def emit_interp_struct(process: str, nt: int, stage_amps: int, num, amputated: b
     src += arr("c_stage_term", "int", stage_term, lambda x: "%d" % x, 16)
     src += arr("c_supmask", "unsigned short", masks, lambda x: "%d" % x, 16)
     src += arr("c_cnum2", "short", cnum2, lambda x: "%d" % x, 24)
+    src += arr("c_diag", "unsigned short", diags, lambda x: "%d" % x, 16)
     src += f"""
 // staged evaluation{' with amputated vertex objects' if amputated else ''}: {len(I.stages)} stages of <= {stage_amps} amplitudes, table peak {I.table_size} entries,
 // {len(tasks)} table tasks ({I.table_flops} flops per event), {len(terms)} colour terms
@@ -584,6 +601,7 @@ struct {name} : Proc {{
     __device__ static __forceinline__ int stage_term_begin(int s) {{ return {prefix}c_stage_term[s]; }}
     __device__ static __forceinline__ unsigned support_mask(int s) {{ return {prefix}c_supmask[s]; }}
     __device__ static __forceinline__ int cnum2(int i, int j) {{ return __ldg({prefix}c_cnum2 + i * NCOL + j); }}
+    __device__ static __forceinline__ int diag(int a) {{ return __ldg({prefix}c_diag + a); }}
 }};
 """
     return src, I
