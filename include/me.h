@@ -154,6 +154,36 @@ int me_sigmakin_sde(me_handle* h, const double* momenta, int64_t nevt, int chann
                     void* cuda_stream);
 
 /*
+ * me_sigmakin_hsample -- helicity sampling instead of the helicity sum (the
+ * alternative Sec. 3.1 describes for lockstep execution: here every event
+ * keeps its own helicity, which needs no bunching because the external
+ * states of both helicities are precomputed per event and only indexed).
+ * The kernels are those of me_sigmakin with one helicity per event: the
+ * per-event tables of the larger processes are still built for every
+ * helicity configuration, so sampling saves the amplitude and colour work.
+ * For event e the kept helicity i with cdf[i-1] <= u[e] < cdf[i] is chosen
+ * (cdf the cumulative probabilities, last bin up to 1) and
+ *     me2[e] = |M_h|^2 / p_h,
+ * an unbiased estimator of me_sigmakin's helicity sum; hel[e] = h (the
+ * helicity index, bit npar-1-i of h set = particle i has helicity +1).
+ * Probabilities (me_hsample_probabilities): adaptive by default,
+ * p_i = 0.9 q_i / sum q + 0.1 / ngood with q_i helicity i's mean share of
+ * |M|^2 over the filter's probe events; uniform with ME_OPT_HSAMPLE_UNIFORM.
+ * u: caller's uniforms in [0, 1) (device, [nevt]); me2 [nevt] and hel [nevt]
+ * (may be NULL) on the device.  Filtering as in me_sigmakin.
+ * Errors: ME_EINVAL, ME_ENOTFILTERED, ME_ENONFINITE, ME_ENOMEM, ME_ECUDA.
+ */
+int me_sigmakin_hsample(me_handle* h, const double* momenta, int64_t nevt, const double* u, double* me2, int* hel,
+                        void* cuda_stream);
+
+/*
+ * me_hsample_probabilities -- the helicity-sampling probability of each kept
+ * helicity, in the order of me_good_helicities (p may be NULL: only *n is set;
+ * otherwise cap >= *n).  Errors: ME_EINVAL.
+ */
+int me_hsample_probabilities(const me_handle* h, double* p, int cap, int* n);
+
+/*
  * me_diagram_lines -- identity of Feynman diagram `diagram` (0 <= diagram <
  * ndiag): its internal lines, each as a mask over the external particles
  * (bit i = particle i in the order of the momenta) on the side of the line
@@ -187,6 +217,8 @@ int me_flops_per_event(const me_handle* h, double* chain_flops, double* colour_f
 #define ME_OPT_CHECK_FINITE 2    /* value 1: reject non-finite momenta (one extra pass, synchronous) */
 #define ME_OPT_GAUGE_CHECK 3     /* value = external gluon index: its polarisation is replaced by its
                                     momentum (Ward identity diagnostic); -1 restores normal running */
+#define ME_OPT_HSAMPLE_UNIFORM 4 /* value 1: helicity sampling with uniform probabilities over the kept
+                                    helicities; 0 (default): adaptive (me_sigmakin_hsample) */
 int me_set_option(me_handle* h, int option, int value);
 
 /* me_free -- destroy a handle (NULL is a no-op).  Synchronises its work. */

@@ -31,6 +31,7 @@ ME_PREC_FP64 = 0
 ME_PREC_FP32 = 1
 ME_PREC_MIXED = 2
 ME_PREC_MIXED64 = 3
+ME_OPT_HSAMPLE_UNIFORM = 4
 PRECISIONS = {"fp64": ME_PREC_FP64, "fp32": ME_PREC_FP32, "mixed": ME_PREC_MIXED, "mixed64": ME_PREC_MIXED64}
 
 ME_OPT_REQUIRE_FILTER = 1
@@ -39,7 +40,8 @@ ME_OPT_GAUGE_CHECK = 3
 
 #: symbols declared in include/me.h
 EXPORTS = ("me_init", "me_filter_helicities", "me_filter_helicities_noalloc", "me_sigmakin", "me_sigmakin_hel",
-           "me_sigmakin_sde", "me_diagram_lines", "me_info", "me_good_helicities", "me_flops_per_event",
+           "me_sigmakin_sde", "me_diagram_lines", "me_sigmakin_hsample", "me_hsample_probabilities", "me_info",
+           "me_good_helicities", "me_flops_per_event",
            "me_set_option", "me_free", "rambo_sample", "me_strerror", "me_version")
 
 _lock = threading.Lock()
@@ -74,6 +76,8 @@ def load():
         lib.me_sigmakin_hel.argtypes = [P, P, i64, P, P, P]
         lib.me_sigmakin_sde.argtypes = [P, P, i64, i, P, P, P]
         lib.me_diagram_lines.argtypes = [P, i, P, i, ctypes.POINTER(i)]
+        lib.me_sigmakin_hsample.argtypes = [P, P, i64, P, P, P, P]
+        lib.me_hsample_probabilities.argtypes = [P, P, i, ctypes.POINTER(i)]
         lib.me_info.argtypes = [P, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i), P]
         lib.me_good_helicities.argtypes = [P, P, i, ctypes.POINTER(i)]
         lib.me_flops_per_event.argtypes = [P, ctypes.POINTER(d), ctypes.POINTER(d)]
@@ -86,7 +90,8 @@ def load():
         lib.me_strerror.restype = ctypes.c_char_p
         lib.me_version.restype = ctypes.c_char_p
         for name in ("me_init", "me_filter_helicities", "me_filter_helicities_noalloc", "me_sigmakin", "me_sigmakin_hel",
-                     "me_sigmakin_sde", "me_diagram_lines", "me_info", "me_good_helicities", "me_flops_per_event",
+                     "me_sigmakin_sde", "me_diagram_lines", "me_sigmakin_hsample", "me_hsample_probabilities", "me_info",
+           "me_good_helicities", "me_flops_per_event",
                      "me_set_option", "rambo_sample"):
             getattr(lib, name).restype = i
         _lib = lib
@@ -216,6 +221,26 @@ def me_sigmakin_sde(h: Handle, momenta, channel, me2=None, weight=None, stream=N
     _check(load().me_sigmakin_sde(h.ptr, _ptr(momenta), nevt, int(channel), _ptr(me2), _ptr(weight),
                                   _stream(stream)), "me_sigmakin_sde")
     return me2, weight
+
+
+def me_sigmakin_hsample(h: Handle, momenta, u, me2=None, hel=None, stream=None):
+    """helicity sampling: per event one kept helicity drawn with the uniforms u;
+    returns (me2 = |M_h|^2 / p_h, hel) (device tensors)"""
+    import torch
+
+    nevt = momenta.shape[0]
+    me2 = momenta.new_empty((nevt,)) if me2 is None else me2
+    hel = torch.empty(nevt, dtype=torch.int32, device=momenta.device) if hel is None else hel
+    _check(load().me_sigmakin_hsample(h.ptr, _ptr(momenta), nevt, _ptr(u), _ptr(me2), _ptr(hel), _stream(stream)),
+           "me_sigmakin_hsample")
+    return me2, hel
+
+
+def me_hsample_probabilities(h: Handle) -> list:
+    n = ctypes.c_int()
+    buf = (ctypes.c_double * 128)()
+    _check(load().me_hsample_probabilities(h.ptr, buf, 128, ctypes.byref(n)), "me_hsample_probabilities")
+    return [buf[i] for i in range(n.value)]
 
 
 def me_diagram_lines(h: Handle, diagram) -> tuple:

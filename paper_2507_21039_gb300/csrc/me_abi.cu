@@ -26,6 +26,14 @@ struct me_handle {
     int ngood;
     short good[128];      // host copy of the kept helicities
     short* d_hel;         // device copy
+    // helicity sampling over the kept helicities: probabilities (adaptive:
+    // the filter probe's mean share of each helicity mixed with a uniform
+    // floor; or uniform), their cumulative sums and inverses (host), and the
+    // cumulative sums and inverses on the device (d_hs[0..127], d_hs[128..255])
+    double hs_mean[128];
+    double hs_p[128], hs_cdf[128], hs_invp[128];
+    double* d_hs;
+    int hs_uniform;
     int filtered;
     int require_filter;
     int check_finite;
@@ -61,27 +69,42 @@ int slots_for(int nlist)
     return s;
 }
 
-// per-helicity maximum of |M_h|^2 / |M|^2 over the probe events
+// per helicity, over the probe events: the maximum of |M_h|^2 / |M|^2 into
+// ratio[h] (the filter decision) and its mean into ratio[nhel + h] (the
+// helicity-sampling probabilities)
 __global__ void filter_reduce(const double* __restrict__ hel_out, const double* __restrict__ me2, int nprobe,
                               int nhel, double* __restrict__ ratio)
 {
     const int h = blockIdx.x;
-    double m = 0.0;
+    double m = 0.0, sum = 0.0;
+    int cnt = 0;
     for (int e = threadIdx.x; e < nprobe; e += blockDim.x) {
         const double tot = me2[e];
         if (tot > 0.0 && isfinite(tot)) {
             const double r = hel_out[(long long)e * nhel + h] / tot;
             m = fmax(m, r);
+            sum += r;
+            ++cnt;
         }
     }
-    __shared__ double red[256];
+    __shared__ double red[256], reds[256];
+    __shared__ int redc[256];
     red[threadIdx.x] = m;
+    reds[threadIdx.x] = sum;
+    redc[threadIdx.x] = cnt;
     __syncthreads();
     for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-        if (threadIdx.x < s) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + s]);
+        if (threadIdx.x < s) {
+            red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + s]);
+            reds[threadIdx.x] += reds[threadIdx.x + s];
+            redc[threadIdx.x] += redc[threadIdx.x + s];
+        }
         __syncthreads();
     }
-    if (threadIdx.x == 0) ratio[h] = red[0];
+    if (threadIdx.x == 0) {
+        ratio[h] = red[0];
+        ratio[nhel + h] = redc[0] > 0 ? reds[0] / redc[0] : 0.0;
+    }
 }
 
 __global__ void count_nonfinite(const double* __restrict__ p, long long n, unsigned long long* bad)
@@ -92,8 +115,25 @@ __global__ void count_nonfinite(const double* __restrict__ p, long long n, unsig
     if (local) atomicAdd(bad, local);
 }
 
+// helicity sampling: the kept helicity whose cumulative-probability bin holds
+// u (the smallest i with u < cdf[i]; the last bin takes the rest) and 1 / p
+__global__ void hsample_select(const double* __restrict__ u, long long n, const double* __restrict__ hs, int ngood,
+                               const short* __restrict__ list, short* __restrict__ hel_ev, double* __restrict__ w_ev,
+                               int* __restrict__ hel_out)
+{
+    const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (e >= n) return;
+    const double x = u[e];
+    int i = 0;
+    while (i < ngood - 1 && !(x < hs[i])) ++i;
+    hel_ev[e] = list[i];
+    w_ev[e] = hs[128 + i];
+    if (hel_out) hel_out[e] = list[i];
+}
+
 int launch_me(me_handle* h, int precision, const double* d_mom, int64_t nevt, double* d_me2, double* d_hel_out,
-              const short* d_list, int nlist, cudaStream_t st, double* d_sde_w = nullptr, int sde_channel = 0)
+              const short* d_list, int nlist, cudaStream_t st, double* d_sde_w = nullptr, int sde_channel = 0,
+              const short* d_hel_ev = nullptr, const double* d_w_ev = nullptr)
 {
     LaunchArgs a{};
     a.mom = d_mom;
@@ -109,8 +149,35 @@ int launch_me(me_handle* h, int precision, const double* d_mom, int64_t nevt, do
     a.stream = st;
     a.sde_w = d_sde_w;
     a.sde_channel = sde_channel;
+    a.hel_ev = d_hel_ev;
+    a.w_ev = d_w_ev;
+    if (d_hel_ev) a.slots = 1;
     cudaError_t e = h->proc->launch(precision, a);
     return e == cudaSuccess ? ME_OK : ME_ECUDA;
+}
+
+// Helicity-sampling probabilities over the kept helicities: adaptive,
+// p_i = 0.9 q_i / sum q + 0.1 / ngood with q_i the mean share of helicity i in
+// the filter probe (every kept helicity keeps probability >= 0.1 / ngood, so
+// the estimator stays unbiased with bounded weights); or uniform, 1 / ngood.
+// Cumulative sums are formed left to right in FP64; the last one is 1.
+int set_hsample(me_handle* h)
+{
+    const int n = h->ngood;
+    double q = 0.0;
+    for (int i = 0; i < n; ++i) q += h->hs_mean[h->good[i]];
+    double c = 0.0;
+    for (int i = 0; i < n; ++i) {
+        const double p = (h->hs_uniform || !(q > 0.0)) ? 1.0 / n : 0.9 * h->hs_mean[h->good[i]] / q + 0.1 / n;
+        h->hs_p[i] = p;
+        h->hs_invp[i] = 1.0 / p;
+        c += p;
+        h->hs_cdf[i] = i == n - 1 ? 1.0 : c;
+    }
+    double dev[256] = {};
+    memcpy(dev, h->hs_cdf, sizeof(double) * n);
+    memcpy(dev + 128, h->hs_invp, sizeof(double) * n);
+    return cudaMemcpy(h->d_hs, dev, sizeof dev, cudaMemcpyHostToDevice) == cudaSuccess ? ME_OK : ME_ECUDA;
 }
 
 int set_good(me_handle* h, const short* list, int n)
@@ -118,7 +185,7 @@ int set_good(me_handle* h, const short* list, int n)
     memcpy(h->good, list, sizeof(short) * n);
     h->ngood = n;
     if (cudaMemcpy(h->d_hel, h->good, sizeof(short) * n, cudaMemcpyHostToDevice) != cudaSuccess) return ME_ECUDA;
-    return ME_OK;
+    return set_hsample(h);
 }
 
 // FP64 per-helicity evaluation of the probe events and the filter decision
@@ -133,11 +200,11 @@ int filter_device(me_handle* h, const double* d_mom, int64_t nevt)
     int rc = ME_OK;
     if (cudaMalloc(&d_hel_out, sizeof(double) * (size_t)nprobe * nhel) != cudaSuccess ||
         cudaMalloc(&d_me2, sizeof(double) * nprobe) != cudaSuccess ||
-        cudaMalloc(&d_ratio, sizeof(double) * nhel) != cudaSuccess ||
+        cudaMalloc(&d_ratio, sizeof(double) * 2 * nhel) != cudaSuccess ||
         cudaMalloc(&d_all, sizeof(short) * nhel) != cudaSuccess) {
         rc = ME_ENOMEM;
     }
-    double ratio[128];
+    double ratio[256];
     if (rc == ME_OK && cudaMemcpy(d_all, all, sizeof(short) * nhel, cudaMemcpyHostToDevice) != cudaSuccess)
         rc = ME_ECUDA;
     if (rc == ME_OK) rc = launch_me(h, me::PREC_FP64, d_mom, nprobe, d_me2, d_hel_out, d_all, nhel, 0);
@@ -145,7 +212,7 @@ int filter_device(me_handle* h, const double* d_mom, int64_t nevt)
         filter_reduce<<<nhel, 256>>>(d_hel_out, d_me2, nprobe, nhel, d_ratio);
         if (cudaGetLastError() != cudaSuccess) rc = ME_ECUDA;
     }
-    if (rc == ME_OK && cudaMemcpy(ratio, d_ratio, sizeof(double) * nhel, cudaMemcpyDeviceToHost) != cudaSuccess)
+    if (rc == ME_OK && cudaMemcpy(ratio, d_ratio, sizeof(double) * 2 * nhel, cudaMemcpyDeviceToHost) != cudaSuccess)
         rc = ME_ECUDA;
     cudaFree(d_hel_out);
     cudaFree(d_me2);
@@ -160,6 +227,7 @@ int filter_device(me_handle* h, const double* d_mom, int64_t nevt)
         for (int i = 0; i < nhel; ++i) good[i] = (short)i;
         n = nhel;
     }
+    memcpy(h->hs_mean, ratio + nhel, sizeof(double) * nhel);
     rc = set_good(h, good, n);
     if (rc == ME_OK) h->filtered = 1;
     return rc;
@@ -248,10 +316,16 @@ int me_init(me_handle** hp, const char* process, const double* masses, int nmass
         delete h;
         return ME_ENOMEM;
     }
+    if (cudaMalloc(&h->d_hs, sizeof(double) * 256) != cudaSuccess) {
+        cudaFree(h->d_hel);
+        delete h;
+        return ME_ENOMEM;
+    }
     short all[128];
     for (int i = 0; i < pd->nhel; ++i) all[i] = (short)i;
     if (set_good(h, all, pd->nhel) != ME_OK) {
         cudaFree(h->d_hel);
+        cudaFree(h->d_hs);
         delete h;
         return ME_ECUDA;
     }
@@ -264,6 +338,7 @@ void me_free(me_handle* h)
     if (!h) return;
     cudaDeviceSynchronize();
     cudaFree(h->d_hel);
+    cudaFree(h->d_hs);
     if (h->pipe_ready) {
         for (int i = 0; i < 2; ++i) {
             cudaStreamDestroy(h->pipe[i]);
@@ -280,6 +355,9 @@ int me_set_option(me_handle* h, int option, int value)
     switch (option) {
     case ME_OPT_REQUIRE_FILTER: h->require_filter = value != 0; return ME_OK;
     case ME_OPT_CHECK_FINITE: h->check_finite = value != 0; return ME_OK;
+    case ME_OPT_HSAMPLE_UNIFORM:
+        h->hs_uniform = value != 0;
+        return set_hsample(h);
     case ME_OPT_GAUGE_CHECK:
         if (value < -1 || value >= h->proc->npar) return ME_EINVAL;
         if (value >= 0 && h->proc->ngluon == 0) return ME_EINVAL;
@@ -473,6 +551,53 @@ int me_sigmakin_sde(me_handle* h, const double* momenta, int64_t nevt, int chann
     return launch_me(h, h->precision, momenta, nevt, me2, nullptr, h->d_hel, h->ngood, st, weight, channel);
 }
 
+int me_sigmakin_hsample(me_handle* h, const double* momenta, int64_t nevt, const double* u, double* me2, int* hel,
+                        void* cuda_stream)
+{
+    if (!h || nevt < 0) return ME_EINVAL;
+    if (nevt == 0) return ME_OK;
+    if (!momenta || !u || !me2 || !is_device_ptr(momenta) || !is_device_ptr(u) || !is_device_ptr(me2) ||
+        (hel && !is_device_ptr(hel)))
+        return ME_EINVAL;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    if (!h->filtered) {
+        if (h->require_filter) return ME_ENOTFILTERED;
+        if (cudaStreamSynchronize(st) != cudaSuccess) return ME_ECUDA;
+        int rc = me_filter_helicities(h, momenta, nevt, nullptr);
+        if (rc != ME_OK) return rc;
+    }
+    if (h->check_finite) {
+        int rc = check_finite(momenta, nevt * 4 * h->proc->npar, st);
+        if (rc != ME_OK) return rc;
+    }
+    short* d_hel_ev = nullptr;
+    double* d_w_ev = nullptr;
+    if (cudaMallocAsync(&d_hel_ev, sizeof(short) * nevt, st) != cudaSuccess) return ME_ENOMEM;
+    int rc = ME_OK;
+    if (cudaMallocAsync(&d_w_ev, sizeof(double) * nevt, st) != cudaSuccess) rc = ME_ENOMEM;
+    if (rc == ME_OK) {
+        hsample_select<<<(unsigned)((nevt + 255) / 256), 256, 0, st>>>(u, nevt, h->d_hs, h->ngood, h->d_hel, d_hel_ev,
+                                                                       d_w_ev, hel);
+        if (cudaGetLastError() != cudaSuccess) rc = ME_ECUDA;
+    }
+    if (rc == ME_OK)
+        rc = launch_me(h, h->precision, momenta, nevt, me2, nullptr, h->d_hel, 1, st, nullptr, 0, d_hel_ev, d_w_ev);
+    if (d_hel_ev) cudaFreeAsync(d_hel_ev, st);
+    if (d_w_ev) cudaFreeAsync(d_w_ev, st);
+    return rc;
+}
+
+int me_hsample_probabilities(const me_handle* h, double* p, int cap, int* n)
+{
+    if (!h || !n) return ME_EINVAL;
+    *n = h->ngood;
+    if (p) {
+        if (cap < h->ngood) return ME_EINVAL;
+        memcpy(p, h->hs_p, sizeof(double) * h->ngood);
+    }
+    return ME_OK;
+}
+
 int me_diagram_lines(const me_handle* h, int diagram, int* masks, int cap, int* n)
 {
     if (!h || !n || diagram < 0 || diagram >= h->proc->ndiag) return ME_EINVAL;
@@ -544,7 +669,7 @@ extern "C" int me_filter_helicities_noalloc(me_handle* h, const double* momenta,
     const int nhel = h->nhel;
     const size_t b_hel = align256(sizeof(double) * (size_t)nevt * nhel);
     const size_t b_me2 = align256(sizeof(double) * (size_t)nevt);
-    const size_t b_ratio = align256(sizeof(double) * nhel);
+    const size_t b_ratio = align256(sizeof(double) * 2 * nhel);
     const size_t b_list = align256(sizeof(short) * nhel);
     if ((size_t)nevt > kStaticScratchBytes || b_hel + b_me2 + b_ratio + b_list > kStaticScratchBytes)
         return ME_ETOOLARGE;
@@ -567,8 +692,8 @@ extern "C" int me_filter_helicities_noalloc(me_handle* h, const double* momenta,
     if (rc != ME_OK) return rc;
     filter_reduce<<<nhel, 256>>>(d_hel_out, d_me2, (int)nevt, nhel, d_ratio);
     if (cudaGetLastError() != cudaSuccess) return ME_ECUDA;
-    double ratio[128];
-    if (cudaMemcpy(ratio, d_ratio, sizeof(double) * nhel, cudaMemcpyDeviceToHost) != cudaSuccess) return ME_ECUDA;
+    double ratio[256];
+    if (cudaMemcpy(ratio, d_ratio, sizeof(double) * 2 * nhel, cudaMemcpyDeviceToHost) != cudaSuccess) return ME_ECUDA;
     short good[128];
     int n = 0;
     for (int i = 0; i < nhel; ++i)
@@ -577,6 +702,7 @@ extern "C" int me_filter_helicities_noalloc(me_handle* h, const double* momenta,
         for (int i = 0; i < nhel; ++i) good[i] = (short)i;
         n = nhel;
     }
+    memcpy(h->hs_mean, ratio + nhel, sizeof(double) * nhel);
     rc = set_good(h, good, n);
     if (rc != ME_OK) return rc;
     h->filtered = 1;

@@ -178,7 +178,10 @@ __global__ void __launch_bounds__(P::THREADS) me_kernel_scalar(LaunchArgs a)
         const Wf<T>* ext = sext + ev * NPAR * 2;
         const Ln<T>* ln = sln + ev * NL;
         for (int i = slot; i < a.nlist; i += S) {
-            const int hel = a.hel_list[i];
+            // helicity sampling: one helicity per event (external states of
+            // both helicities are in shared memory, so lanes with different
+            // helicities run the same instructions)
+            const int hel = a.hel_ev ? a.hel_ev[e0 + ev] : a.hel_list[i];
             SdeAcc<T> sde{T(0), T(0), a.sde_channel};
             T v;
             if constexpr (P::J_SMEM) {
@@ -212,7 +215,7 @@ __global__ void __launch_bounds__(P::THREADS) me_kernel_scalar(LaunchArgs a)
     }
     // (a7) normalisation g^{2k} / (IDEN * colour denominator)
     if (ev < ne && slot == 0) {
-        a.me2[e0 + ev] = acc * a.norm;
+        a.me2[e0 + ev] = acc * a.norm * (a.w_ev ? a.w_ev[e0 + ev] : 1.0);
         if constexpr (SDE) a.sde_w[e0 + ev] = sden > 0.0 ? snum / sden : 0.0;
     }
 }

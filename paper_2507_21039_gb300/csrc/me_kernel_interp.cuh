@@ -92,18 +92,21 @@ __global__ void __launch_bounds__(P::NT) me_kernel_interp(LaunchArgs a, cx<T>* _
     __shared__ float rowv[NT];
     const int tid = threadIdx.x;
     const bool act = tid < a.nlist;
-    const int h = a.hel_list[act ? tid : 0];
-    // compressed variant index of every operand support for this helicity
+    // compressed variant index of every operand support for helicity h
     // (support particles in descending order = helicity bits from low to high)
-    for (int s = 0; s < P::NSUP; ++s) {
-        const unsigned m = P::support_mask(s);
-        unsigned v = 0, j = 0;
-        for (int b = 0; b < NPAR; ++b)
-            if ((m >> b) & 1) v |= ((h >> b) & 1) << j++;
-        vsup[s * NT + tid] = (unsigned char)v;
-    }
+    auto variants = [&](int h) {
+        for (int s = 0; s < P::NSUP; ++s) {
+            const unsigned m = P::support_mask(s);
+            unsigned v = 0, j = 0;
+            for (int b = 0; b < NPAR; ++b)
+                if ((m >> b) & 1) v |= ((h >> b) & 1) << j++;
+            vsup[s * NT + tid] = (unsigned char)v;
+        }
+    };
+    if (!a.hel_ev) variants(a.hel_list[act ? tid : 0]);
 
     for (long long e = blockIdx.x; e < a.nevt; e += gridDim.x) {
+        if (a.hel_ev) variants(a.hel_ev[e]);  // helicity sampling: one helicity per event (nlist = 1)
         const double* g = a.mom + e * NPAR * 4;
         for (int i = tid; i < NPAR * 4; i += NT) smom[i] = __ldg(g + i);
         for (int c = 0; c < NCOL; ++c) jp[c * NT] = {T(0), T(0)};
@@ -213,7 +216,7 @@ __global__ void __launch_bounds__(P::NT) me_kernel_interp(LaunchArgs a, cx<T>* _
                     sd += red_sde[1][w];
                 }
             }
-            a.me2[e] = s * a.norm;
+            a.me2[e] = s * a.norm * (a.w_ev ? a.w_ev[e] : 1.0);
             if constexpr (SDE) a.sde_w[e] = sd > 0.0 ? sn / sd : 0.0;
         }
         __syncthreads();

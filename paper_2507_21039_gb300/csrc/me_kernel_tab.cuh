@@ -181,7 +181,8 @@ __global__ void __launch_bounds__(P::NT * tab_epc<P, T>(), is_fp64<T>() ? P::MIN
         for (int base = 0; base < a.nlist; base += NT) {
             const int i = base + tid;
             const bool act = live && i < a.nlist;
-            const int h = a.hel_list[i < a.nlist ? i : 0];
+            // helicity sampling: one helicity per event (nlist = 1)
+            const int h = a.hel_ev ? a.hel_ev[live ? e : 0] : a.hel_list[i < a.nlist ? i : 0];
             cx<T> J[P::NCOL];
 #pragma unroll
             for (int c = 0; c < P::NCOL; ++c) J[c] = {T(0), T(0)};
@@ -230,12 +231,12 @@ __global__ void __launch_bounds__(P::NT * tab_epc<P, T>(), is_fp64<T>() ? P::MIN
                         sd += red_sde[grp][1][w];
                     }
                 }
-                a.me2[e] = s * a.norm;
+                a.me2[e] = s * a.norm * (a.w_ev ? a.w_ev[e] : 1.0);
                 if constexpr (SDE) a.sde_w[e] = sd > 0.0 ? sn / sd : 0.0;
             }
         } else {
             if (tid == 0 && live) {
-                a.me2[e] = acc * a.norm;
+                a.me2[e] = acc * a.norm * (a.w_ev ? a.w_ev[e] : 1.0);
                 if constexpr (SDE) a.sde_w[e] = sden > 0.0 ? snum / sden : 0.0;
             }
         }
@@ -398,8 +399,9 @@ template <class P, bool TC> cudaError_t launch_pair(const LaunchArgs& a)
 template <class P, class T, bool TC = false, class C = T, bool SDE = false> cudaError_t launch_tab(const LaunchArgs& a)
 {
     if constexpr (!is_fp64<T>() && std::is_same<C, T>::value && !SDE && P::PAIR_F) {
-        return launch_pair<P, TC>(a);
-    } else {
+        if (!a.hel_ev) return launch_pair<P, TC>(a);  // the pair kernel shares each helicity between two events
+    }
+    {
         constexpr int EPC = tab_epc<P, T>();
         constexpr size_t smem = tab_smem_bytes<P, T>() * EPC;
         if (P::STAGED && a.nlist > P::NT) return cudaErrorInvalidValue;

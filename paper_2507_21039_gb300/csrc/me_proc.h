@@ -20,6 +20,8 @@ struct LaunchArgs {
     cudaStream_t stream;
     double* sde_w;          // optional [nevt]: single-diagram-enhancement weight of diagram sde_channel
     int sde_channel;
+    const short* hel_ev;    // optional [nevt]: one sampled helicity per event (with nlist = 1, slots = 1)
+    const double* w_ev;     // [nevt] with hel_ev: 1 / probability of the sampled helicity
 };
 
 enum Precision : int { PREC_FP64 = 0, PREC_FP32 = 1, PREC_MIXED = 2, PREC_MIXED64 = 3 };
