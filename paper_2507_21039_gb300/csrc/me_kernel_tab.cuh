@@ -422,13 +422,18 @@ template <class P, class T, bool TC = false, class C = T, bool SDE = false> cuda
 // colour flows when every thread holds one helicity, FP32 scalar otherwise.
 template <class P, class T, bool TC, class C, bool SDE> cudaError_t launch_interp(const LaunchArgs& a);
 
+// Build option ME_MIXED_TC_MIN_NCOL: smallest colour basis whose mixed-precision
+// colour sum runs on the tensor cores (default 24).
+#ifndef ME_MIXED_TC_MIN_NCOL
+#define ME_MIXED_TC_MIN_NCOL 24
+#endif
 template <class P> cudaError_t launch_mixed(const LaunchArgs& a)
 {
     if constexpr (P::IS_INTERP) {
-        if constexpr (P::NCOL >= 24) return launch_interp<P, float, true, float, false>(a);
+        if constexpr (P::NCOL >= ME_MIXED_TC_MIN_NCOL) return launch_interp<P, float, true, float, false>(a);
         else return launch_interp<P, float, false, float, false>(a);
     } else if constexpr (P::IS_TAB) {
-        if constexpr (P::NCOL >= 24) {
+        if constexpr (P::NCOL >= ME_MIXED_TC_MIN_NCOL) {
             if (a.nlist <= P::NT) return launch_tab<P, float, true>(a);
         }
         return launch_tab<P, float, false>(a);

@@ -55,6 +55,7 @@ struct Params {
     double w0;  // massless weight (pi/2)^{n-1} s^{n-2} / ((n-1)!(n-2)!) (2 pi)^{4-3n}
     double ptmin, drmin;
     uint32_t cutmask;
+    int chunk;  // events per warp (a multiple of 32)
     double* mom;
     double* wt;
     unsigned long long* nfail;
@@ -66,10 +67,14 @@ struct Params {
 __device__ bool passes(const double (*k)[4], int n, const Params& a)
 {
     if (!a.cutmask) return true;
-    double eta[kMaxFinal], phi[kMaxFinal];
     for (int i = 0; i < n; ++i) {
         if (!((a.cutmask >> i) & 1)) continue;
         if (!(sqrt(k[i][1] * k[i][1] + k[i][2] * k[i][2]) > a.ptmin)) return false;
+    }
+    if (__popc(a.cutmask) < 2) return true;  // no pairs
+    double eta[kMaxFinal], phi[kMaxFinal];
+    for (int i = 0; i < n; ++i) {
+        if (!((a.cutmask >> i) & 1)) continue;
         const double P = sqrt(k[i][1] * k[i][1] + k[i][2] * k[i][2] + k[i][3] * k[i][3]);
         eta[i] = 0.5 * log((P + k[i][3]) / (P - k[i][3]));
         phi[i] = atan2(k[i][2], k[i][1]);
@@ -157,24 +162,18 @@ __device__ bool rambo_point(const Params& a, long long ev, int attempt, double (
     return true;
 }
 
-__global__ void rambo_kernel(Params a)
+// Each warp generates a contiguous chunk of a.chunk events.  A lane that has
+// finished its event (accepted, Newton failure, or out of attempts) takes the
+// warp's next unstarted event, so lanes do not idle while a neighbour retries a
+// rejected attempt (with one event per lane for the whole kernel, a warp runs as
+// many attempts as its unluckiest lane).  Every attempt's random numbers depend
+// only on (event, attempt), so which lane runs it does not change the result.
+// Chunks of 256 events pay off when pair cuts reject often; without them one
+// event per lane (chunk 32) keeps more warps in flight.
+constexpr int kChunkCut = 256, kChunkPlain = 32;
+
+__device__ void rambo_store(const Params& a, long long i, const double (*k)[4], double w, bool ok)
 {
-    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (i >= a.nevt) return;
-    const long long ev = a.ev0 + i;
-    double k[kMaxFinal][4];
-    double w = 0.0;
-    bool done = false, newton_fail = false;
-    for (int att = 0; att < kMaxAttempts; ++att) {
-        if (!rambo_point(a, ev, att, k, w)) {
-            newton_fail = true;
-            break;
-        }
-        if (passes(k, a.nfin, a)) {
-            done = true;
-            break;
-        }
-    }
     const int npar = a.nfin + 2;
     double* o = a.mom + i * npar * 4;
     const double h = 0.5 * a.sqrt_s;
@@ -182,11 +181,52 @@ __global__ void rambo_kernel(Params a)
     o[4] = h; o[5] = 0.0; o[6] = 0.0; o[7] = -h;
     for (int j = 0; j < a.nfin; ++j)
         for (int mu = 0; mu < 4; ++mu) o[8 + 4 * j + mu] = k[j][mu];
-    if (!done || newton_fail) {
+    if (!ok) {
         w = -1.0;
         if (a.nfail) atomicAdd(a.nfail, 1ULL);
     }
     if (a.wt) a.wt[i] = w;
+}
+
+__global__ void rambo_kernel(Params a)
+{
+    const int lane = threadIdx.x & 31;
+    const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+    const long long c0 = warp * a.chunk;
+    if (c0 >= a.nevt) return;  // the whole warp leaves together
+    const long long c1 = c0 + a.chunk < a.nevt ? c0 + a.chunk : a.nevt;
+    long long i = c0 + lane;   // this lane's event (index into the batch)
+    long long next = c0 + 32;  // the warp's next unstarted event (the same in every lane)
+    int att = 0;
+    for (;;) {
+        const bool active = i < c1;
+        if (!__any_sync(0xffffffffu, active)) break;
+        bool finished = false;
+        if (active) {
+            double k[kMaxFinal][4];
+            double w = 0.0;
+            const bool newton_ok = rambo_point(a, a.ev0 + i, att, k, w);
+            const bool done = newton_ok && passes(k, a.nfin, a);
+            if (done || !newton_ok || att + 1 >= kMaxAttempts) {
+                rambo_store(a, i, k, w, done);
+                finished = true;
+            } else {
+                ++att;
+            }
+        }
+        const unsigned fin = __ballot_sync(0xffffffffu, finished);
+        if (finished) {
+            i = next + __popc(fin & ((1u << lane) - 1u));
+            att = 0;
+        }
+        next += __popc(fin);
+    }
+}
+
+unsigned rambo_blocks(int64_t n, int chunk, int threads)
+{
+    const int64_t warps = (n + chunk - 1) / chunk;
+    return (unsigned)((warps * 32 + threads - 1) / threads);
 }
 
 bool is_dev(const void* p)
@@ -235,6 +275,7 @@ extern "C" int rambo_sample(uint64_t seed, int64_t ev0, int64_t nevt, double sqr
         a.drmin = cuts->drmin;
         a.cutmask = cuts->final_mask & ((1u << n) - 1u);
     }
+    a.chunk = __builtin_popcount(a.cutmask) >= 2 ? kChunkCut : kChunkPlain;
     cudaStream_t st = (cudaStream_t)cuda_stream;
     const bool dev_m = is_dev(momenta_out);
     const bool dev_w = !weights_out || is_dev(weights_out);
@@ -274,7 +315,7 @@ extern "C" int rambo_sample(uint64_t seed, int64_t ev0, int64_t nevt, double sqr
             b.nevt = n;
             b.mom = a.mom + c0 * 4 * npar;
             b.wt = a.wt ? a.wt + c0 : nullptr;
-            rambo_kernel<<<(unsigned)((n + th - 1) / th), th, 0, s2[k & 1]>>>(b);
+            rambo_kernel<<<rambo_blocks(n, a.chunk, th), th, 0, s2[k & 1]>>>(b);
             ok = cudaGetLastError() == cudaSuccess &&
                  cudaMemcpyAsync(reinterpret_cast<char*>(momenta_out) + c0 * per, b.mom, per * n, cudaMemcpyDeviceToHost,
                                  s2[k & 1]) == cudaSuccess;
@@ -299,7 +340,7 @@ extern "C" int rambo_sample(uint64_t seed, int64_t ev0, int64_t nevt, double sqr
             rc = ME_ECUDA;
         }
     } else if (rc == ME_OK) {
-        rambo_kernel<<<(unsigned)((nevt + th - 1) / th), th, 0, st>>>(a);
+        rambo_kernel<<<rambo_blocks(nevt, a.chunk, th), th, 0, st>>>(a);
         if (cudaGetLastError() != cudaSuccess) rc = ME_ECUDA;
         if (rc == ME_OK && !dev_m && cudaMemcpyAsync(momenta_out, d_m, mbytes, cudaMemcpyDeviceToHost, st) != cudaSuccess)
             rc = ME_ECUDA;
