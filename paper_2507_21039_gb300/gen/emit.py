@@ -24,7 +24,7 @@ EXT_KINDS = {"VIN": 0, "VOUT": 1, "FO_U": 2, "FO_V": 3, "FI_U": 4, "FI_V": 5}
 #             amplitudes per stage (0: one resident table),
 #             warp fence every n amplitudes in FP32, FP32x2, FP64)
 # (measured on GB300 over stage sizes, events per CTA and fence intervals)
-TAB_PROCESSES = {"gg_ttxg": (32, 1, 1, 0, 1, 0, 1, 6, 4), "gg_ttxgg": (64, 2, 2, 0, 1, 64, 5, 6, 4)}
+TAB_PROCESSES = {"gg_ttxg": (32, 1, 1, 0, 1, 0, 1, 6, 4), "gg_ttxgg": (64, 2, 2, 0, 1, 120, 7, 6, 4)}
 # processes evaluated with the staged descriptor kernel (me_kernel_interp.cuh)
 # process -> (threads per event, amplitudes per stage and amputated vertex objects
 #             in FP32 / mixed, the same in FP64).  FP32 keeps J in shared memory,
