@@ -535,3 +535,24 @@ def test_sde_gg_ttx_diagrams_by_traces(orc):
                 ref[(0b011,)] += spin_sum(slash(J))
         for key in ref:
             assert abs(by[key] / ref[key] - 1) < 1e-12, (key, by[key], ref[key])
+
+
+# ---------------------------------------------------------------- normalisation
+@pytest.mark.parametrize("name,iden", [("ee_mumu", 4), ("gg_ttx", 256), ("gg_ttxg", 256), ("gg_ttxgg", 512),
+                                       ("gg_ttxggg", 1536)])
+def test_averaging_and_symmetry_factor(orc, name, iden):
+    """Reading R1: |M|^2 is averaged over the incoming spins and colours and
+    divided by the number of orderings of identical final-state gluons.  The
+    factor is counted here from the states themselves (2 helicities per
+    incoming parton, 8 colours per incoming gluon, permutations of the final
+    gluons), and |M|^2 equals the sum over all helicities of the unaveraged
+    per-helicity values divided by it."""
+    w = WORKLOADS[name]
+    incoming_states = 2 * 2 * (1 if name == "ee_mumu" else 8 * 8)
+    final_gluons = max(w.npar - 4, 0) if name != "ee_mumu" else 0
+    counted = incoming_states * math.factorial(final_gluons)
+    assert counted == iden
+    mom = events(orc, name, 3)
+    mt = 0.0 if name == "ee_mumu" else MT
+    me, hel = orc.me2(name, mom, mt=mt, alpha=w.alpha, per_helicity=True)
+    assert np.allclose(me, hel.sum(1) / iden, rtol=1e-15, atol=0)
