@@ -14,8 +14,6 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
-#include "f32x2.cuh"
-
 namespace me {
 
 template <class T> struct cx { T re, im; };
@@ -69,35 +67,6 @@ template <class T> __device__ __forceinline__ Blk<T> sblk(const Wf<T>& V)
     b.s01 = {-(V.c[1].re + V.c[2].im), V.c[2].re - V.c[1].im};   // -V1 + i V2
     b.s10 = {V.c[2].im - V.c[1].re, -(V.c[1].im + V.c[2].re)};   // -V1 - i V2
     return b;
-}
-
-// Packed-FP32x2 forms of the complex helpers: products are grouped into
-// positive and negative parts joined by one subtraction, because the packed
-// instruction set has no negated-operand form (the operations per lane are the
-// same products and sums, in a different order).
-__device__ __forceinline__ cx<f2> operator*(cx<f2> a, cx<f2> b)
-{
-    return {a.re * b.re - a.im * b.im, fma(a.re, b.im, a.im * b.re)};
-}
-__device__ __forceinline__ cx<f2> cfma(cx<f2> a, cx<f2> b, cx<f2> c)
-{
-    return {fma(a.re, b.re, c.re) - a.im * b.im, fma(a.re, b.im, fma(a.im, b.re, c.im))};
-}
-__device__ __forceinline__ cx<f2> mdot(const Wf<f2>& a, const Wf<f2>& b)
-{
-    const cx<f2>*x = a.c, *y = b.c;
-    const f2 pr = fma(x[3].im, y[3].im, fma(x[2].im, y[2].im, fma(x[1].im, y[1].im, x[0].re * y[0].re)));
-    const f2 nr = fma(x[3].re, y[3].re, fma(x[2].re, y[2].re, fma(x[1].re, y[1].re, x[0].im * y[0].im)));
-    const f2 pi = fma(x[0].re, y[0].im, x[0].im * y[0].re);
-    const f2 ni = fma(x[3].re, y[3].im, fma(x[3].im, y[3].re, fma(x[2].re, y[2].im,
-                  fma(x[2].im, y[2].re, fma(x[1].re, y[1].im, x[1].im * y[1].re)))));
-    return {pr - nr, pi - ni};
-}
-__device__ __forceinline__ cx<f2> rdot(const f2* k, const Wf<f2>& a)
-{
-    const f2 nr = fma(k[3], a.c[3].re, fma(k[2], a.c[2].re, k[1] * a.c[1].re));
-    const f2 ni = fma(k[3], a.c[3].im, fma(k[2], a.c[2].im, k[1] * a.c[1].im));
-    return {k[0] * a.c[0].re - nr, k[0] * a.c[0].im - ni};
 }
 
 // ---------------------------------------------------------------------------
@@ -270,15 +239,6 @@ template <class T> __device__ __forceinline__ cx<T> sdot(const Wf<T>& a, const W
     s = cfma(a.c[2], b.c[2], s);
     s = cfma(a.c[3], b.c[3], s);
     return s;
-}
-__device__ __forceinline__ cx<f2> sdot(const Wf<f2>& a, const Wf<f2>& b)
-{
-    const cx<f2>*x = a.c, *y = b.c;
-    const f2 pr = fma(x[3].re, y[3].re, fma(x[2].re, y[2].re, fma(x[1].re, y[1].re, x[0].re * y[0].re)));
-    const f2 nr = fma(x[3].im, y[3].im, fma(x[2].im, y[2].im, fma(x[1].im, y[1].im, x[0].im * y[0].im)));
-    const f2 im = fma(x[3].re, y[3].im, fma(x[3].im, y[3].re, fma(x[2].re, y[2].im, fma(x[2].im, y[2].re,
-                  fma(x[1].re, y[1].im, fma(x[1].im, y[1].re, fma(x[0].re, y[0].im, x[0].im * y[0].re)))))));
-    return {pr - nr, im};
 }
 template <class T> __device__ __forceinline__ cx<T> DOTV(const Wf<T>& a, const Wf<T>& b) { return mdot(a, b); }
 template <class T> __device__ __forceinline__ cx<T> DOTF(const Wf<T>& a, const Wf<T>& b) { return sdot(a, b); }

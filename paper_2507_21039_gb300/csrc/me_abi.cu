@@ -423,7 +423,10 @@ int me_filter_helicities(me_handle* h, const double* momenta, int64_t nevt, int*
 // of the other (copy engines and SMs work at the same time).  The caller's
 // stream orders the call: its earlier work comes first, and it waits for every
 // chunk before the call returns.
-constexpr int64_t kPipeChunk = int64_t(1) << 17;
+#ifndef ME_PIPE_CHUNK_LOG2
+#define ME_PIPE_CHUNK_LOG2 17  // build option: log2 of the events per host-pipeline chunk
+#endif
+constexpr int64_t kPipeChunk = int64_t(1) << ME_PIPE_CHUNK_LOG2;
 
 static int sigmakin_host_pipelined(me_handle* h, const double* momenta, int64_t nevt, double* me2, cudaStream_t st)
 {

@@ -16,7 +16,10 @@ namespace {
 
 constexpr int kMaxFinal = 6;
 constexpr int kMaxAttempts = 1000;
-constexpr int64_t kPipeChunk = int64_t(1) << 17;  // events per chunk of the host-output pipeline
+#ifndef ME_PIPE_CHUNK_LOG2
+#define ME_PIPE_CHUNK_LOG2 17  // build option: log2 of the events per host-output pipeline chunk
+#endif
+constexpr int64_t kPipeChunk = int64_t(1) << ME_PIPE_CHUNK_LOG2;
 
 struct U4 { uint64_t x[4]; };
 

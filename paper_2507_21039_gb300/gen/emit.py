@@ -18,13 +18,12 @@ from .tabplan import build_tabplan
 
 EXT_KINDS = {"VIN": 0, "VOUT": 1, "FO_U": 2, "FO_V": 3, "FI_U": 4, "FI_V": 5}
 # processes evaluated with the helicity-recycled table kernel (me_kernel_tab.cuh)
-# process -> (threads per event, events (event pairs) per CTA in FP32 / mixed,
-#             events per CTA in FP64, FP32 / mixed as packed FP32x2 event pairs,
+# process -> (threads per event, events per CTA in FP32 / mixed, in FP64,
 #             amplitudes as contractions of amputated vertex objects,
 #             amplitudes per stage (0: one resident table),
-#             warp fence every n amplitudes in FP32, FP32x2, FP64)
+#             warp fence every n amplitudes in FP32, in FP64)
 # (measured on GB300 over stage sizes, events per CTA and fence intervals)
-TAB_PROCESSES = {"gg_ttxg": (32, 1, 1, 0, 1, 0, 1, 6, 4), "gg_ttxgg": (64, 2, 2, 0, 1, 120, 7, 6, 4)}
+TAB_PROCESSES = {"gg_ttxg": (32, 1, 1, 1, 0, 1, 4), "gg_ttxgg": (64, 2, 2, 1, 120, 7, 4)}
 # processes evaluated with the staged descriptor kernel (me_kernel_interp.cuh)
 # process -> (threads per event, amplitudes per stage and amputated vertex objects
 #             in FP32 / mixed, the same in FP64).  FP32 keeps J in shared memory,
@@ -48,8 +47,8 @@ def _apply_kernel_overrides():
             dflt = (0, 16, 0, 16, 1)
             INTERP_PROCESSES[proc] = tuple(int(parts[i + 1]) if len(parts) > i + 1 else dflt[i] for i in range(5))
         elif parts[0] == "tab":
-            dflt = (0, 1, 1, 0, 1, 0, 1, 6, 4)
-            TAB_PROCESSES[proc] = tuple(int(parts[i + 1]) if len(parts) > i + 1 else dflt[i] for i in range(9))
+            dflt = (0, 1, 1, 1, 0, 1, 4)
+            TAB_PROCESSES[proc] = tuple(int(parts[i + 1]) if len(parts) > i + 1 else dflt[i] for i in range(7))
 
 
 _apply_kernel_overrides()
@@ -387,8 +386,8 @@ def _variant_code(npar, supports):
     return bits + sups
 
 
-def emit_tab_struct(process: str, nt: int, epc_f: int, epc_d: int, pair: int, amputated: int, stage: int,
-                    fence_f: int, fence_p: int, fence_d: int, ncol: int, nlines: int, colour_body: list):
+def emit_tab_struct(process: str, nt: int, epc_f: int, epc_d: int, amputated: int, stage: int,
+                    fence_f: int, fence_d: int, ncol: int, nlines: int, colour_body: list):
     """ProcTab: task table, table rounds and per-helicity amplitudes.
 
     stage == 0: one resident table (every object, all levels), then the
@@ -485,12 +484,6 @@ def emit_tab_struct(process: str, nt: int, epc_f: int, epc_d: int, pair: int, am
     }}"""
 
     task_init = ",\n    ".join("{%d, %d, %d, %d, %d, %d, %d, 0, 0}" % t for t in tasks)
-    # event-pair kernel: CTAs per SM that its shared memory admits (momenta,
-    # packed line data of 40 bytes, packed table entries of 64 bytes; 1 KB
-    # reserved per CTA), but never a register budget below ~232 per thread
-    # (the packed colour-flow vector alone takes 4 * NCOL registers)
-    pair_bytes = ((2 * npar * 32 + nlines * 40 + 15) // 16 * 16 + (size + 7) // 8 * 8 * 64) * epc_f
-    min_ctas_p = max(1, min(16, (228 * 1024) // (pair_bytes + 1024), 65536 // (nt * epc_f * 232)))
     desc = (f"{'staged (' + str(stage) + ' amplitudes per stage)' if stage else 'resident'}"
             f"{', amputated vertex objects' if amputated else ''}")
     src = f"""
@@ -508,13 +501,10 @@ struct ProcTab : Proc {{
     // register budget: FP32 <= 128 per thread (occupancy bound by shared memory
     // anyway), FP64 <= 255 (its tables are twice as large)
     static constexpr int MIN_CTAS_F = {max(1, 65536 // (nt * epc_f * 128))}, MIN_CTAS_D = {max(1, 65536 // (nt * epc_d * 255))};
-    // FP32 / mixed as packed FP32x2 event pairs (me_kernel_pair), EPC_F pairs per CTA
-    static constexpr bool PAIR_F = {"true" if pair else "false"};
-    static constexpr int PPC = {epc_f}, MIN_CTAS_P = {min_ctas_p};
     static constexpr bool IS_TAB = true, IS_INTERP = false;
     static constexpr long long TABLE_FLOPS = {table_flops}LL, AMP_FLOPS = {TP.amplitude_flops_per_helicity()}LL;
-    // warp fence every n amplitudes (FP32, packed FP32x2, FP64)
-    static constexpr int FENCE_F = {fence_f}, FENCE_P = {fence_p}, FENCE_D = {fence_d};
+    // warp fence every n amplitudes (FP32, FP64)
+    static constexpr int FENCE_F = {fence_f}, FENCE_D = {fence_d};
 {body}
 }};
 """
