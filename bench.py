@@ -51,6 +51,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--small", action="store_true",
+                    help="the small processes (ee -> mu mu, gg -> t t~): HBM GB/s, launch overhead, FP-pipe fraction")
     ap.add_argument("--case", nargs=3, metavar=("WORKLOAD", "PRECISION", "NEVT"),
                     help="profiling case: sample NEVT events, then one warm and one measured me_sigmakin")
     return ap.parse_args()
@@ -164,10 +166,18 @@ def cpu_baseline(name, seconds, rank):
     t = time.perf_counter()
     oracle.me2(name, mom, mt=MT, alpha=w.alpha)
     dt = time.perf_counter() - t
-    return {"value": n / dt, "unit": "events/s", "cores": oracle.max_threads(), "kind": "oracle",
+    # one core, on a sample of about a sixth of the time
+    cores = oracle.max_threads()
+    n1 = int(max(64, min(n, (n / dt) / cores * seconds / 6)))
+    t = time.perf_counter()
+    oracle.me2(name, mom[:n1], mt=MT, alpha=w.alpha, nthreads=1)
+    dt1 = time.perf_counter() - t
+    return {"value": n / dt, "unit": "events/s", "cores": cores, "kind": "oracle",
             "sample": f"first {n} events of the {name} workload (seed {w.seed}), FP64 Berends-Giele "
                       f"colour-ordered recursion + brute-force colour matrix, all helicities, "
-                      f"OpenMP over events; {dt:.1f} s"}
+                      f"OpenMP over events; {dt:.1f} s",
+            "single_core": {"value": n1 / dt1, "unit": "events/s", "cores": 1,
+                            "sample": f"first {n1} events, one thread; {dt1:.1f} s"}}
 
 
 # ------------------------------------------------------------------ arms
@@ -367,6 +377,62 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_small():
+    """ee -> mu mu and gg -> t t~ at their workload sizes: |M|^2 kernel time
+    (CUDA events, momenta resident), HBM GB/s of the algorithmic bytes
+    (32 npar + 8 per event), FP32-pipe fraction of the generator flops, and the
+    launch overhead (host time of a one-event me_sigmakin call against its
+    device time)."""
+    import torch
+
+    import paper_2507_21039_gb300 as me
+    from paper_2507_21039_gb300.workloads import WORKLOADS
+
+    peaks, _ = measured_peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    fp32_peak = N_SM * FP32_LANES_PER_SM * 2 * sm_max * 1e6
+    out = {}
+    for name in ("ee_mumu", "gg_ttx"):
+        w = WORKLOADS[name]
+        masses = [0.0, 0.0] + list(w.masses_final)
+        mom = me.rambo_sample(w.seed, 0, w.nevt, w.sqrt_s, masses, me.cuts_for(name), check=True)
+        for prec in ("fp64", "fp32"):
+            h = me.workload_handle(name, prec)
+            me.me_filter_helicities(h, mom)
+            me2 = me.me_sigmakin(h, mom)
+            s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            s0.record()
+            for _ in range(20):
+                me.me_sigmakin(h, mom, me2)
+            s1.record()
+            torch.cuda.synchronize()
+            t = s0.elapsed_time(s1) / 20 / 1e3
+            chain_f, colour_f = me.me_flops_per_event(h)
+            one, one_out = mom[:1].clone(), me2[:1].clone()
+            for _ in range(50):
+                me.me_sigmakin(h, one, one_out)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for _ in range(1000):
+                me.me_sigmakin(h, one, one_out)
+            torch.cuda.synchronize()
+            host = (time.perf_counter() - t0) / 1000
+            s0.record()
+            for _ in range(1000):
+                me.me_sigmakin(h, one, one_out)
+            s1.record()
+            torch.cuda.synchronize()
+            dev = s0.elapsed_time(s1) / 1000 / 1e3
+            h.close()
+            out[f"{name}/{prec}"] = {
+                "events": w.nevt, "kernel_ms": t * 1e3, "events_per_s": w.nevt / t,
+                "hbm_gb_s": w.nevt * (32 * w.npar + 8) / t / 1e9,
+                "fp32_pipe_fraction": (chain_f + colour_f) * w.nevt / t / fp32_peak,
+                "one_event_call_us": {"host": host * 1e6, "device": dev * 1e6}}
+    print(json.dumps(out))
+
+
 def run_case(name, prec, nevt):
     """Small fixed case for ncu captures: sampler, filter, two |M|^2 launches."""
     import torch
@@ -394,6 +460,8 @@ if __name__ == "__main__":
     a = parse()
     if a.case:
         run_case(a.case[0], a.case[1], int(a.case[2]))
+    elif a.small:
+        run_small()
     elif a.impl == "reference":
         run_reference(a)
     else:

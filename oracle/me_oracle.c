@@ -722,12 +722,13 @@ int orc_me2(int proc, const double *mom, int64_t nevt, double mt, double alpha, 
     init_su3();
     if (proc > 0) colour_matrix_cached(orc_ngluon(proc));
     int npar = orc_npar(proc), nhel = 1 << npar;
+    /* nthreads > 0 limits this call only; the process-wide default stays */
 #ifdef _OPENMP
-    if (nthreads > 0) omp_set_num_threads(nthreads);
+    int nt = nthreads > 0 ? nthreads : omp_get_max_threads();
 #else
     (void)nthreads;
 #endif
-#pragma omp parallel for schedule(dynamic, 4)
+#pragma omp parallel for schedule(dynamic, 4) num_threads(nt)
     for (int64_t e = 0; e < nevt; ++e)
         me2_out[e] = me2_event(proc, mom + (size_t)e * npar * 4, mt, alpha, hel_out ? hel_out + (size_t)e * nhel : NULL);
     return 0;
