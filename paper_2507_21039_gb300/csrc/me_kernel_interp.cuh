@@ -8,11 +8,23 @@
 // level, the table objects its amplitudes need that are not yet resident (into
 // slots freed by objects whose last reader has passed), then every thread
 // evaluates the stage's amplitudes for its helicity from compact descriptors
-// and adds them into its colour-flow vector J.  J lives in shared memory in
-// FP32 and in a global scratch (L2-resident) in FP64, whose tables alone fill
-// shared memory.
+// and adds them into its colour-flow vector J.  Amplitudes with the same colour
+// vector up to a sign form a colour group: their signed sum G is added into J
+// once, by the group's last member.  In FP32, J lives in shared memory (or, as a
+// build option, in tensor memory: one TMEM lane per thread, two columns per
+// flow, updated from per-thread accumulator slots at the end of each colour
+// window, which leaves shared memory to the table so that two CTAs share an
+// SM); in FP64 it lives in a global scratch (L2-resident), whose tables alone
+// fill shared memory.
 #pragma once
 #include "me_kernel_tab.cuh"
+#include "me_tmem.cuh"
+
+// Build option ME_INTERP_J_TMEM: FP32 colour-flow vector in tensor memory (1)
+// or in shared memory (0, measured faster)
+#ifndef ME_INTERP_J_TMEM
+#define ME_INTERP_J_TMEM 0
+#endif
 
 namespace me {
 
@@ -36,6 +48,9 @@ enum IRoutine : unsigned char {
     R_FFV1A_3, R_FFV1A_2, R_FFV1A_1, R_VVV1A_1, R_VVV1A_2, R_VVV1A_3, R_VVVV1A, R_VVVV3A, R_VVVV4A
 };
 enum IAmpKind : unsigned char { A_FFV1_0 = 0, A_VVV1_0, A_VVVV1_0, A_VVVV3_0, A_VVVV4_0, A_DOTV, A_DOTF };
+// IAmp.kind flags above the kind: the amplitude enters its colour group's sum
+// with a minus sign; the amplitude closes a colour window
+constexpr unsigned char AMP_NEG = 0x80, AMP_WINDOW_END = 0x40;
 
 template <class P, class T> struct InterpLayout {
     static constexpr size_t mom = 0;
@@ -43,8 +58,21 @@ template <class P, class T> struct InterpLayout {
     static constexpr size_t vsup = (lines + P::NLINES * sizeof(Ln<T>) + 15) / 16 * 16;
     static constexpr size_t table = (vsup + (size_t)P::NSUP * P::NT + 15) / 16 * 16;
     static constexpr size_t jsm = table + (size_t)P::TAB * sizeof(Wf<T>);
-    static constexpr bool J_IN_SMEM = sizeof(T) == 4;
-    static constexpr size_t bytes = jsm + (J_IN_SMEM ? (size_t)P::NCOL * P::NT * sizeof(cx<T>) : 0);
+    // TMEM: 4 warps = 128 lanes, 2 FP32 columns per flow in a 256-column allocation
+    static constexpr bool J_IN_TMEM = sizeof(T) == 4 && ME_INTERP_J_TMEM && P::NT == 128 && 2 * P::NCOL <= 256 &&
+                                      (2 * P::NCOL) % 16 == 0;
+    static constexpr bool J_IN_SMEM = sizeof(T) == 4 && !J_IN_TMEM;
+    static constexpr uint32_t TMEM_COLS = 256;
+    // J in TMEM: the colour windows' accumulator slots, [slot][thread] FP32 complex
+    static constexpr size_t acc = jsm;
+    static constexpr size_t bytes = jsm + (J_IN_SMEM ? (size_t)P::NCOL * P::NT * sizeof(cx<T>) : 0) +
+                                    (J_IN_TMEM ? (size_t)P::NSLOT * P::NT * sizeof(cx<float>) : 0);
+    // colour sum from TMEM: per warp, J as [flow][lane] FP32 and 32 floats of row
+    // totals, two warps at a time over the (then dead) table
+    static constexpr size_t WJ = (size_t)P::NCOL * 32 * sizeof(cx<float>) + 32 * sizeof(float);
+    // at most 512 / TMEM_COLS CTAs may share an SM: shared memory is requested so
+    // that no third one fits (228 KB per SM, 1 KB reserved per CTA)
+    static constexpr size_t launch_bytes = J_IN_TMEM && bytes < 78 * 1024 ? 78 * 1024 : bytes;
 };
 
 template <class T, int TAB>
@@ -84,14 +112,29 @@ __global__ void __launch_bounds__(P::NT) me_kernel_interp(LaunchArgs a, cx<T>* _
     Ln<T>* sln = reinterpret_cast<Ln<T>*>(smem + L::lines);
     unsigned char* vsup = smem + L::vsup;
     const TabRef<T, P::TAB> tab{reinterpret_cast<uint4*>(smem + L::table)};
-    // this thread's colour-flow vector: J[c] at jp[c * NT]
-    cx<T>* jp = L::J_IN_SMEM ? reinterpret_cast<cx<T>*>(smem + L::jsm) + threadIdx.x
-                             : jglobal + (size_t)blockIdx.x * NCOL * NT + threadIdx.x;
+    // this thread's colour-flow vector: J[c] at jp[c * NT] (shared or global
+    // memory), or TMEM columns 2c, 2c+1 of its lane from tj
+    cx<T>* jp = nullptr;
+    if constexpr (L::J_IN_SMEM) jp = reinterpret_cast<cx<T>*>(smem + L::jsm) + threadIdx.x;
+    else if constexpr (!L::J_IN_TMEM) jp = jglobal + (size_t)blockIdx.x * NCOL * NT + threadIdx.x;
     __shared__ double red[NT / 32];
     __shared__ double red_sde[SDE ? 2 : 1][NT / 32];
     __shared__ float rowv[NT];
+    __shared__ uint32_t tmem_base;
     const int tid = threadIdx.x;
     const bool act = tid < a.nlist;
+    uint32_t tj = 0;
+    if constexpr (L::J_IN_TMEM) {
+        static_assert(2 * L::WJ <= (size_t)P::TAB * sizeof(Wf<T>), "colour staging exceeds the table");
+        if (tid < 32) {
+            tmem_alloc(&tmem_base, L::TMEM_COLS);
+            tmem_relinquish();
+        }
+        tmem_fence_before_sync();
+        __syncthreads();
+        tmem_fence_after_sync();
+        tj = tmem_base + ((uint32_t)(32 * ((tid >> 5) & 3)) << 16);
+    }
     // compressed variant index of every operand support for helicity h
     // (support particles in descending order = helicity bits from low to high)
     auto variants = [&](int h) {
@@ -109,7 +152,11 @@ __global__ void __launch_bounds__(P::NT) me_kernel_interp(LaunchArgs a, cx<T>* _
         if (a.hel_ev) variants(a.hel_ev[e]);  // helicity sampling: one helicity per event (nlist = 1)
         const double* g = a.mom + e * NPAR * 4;
         for (int i = tid; i < NPAR * 4; i += NT) smom[i] = __ldg(g + i);
-        for (int c = 0; c < NCOL; ++c) jp[c * NT] = {T(0), T(0)};
+        if constexpr (L::J_IN_TMEM) {
+            for (int c = 0; c < 2 * NCOL; c += 16) tmem_zero_16(tj + c);
+        } else {
+            for (int c = 0; c < NCOL; ++c) jp[c * NT] = {T(0), T(0)};
+        }
         __syncthreads();
         for (int it = tid; it < 2 * NPAR + NL; it += NT) {
             if (it < 2 * NPAR) tab.st(it, ext_wavefunction<P, T>(smom, it, a.mt, a.gauge_ext));
@@ -118,6 +165,8 @@ __global__ void __launch_bounds__(P::NT) me_kernel_interp(LaunchArgs a, cx<T>* _
         __syncthreads();
         const T mt = (T)a.mt;
         T snum = T(0), sden = T(0);
+        cx<T> G = {T(0), T(0)};  // open colour group: sum of its amplitudes with their signs
+        int win = 0;              // current colour window (J in TMEM)
         for (int s = 0; s < P::NSTAGE; ++s) {
             const IStage st = P::stage(s);
             for (int r = st.round_begin; r < st.round_end; ++r) {
@@ -129,22 +178,23 @@ __global__ void __launch_bounds__(P::NT) me_kernel_interp(LaunchArgs a, cx<T>* _
             int term = P::stage_term_begin(s);
             for (int ai = st.amp_begin; ai < st.amp_end; ++ai) {
                 const IAmp d = P::amp(ai);
+                const int kind = d.kind & 0x3f;
                 const Wf<T> w0 = tab.ld(d.op[0] + vsup[d.sup[0] * NT + tid]);
                 const Wf<T> w1 = tab.ld(d.op[1] + vsup[d.sup[1] * NT + tid]);
                 cx<T> x;
-                if (d.kind == A_DOTV) {         // amputated: two-operand contractions
+                if (kind == A_DOTV) {           // amputated: two-operand contractions
                     x = DOTV<T>(w0, w1);
-                } else if (d.kind == A_DOTF) {
+                } else if (kind == A_DOTF) {
                     x = DOTF<T>(w0, w1);
                 } else {
                     const Wf<T> w2 = tab.ld(d.op[2] + vsup[d.sup[2] * NT + tid]);
-                    switch (d.kind) {
+                    switch (kind) {
                     case A_FFV1_0: x = FFV1_0<T>(w0, w1, w2); break;
                     case A_VVV1_0: x = VVV1_0<T>(w0, sln[d.la].p, w1, sln[d.lb].p, w2); break;
                     default: {
                         const Wf<T> w3 = tab.ld(d.op[3] + vsup[d.sup[3] * NT + tid]);
-                        x = d.kind == A_VVVV1_0 ? VVVV1_0<T>(w0, w1, w2, w3)
-                          : d.kind == A_VVVV3_0 ? VVVV3_0<T>(w0, w1, w2, w3) : VVVV4_0<T>(w0, w1, w2, w3);
+                        x = kind == A_VVVV1_0 ? VVVV1_0<T>(w0, w1, w2, w3)
+                          : kind == A_VVVV3_0 ? VVVV3_0<T>(w0, w1, w2, w3) : VVVV4_0<T>(w0, w1, w2, w3);
                     }
                     }
                 }
@@ -153,35 +203,100 @@ __global__ void __launch_bounds__(P::NT) me_kernel_interp(LaunchArgs a, cx<T>* _
                     sden += w2;
                     if (P::diag(ai) == a.sde_channel) snum += w2;
                 }
-                // every colour coefficient is +-i: J_c += +-i x
-                for (int k = 0; k < d.nterm; ++k, ++term) {
-                    const unsigned short ct = P::term(term);
-                    cx<T>& jc = jp[(ct & 0x7fff) * NT];
-                    const cx<T> j = jc;
-                    jc = (ct & 0x8000) ? cx<T>{j.re + x.im, j.im - x.re} : cx<T>{j.re - x.im, j.im + x.re};
+                if (d.kind & AMP_NEG) { G.re -= x.re; G.im -= x.im; }
+                else { G.re += x.re; G.im += x.im; }
+                // the group's last member: every colour coefficient is +-i, J_c += +-i G
+                if (d.nterm) {
+                    if constexpr (L::J_IN_TMEM) {
+                        // into this window's accumulator slots (first touch assigns)
+                        cx<float>* accp = reinterpret_cast<cx<float>*>(smem + L::acc) + tid;
+                        for (int k = 0; k < d.nterm; ++k, ++term) {
+                            const unsigned short ct = P::sterm(term);
+                            cx<float>& s = accp[(ct & 0x1f) * NT];
+                            const cx<float> x = (ct & 0x8000) ? cx<float>{(float)G.im, -(float)G.re}
+                                                               : cx<float>{-(float)G.im, (float)G.re};
+                            s = (ct & 0x4000) ? x : cx<float>{s.re + x.re, s.im + x.im};
+                        }
+                    } else {
+                        for (int k = 0; k < d.nterm; ++k, ++term) {
+                            const unsigned short ct = P::term(term);
+                            cx<T>& jc = jp[(ct & 0x7fff) * NT];
+                            const cx<T> j = jc;
+                            jc = (ct & 0x8000) ? cx<T>{j.re + G.im, j.im - G.re} : cx<T>{j.re - G.im, j.im + G.re};
+                        }
+                    }
+                    G = {T(0), T(0)};
+                }
+                if constexpr (L::J_IN_TMEM) {
+                    if (d.kind & AMP_WINDOW_END) {  // J += the window's slots, eight flows per TMEM round trip
+                        const cx<float>* accp = reinterpret_cast<const cx<float>*>(smem + L::acc) + tid;
+                        const int f0 = P::wbegin(win), n = P::wbegin(win + 1) - f0;
+                        __syncwarp();  // the TMEM accesses are warp-collective
+                        for (int k0 = 0; k0 < n; k0 += 8) {
+                            uint32_t ad[8], v[16];
+#pragma unroll
+                            for (int q = 0; q < 8; ++q) ad[q] = tj + 2u * (uint32_t)P::wflow(f0 + min(k0 + q, n - 1));
+                            tmem_ld_8x2(ad, v);
+#pragma unroll
+                            for (int q = 0; q < 8; ++q) {
+                                if (k0 + q < n) {  // a short last round repeats its last flow and stores nothing for it
+                                    const cx<float> sl = accp[(k0 + q) * NT];
+                                    tmem_st_2(ad[q], __float_as_uint(__uint_as_float(v[2 * q]) + sl.re),
+                                              __float_as_uint(__uint_as_float(v[2 * q + 1]) + sl.im));
+                                }
+                            }
+                        }
+                        ++win;
+                    }
                 }
             }
             __syncthreads();  // stage done: its dead table slots are reused by the next stage
         }
         // colour quadratic form sum_ij N_ij Re(conj J_i J_j)
         T v = T(0);
-        if constexpr (TC) {
-            v = colour_tc_smem<NCOL, NT, P::NSPLIT>(reinterpret_cast<const cx<float>*>(smem + L::jsm), P::bfrag(),
-                                                    rowv, tid);
-        } else {
+        auto colour_scalar = [&](const cx<T>* jq, int stride) {  // J_c at jq[c * stride], in precision C
             C w = C(0);
             for (int i = 0; i < NCOL; ++i) {
-                const cx<T> ji = jp[i * NT];
+                const cx<T> ji = jq[i * stride];
                 C zr = C(0), zi = C(0);
                 for (int j = i; j < NCOL; ++j) {
                     const C n = (C)P::cnum2(i, j);
-                    const cx<T> jj = jp[j * NT];
+                    const cx<T> jj = jq[j * stride];
                     zr = fma(n, (C)jj.re, zr);
                     zi = fma(n, (C)jj.im, zi);
                 }
                 w = fma((C)ji.re, zr, fma((C)ji.im, zi, w));
             }
-            v = (T)w;
+            return (T)w;
+        };
+        if constexpr (L::J_IN_TMEM) {
+            __syncthreads();  // every warp has finished its amplitudes: the table is dead
+            const int w = tid >> 5, lane = tid & 31;
+            unsigned char* stage = smem + L::table + (size_t)(w & 1) * L::WJ;
+            cx<float>* js = reinterpret_cast<cx<float>*>(stage);
+            for (int r = 0; r < 2; ++r) {   // warps 0, 1 then warps 2, 3
+                if ((w >> 1) == r) {
+                    for (int c = 0; c < 2 * NCOL; c += 16) {
+                        uint32_t q16[16];
+                        tmem_ld_16(tj + c, q16);
+#pragma unroll
+                        for (int q = 0; q < 8; ++q)
+                            js[(c / 2 + q) * 32 + lane] = {__uint_as_float(q16[2 * q]), __uint_as_float(q16[2 * q + 1])};
+                    }
+                    __syncwarp();
+                    if constexpr (TC)
+                        v = colour_tc_smem<NCOL, 32, P::NSPLIT>(
+                            js, P::bfrag(), reinterpret_cast<float*>(stage + (size_t)NCOL * 32 * sizeof(cx<float>)), lane);
+                    else
+                        v = colour_scalar(reinterpret_cast<const cx<T>*>(js) + lane, 32);
+                }
+                __syncthreads();
+            }
+        } else if constexpr (TC) {
+            v = colour_tc_smem<NCOL, NT, P::NSPLIT>(reinterpret_cast<const cx<float>*>(smem + L::jsm), P::bfrag(),
+                                                    rowv, tid);
+        } else {
+            v = colour_scalar(jp, NT);
         }
         double acc = 0.0, dn = 0.0, dd = 0.0;
         if (act) {
@@ -221,33 +336,43 @@ __global__ void __launch_bounds__(P::NT) me_kernel_interp(LaunchArgs a, cx<T>* _
         }
         __syncthreads();
     }
+    if constexpr (L::J_IN_TMEM) {   // every load was waited for; the allocating warp releases the columns
+        tmem_fence_before_sync();
+        __syncthreads();
+        if (tid < 32) {
+            tmem_fence_after_sync();
+            tmem_dealloc(tmem_base, L::TMEM_COLS);
+        }
+    }
 }
 
 template <class P, class T, bool TC = false, class C = T, bool SDE = false> cudaError_t launch_interp(const LaunchArgs& a)
 {
     using L = InterpLayout<P, T>;
     static_assert(!TC || sizeof(T) == 4, "tensor-core colour sum is the mixed-precision path");
-    static_assert(L::bytes <= 232448, "interpreter shared memory exceeds 227 KB");
+    static_assert(L::launch_bytes <= 232448, "interpreter shared memory exceeds 227 KB");
     if (a.nlist > P::NT) return cudaErrorInvalidValue;
     static size_t granted = 0;
-    cudaError_t e = ensure_smem(me_kernel_interp<P, T, TC, C, SDE>, L::bytes, granted);
+    cudaError_t e = ensure_smem(me_kernel_interp<P, T, TC, C, SDE>, L::launch_bytes, granted);
     if (e != cudaSuccess) return e;
     int dev = 0, nsm = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, me_kernel_interp<P, T, TC, C, SDE>, P::NT, L::bytes) != cudaSuccess ||
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, me_kernel_interp<P, T, TC, C, SDE>, P::NT,
+                                                      L::launch_bytes) != cudaSuccess ||
         per_sm < 1) {
         cudaGetLastError();
         per_sm = 1;
     }
+    if (L::J_IN_TMEM && per_sm > (int)(512 / L::TMEM_COLS)) per_sm = 512 / L::TMEM_COLS;
     const long long slots = (long long)nsm * per_sm;  // resident CTAs, persistent over events
     const long long grid = a.nevt < slots ? a.nevt : slots;
     cx<T>* jg = nullptr;
-    if constexpr (!L::J_IN_SMEM) {
+    if constexpr (!L::J_IN_SMEM && !L::J_IN_TMEM) {
         e = cudaMallocAsync(&jg, sizeof(cx<T>) * (size_t)grid * P::NCOL * P::NT, a.stream);
         if (e != cudaSuccess) return e;
     }
-    me_kernel_interp<P, T, TC, C, SDE><<<(unsigned)grid, P::NT, L::bytes, a.stream>>>(a, jg);
+    me_kernel_interp<P, T, TC, C, SDE><<<(unsigned)grid, P::NT, L::launch_bytes, a.stream>>>(a, jg);
     e = cudaGetLastError();
     if (jg) cudaFreeAsync(jg, a.stream);
     return e;

@@ -111,6 +111,12 @@ template <class P, class T> __host__ __device__ constexpr size_t tab_smem_bytes(
 // EPC events share a CTA (NT threads each, own shared-memory region); CTA-wide
 // barriers keep their warps at the same point of the amplitude code, so they
 // share instruction-cache lines and overlap each other's long-latency FP64 work.
+// Build option ME_TAB_TC_FROM_SMEM: tensor-core colour sum from a shared-memory
+// copy of J (1) or from J in registers (0)
+#ifndef ME_TAB_TC_FROM_SMEM
+#define ME_TAB_TC_FROM_SMEM 1
+#endif
+
 template <class P, class T> __host__ __device__ constexpr int tab_epc() { return is_fp64<T>() ? P::EPC_D : P::EPC_F; }
 
 template <class P, class T, bool TC, class C = T, bool SDE = false>
@@ -178,8 +184,23 @@ __global__ void __launch_bounds__(P::NT * tab_epc<P, T>(), is_fp64<T>() ? P::MIN
             T v;
             if constexpr (TC) {
                 __syncthreads();  // single pass (nlist <= NT): the tables are dead, reuse them as staging
+#if ME_TAB_TC_FROM_SMEM
+                // J leaves the registers first ([flow][lane] FP32 per warp), so the
+                // tensor-core phase does not hold it next to its fragments
+                constexpr size_t WJ = (size_t)P::NCOL * 32 * sizeof(cx<float>) + 32 * sizeof(float);
+                static_assert((size_t)(NT / 32) * WJ <= (size_t)P::TAB * sizeof(Wf<T>), "staging exceeds the table");
+                unsigned char* stage = smem + tab_table_offset<P, T>() + (tid >> 5) * WJ;
+                cx<float>* js = reinterpret_cast<cx<float>*>(stage);
+#pragma unroll
+                for (int c = 0; c < P::NCOL; ++c) js[c * 32 + (tid & 31)] = J[c];
+                __syncwarp();
+                v = colour_tc_smem<P::NCOL, 32, P::NSPLIT>(js, P::bfrag(),
+                                                           reinterpret_cast<float*>(stage + (size_t)P::NCOL * 32 * sizeof(cx<float>)),
+                                                           tid & 31);
+#else
                 unsigned char* stage = smem + tab_table_offset<P, T>() + (tid >> 5) * TcShape<P::NCOL>::WARP_BYTES;
                 v = colour_tc_warp<P::NCOL, P::NSPLIT>(J, stage, P::bfrag(), tid & 31);
+#endif
             } else {
                 v = colour_as<P, T, C>(J);
             }

@@ -12,24 +12,25 @@ import math
 import struct
 
 from .colour import colour_matrix
-from .plan import Plan, build_plan
+from .plan import Plan, build_plan, colour_groups
 from .interp import AMP_KINDS, ROUTINES, build_interp
 from .tabplan import build_tabplan
 
 EXT_KINDS = {"VIN": 0, "VOUT": 1, "FO_U": 2, "FO_V": 3, "FI_U": 4, "FI_V": 5}
 # processes evaluated with the helicity-recycled table kernel (me_kernel_tab.cuh)
 # process -> (threads per event, events per CTA in FP32 / mixed, in FP64,
-#             amplitudes as contractions of amputated vertex objects,
-#             amplitudes per stage (0: one resident table),
+#             schedule mode, amplitudes per stage (0: one resident table),
 #             warp fence every n amplitudes in FP32, in FP64)
+# schedule mode: bit 0 = amplitudes as contractions of amputated vertex
+# objects, bit 1 = no colour groups (J updated after every amplitude)
 # (measured on GB300 over stage sizes, events per CTA and fence intervals)
-TAB_PROCESSES = {"gg_ttxg": (32, 1, 1, 1, 0, 1, 4), "gg_ttxgg": (64, 2, 2, 1, 120, 7, 4)}
+TAB_PROCESSES = {"gg_ttxg": (32, 1, 1, 1, 0, 1, 4), "gg_ttxgg": (64, 2, 2, 1, 60, 7, 4)}
 # processes evaluated with the staged descriptor kernel (me_kernel_interp.cuh)
-# process -> (threads per event, amplitudes per stage and amputated vertex objects
-#             in FP32 / mixed, the same in FP64).  FP32 keeps J in shared memory,
-#             so its table must stay small (short stages); FP64 keeps J in a
-#             global scratch and takes the amputated schedule with longer stages.
-INTERP_PROCESSES = {"gg_ttxggg": (128, 16, 0, 16, 1)}
+# process -> (threads per event, amplitudes per stage and schedule mode (as
+#             above) in FP32 / mixed, the same in FP64).  FP32 keeps J in shared
+#             memory, so its table must stay small (short stages); FP64 keeps J in
+#             a global scratch, its table alone fills shared memory.
+INTERP_PROCESSES = {"gg_ttxggg": (128, 16, 0, 16, 0)}
 
 
 def _apply_kernel_overrides():
@@ -211,9 +212,9 @@ def emit_process(process: str) -> tuple[str, dict]:
         tab_src, TP, tab_flops = emit_tab_struct(process, *TAB_PROCESSES[process], ncol, nlines, cbody)
     elif process in INTERP_PROCESSES:
         nt_i, sa, amp_i, sa_d, amp_d = INTERP_PROCESSES[process]
-        tab_src, IP = emit_interp_struct(process, nt_i, sa, num, bool(amp_i))
+        tab_src, IP = emit_interp_struct(process, nt_i, sa, num, amp_i)
         if (sa_d, amp_d) != (sa, amp_i):
-            tab_src += emit_interp_struct(process, nt_i, sa_d, num, bool(amp_d), "ProcInterpD", "d_")[0]
+            tab_src += emit_interp_struct(process, nt_i, sa_d, num, amp_d, "ProcInterpD", "d_")[0]
         else:
             tab_src += "using ProcInterpD = ProcInterp;\n"
         body, cbody = [], []   # the straight-line chain is not used for this process
@@ -222,9 +223,10 @@ def emit_process(process: str) -> tuple[str, dict]:
     launch_fn = "launch_tab" if TP else ("launch_interp" if IP else "launch_scalar")
     nhel_all = 1 << npar
     if TP:
-        flops_hel = TP.amplitude_flops_per_helicity() + -(-tab_flops // nhel_all)
+        flops_hel = TP.amplitude_flops_per_helicity(not TAB_PROCESSES[process][3] & 2) + -(-tab_flops // nhel_all)
     elif IP:
-        flops_hel = IP.tab.amplitude_flops_per_helicity() + -(-IP.table_flops // nhel_all)
+        flops_hel = IP.tab.amplitude_flops_per_helicity(not INTERP_PROCESSES[process][2] & 2) + \
+            -(-IP.table_flops // nhel_all)
     else:
         flops_hel = P.flops_per_helicity()
     tc_members, tc_array = "", ""
@@ -377,6 +379,35 @@ def _amp_block(P, ai, terms, addr, n_amp, diag):
     return out
 
 
+def _group_positions(order, flush):
+    """(first, last) flags of each amplitude of `order` within its colour group
+    (the members of a group are adjacent in `order`; `flush` holds the last
+    member of every group)"""
+    return [(k == 0 or order[k - 1] in flush, a in flush) for k, a in enumerate(order)]
+
+
+def _grouped_amp_block(P, pi, aop, addr, n_amp, diag, sign, first, last, terms):
+    """One amplitude of a colour group: the group sum G = sum_m s_m A_m is
+    opened by the first member and added into J (the group's normalised
+    colour terms) by the last; a group of one adds its own terms directly."""
+    if first and last:
+        return _amp_block(P, aop, P.amps[pi][1], addr, n_amp, diag)
+    out = ["{ cx<T> G;"] if first else []
+    out.append(f"{{ const cx<T> x = {_amp_call(P, aop, addr)};")
+    if first:
+        out.append("  G = x;" if sign > 0 else "  G = cx<T>{-x.re, -x.im};")
+    else:
+        out.append("  G.re += x.re; G.im += x.im;" if sign > 0 else "  G.re -= x.re; G.im -= x.im;")
+    out.append(f"  ME_SDE(x, {diag});")
+    out.append("}")
+    if last:
+        for col, c in terms:
+            out.append(f"jacc<{c[0]}, {c[1]}, T>(J[{col}], G);")
+        out.append("}")
+    out.append(f"ME_FENCE(T, {n_amp});")
+    return out
+
+
 def _variant_code(npar, supports):
     bits = [f"const int b{p} = (h >> {npar - 1 - p}) & 1;" for p in range(npar)]
     sups = []
@@ -413,7 +444,7 @@ def emit_tab_struct(process: str, nt: int, epc_f: int, epc_d: int, amputated: in
                 f"{_table_call(kind)} }}  // {level_note}{kind}")
 
     if stage == 0:
-        TP = build_tabplan(process, bool(amputated))
+        TP = build_tabplan(process, bool(amputated & 1))
         P = TP.plan
         npar = P.npar
         size, table_flops = TP.size, TP.table_flops()
@@ -424,9 +455,15 @@ def emit_tab_struct(process: str, nt: int, epc_f: int, epc_d: int, amputated: in
             prev = r.level
             rounds_code.append(round_code(r.kind, [(t.out, t.ins, t.lines) for t in r.tasks], f"level {r.level}: "))
         addr = lambda a: f"{TP.base[a]} + {_support_name(TP.support[a])}"
+        group_of, sign_of, group_terms, members = colour_groups(P)
+        if amputated & 2:  # no colour groups
+            members = [[a] for a in range(len(P.amps))]
+        order = [a for m in members for a in m]
+        flush = {m[-1]: group_terms[group_of[m[-1]]] for m in members}
         acode = []
-        for n_amp, (ai, terms) in enumerate(P.amps):
-            acode += _amp_block(P, ai, terms, addr, n_amp, P.amp_diag[n_amp])
+        for n_amp, (pi, (first, last)) in enumerate(zip(order, _group_positions(order, flush))):
+            acode += _grouped_amp_block(P, pi, P.amps[pi][0], addr, n_amp, P.amp_diag[pi], sign_of[pi], first, last,
+                                        flush.get(pi, ()))
         used = {TP.support[a] for ai, _ in P.amps for a in P.ops[ai].args}
         body = f"""
     static constexpr bool STAGED = false;
@@ -446,7 +483,7 @@ def emit_tab_struct(process: str, nt: int, epc_f: int, epc_d: int, amputated: in
 {NL.join("        " + x for x in acode)}
     }}"""
     else:
-        I = build_interp(process, stage, bool(amputated))
+        I = build_interp(process, stage, bool(amputated & 1), not amputated & 2)
         TP = I.tab
         P = TP.plan
         npar = P.npar
@@ -457,6 +494,7 @@ def emit_tab_struct(process: str, nt: int, epc_f: int, epc_d: int, amputated: in
         is_obj = lambda x: ops[x].out != "A" and not ops[x].kind.startswith("ext_")
         addr = lambda a: f"{I.slot[a] if is_obj(a) else 2 * ops[a].ext} + {_support_name(TP.support[a])}"
         code, n_amp = [], 0
+        pos = dict(zip(I.amp_order, _group_positions(I.amp_order, I.flush)))
         for si, st in enumerate(I.stages):
             code.append(f"// stage {si}: {sum(len(t) for _, t in st.rounds)} table tasks, {len(st.amps)} amplitudes")
             for ri, (kind, tl) in enumerate(st.rounds):
@@ -465,8 +503,9 @@ def emit_tab_struct(process: str, nt: int, epc_f: int, epc_d: int, amputated: in
                     code.append("__syncthreads();")
             code.append("__syncthreads();")
             for ai in st.amps:
-                aop, terms = P.amps[ai]
-                code += _amp_block(P, aop, terms, addr, n_amp, P.amp_diag[ai])
+                first, last = pos[ai]
+                code += _grouped_amp_block(P, ai, P.amps[ai][0], addr, n_amp, P.amp_diag[ai], I.sign[ai], first, last,
+                                           I.flush.get(ai, ()))
                 n_amp += 1
             code.append("__syncthreads();  // the stage's dead slots are reused by the next one")
         used = {TP.support[a] for ai, _ in P.amps for a in ops[ai].args}
@@ -485,14 +524,14 @@ def emit_tab_struct(process: str, nt: int, epc_f: int, epc_d: int, amputated: in
 
     task_init = ",\n    ".join("{%d, %d, %d, %d, %d, %d, %d, 0, 0}" % t for t in tasks)
     desc = (f"{'staged (' + str(stage) + ' amplitudes per stage)' if stage else 'resident'}"
-            f"{', amputated vertex objects' if amputated else ''}")
+            f"{', amputated vertex objects' if amputated & 1 else ''}{'' if amputated & 2 else ', colour groups'}")
     src = f"""
 __device__ const TabTask c_tasks[{max(len(tasks), 1)}] = {{
     {task_init if tasks else "{0, 0, 0, 0, 0, 0, 0, 0, 0}"}
 }};
 
 // helicity-recycled evaluation, {desc}: {size} table entries, {len(tasks)} table tasks,
-// {table_flops} table flops per event, {TP.amplitude_flops_per_helicity()} amplitude flops per helicity
+// {table_flops} table flops per event, {TP.amplitude_flops_per_helicity(not amputated & 2)} amplitude flops per helicity
 struct ProcTab : Proc {{
     static constexpr int NT = {nt}, TAB = {(size + 7) // 8 * 8};
     // events per CTA (own shared-memory region each; CTA barriers keep their
@@ -502,7 +541,7 @@ struct ProcTab : Proc {{
     // anyway), FP64 <= 255 (its tables are twice as large)
     static constexpr int MIN_CTAS_F = {max(1, 65536 // (nt * epc_f * 128))}, MIN_CTAS_D = {max(1, 65536 // (nt * epc_d * 255))};
     static constexpr bool IS_TAB = true, IS_INTERP = false;
-    static constexpr long long TABLE_FLOPS = {table_flops}LL, AMP_FLOPS = {TP.amplitude_flops_per_helicity()}LL;
+    static constexpr long long TABLE_FLOPS = {table_flops}LL, AMP_FLOPS = {TP.amplitude_flops_per_helicity(not amputated & 2)}LL;
     // warp fence every n amplitudes (FP32, FP64)
     static constexpr int FENCE_F = {fence_f}, FENCE_D = {fence_d};
 {body}
@@ -514,16 +553,44 @@ struct ProcTab : Proc {{
 NL = "\n"
 
 
-def emit_interp_struct(process: str, nt: int, stage_amps: int, num, amputated: bool = False,
+# accumulator slots per thread for the colour windows of the staged descriptor
+# kernel (shared memory: ACC_SLOTS x 8 B per thread)
+ACC_SLOTS = 24
+
+
+def emit_interp_struct(process: str, nt: int, stage_amps: int, num, mode: int = 0,
                        name: str = "ProcInterp", prefix: str = ""):
     """ProcInterp: staged table tasks, amplitude descriptors, colour terms
     (arrays named with `prefix`, struct `name`)."""
-    I = build_interp(process, stage_amps, amputated)
+    amputated = bool(mode & 1)
+    I = build_interp(process, stage_amps, amputated, not mode & 2)
     T = I.tab
     P = T.plan
     npar = P.npar
     ops = P.ops
     tasks, rounds, stages, amps, terms, stage_term, diags = [], [], [], [], [], [], []
+    # colour windows (J in tensor memory): consecutive group updates that touch
+    # at most ACC_SLOTS distinct flows go to per-thread accumulator slots; the
+    # last update of a window adds the slots into J.  A window closes before
+    # the update that would exceed the slots.
+    wend, wflows, cur = set(), [], []
+    last_flush = None
+    for ai in I.amp_order:
+        if ai in I.flush:
+            fl = [f for f, _ in I.flush[ai]]
+            assert len(fl) <= ACC_SLOTS
+            if len(set(cur) | set(fl)) > ACC_SLOTS:
+                wend.add(last_flush)
+                wflows.append(cur)
+                cur = []
+            cur += [f for f in fl if f not in cur]
+            last_flush = ai
+    wend.add(last_flush)
+    wflows.append(cur)
+    wbegin = [0]
+    for w in wflows:
+        wbegin.append(wbegin[-1] + len(w))
+    sterms, wi, assigned = [], 0, set()
     for st in I.stages:
         r0 = len(rounds)
         for ri, (kind, tl) in enumerate(st.rounds):
@@ -547,10 +614,21 @@ def emit_interp_struct(process: str, nt: int, stage_amps: int, num, amputated: b
                 sups.append(0)
             la, lb = (op.mom if op.kind == "VVV1_0" else (0, 0))
             diags.append(P.amp_diag[ai])
-            assert len(op.args) <= 4 and len(coefs) < 256 and all(c in ((0, 1), (0, -1)) for _, c in coefs)
-            amps.append((bases, sups, AMP_KINDS.index(op.kind), la, lb, len(coefs)))
-            for col, c in coefs:
+            # colour group: the amplitude enters the group sum with its sign
+            # (kind bit 7 = minus); the group's last member carries the terms
+            gterms = I.flush.get(ai, ())
+            assert len(op.args) <= 4 and len(gterms) < 256 and all(c in ((0, 1), (0, -1)) for _, c in coefs + gterms)
+            kind = AMP_KINDS.index(op.kind) | (0x80 if I.sign[ai] < 0 else 0) | (0x40 if ai in wend else 0)
+            amps.append((bases, sups, kind, la, lb, len(gterms)))
+            for col, c in gterms:
                 terms.append(col | (0x8000 if c == (0, -1) else 0))
+                # the same term as (slot of the flow in its window, assign on first touch, sign)
+                slot = wflows[wi].index(col)
+                sterms.append(slot | (0x4000 if slot not in assigned else 0) | (0x8000 if c == (0, -1) else 0))
+                assigned.add(slot)
+            if ai in wend:
+                wi += 1
+                assigned = set()
         stages.append((r0, len(rounds), a0, len(amps)))
     masks = []
     for S in I.supports:
@@ -573,6 +651,9 @@ def emit_interp_struct(process: str, nt: int, stage_amps: int, num, amputated: b
         *a[0], *a[1], a[2], a[3], a[4], a[5]), 3)
     src += arr("c_terms", "unsigned short", terms, lambda x: "%d" % x, 16)
     src += arr("c_stage_term", "int", stage_term, lambda x: "%d" % x, 16)
+    src += arr("c_sterms", "unsigned short", sterms, lambda x: "%d" % x, 16)
+    src += arr("c_wflow", "unsigned char", [f for w in wflows for f in w], lambda x: "%d" % x, 24)
+    src += arr("c_wbegin", "unsigned short", wbegin, lambda x: "%d" % x, 16)
     src += arr("c_supmask", "unsigned short", masks, lambda x: "%d" % x, 16)
     src += arr("c_cnum2", "short", cnum2, lambda x: "%d" % x, 24)
     src += arr("c_diag", "unsigned short", diags, lambda x: "%d" % x, 16)
@@ -582,13 +663,18 @@ def emit_interp_struct(process: str, nt: int, stage_amps: int, num, amputated: b
 struct {name} : Proc {{
     static constexpr int NT = {nt}, TAB = {(I.table_size + 7) // 8 * 8}, NSUP = {len(I.supports)}, NSTAGE = {len(I.stages)};
     static constexpr bool IS_TAB = false, IS_INTERP = true;
-    static constexpr long long TABLE_FLOPS = {I.table_flops}LL, AMP_FLOPS = {T.amplitude_flops_per_helicity()}LL;
+    static constexpr long long TABLE_FLOPS = {I.table_flops}LL, AMP_FLOPS = {T.amplitude_flops_per_helicity(not mode & 2)}LL;
     __device__ static __forceinline__ const TabTask* tasks() {{ return {prefix}c_itasks; }}
     __device__ static __forceinline__ IRound round(int r) {{ return {prefix}c_rounds[r]; }}
     __device__ static __forceinline__ IStage stage(int s) {{ return {prefix}c_stages[s]; }}
     __device__ static __forceinline__ IAmp amp(int a) {{ return {prefix}c_amps[a]; }}
     __device__ static __forceinline__ unsigned short term(int t) {{ return __ldg({prefix}c_terms + t); }}
     __device__ static __forceinline__ int stage_term_begin(int s) {{ return {prefix}c_stage_term[s]; }}
+    // colour windows: slot-encoded terms, the flows of each window in slot order
+    static constexpr int NSLOT = {ACC_SLOTS}, NWIN = {len(wflows)};
+    __device__ static __forceinline__ unsigned short sterm(int t) {{ return __ldg({prefix}c_sterms + t); }}
+    __device__ static __forceinline__ int wbegin(int w) {{ return __ldg({prefix}c_wbegin + w); }}
+    __device__ static __forceinline__ int wflow(int i) {{ return __ldg({prefix}c_wflow + i); }}
     __device__ static __forceinline__ unsigned support_mask(int s) {{ return {prefix}c_supmask[s]; }}
     __device__ static __forceinline__ int cnum2(int i, int j) {{ return __ldg({prefix}c_cnum2 + i * NCOL + j); }}
     __device__ static __forceinline__ int diag(int a) {{ return __ldg({prefix}c_diag + a); }}

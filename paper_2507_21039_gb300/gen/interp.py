@@ -17,7 +17,7 @@ from __future__ import annotations
 
 from dataclasses import dataclass, field
 
-from .plan import FLOPS
+from .plan import FLOPS, colour_groups
 from .tabplan import build_tabplan, compress
 
 # descriptor codes of the table routines and amplitude kinds (me_kernel_interp.cuh)
@@ -42,6 +42,8 @@ class InterpPlan:
     amp_order: list
     supports: list      # distinct supports of amplitude operands
     table_flops: int
+    sign: list = field(default_factory=list)    # +-1 of each amplitude in its colour group's sum
+    flush: dict = field(default_factory=dict)   # last member of a group -> the group's colour terms
 
 
 class _Arena:
@@ -74,7 +76,7 @@ class _Arena:
         self.free = merged
 
 
-def build_interp(process: str, stage_amps: int = 48, amputated: bool = False) -> InterpPlan:
+def build_interp(process: str, stage_amps: int = 48, amputated: bool = False, group: bool = True) -> InterpPlan:
     T = build_tabplan(process, amputated)
     P = T.plan
     ops = P.ops
@@ -95,13 +97,23 @@ def build_interp(process: str, stage_amps: int = 48, amputated: bool = False) ->
             closure(a, s)
         amp_deps.append(s)
 
-    # greedy order: next amplitude = fewest new table entries (ties: plan order)
-    live, order, remaining = set(), [], set(range(len(P.amps)))
+    # greedy order over colour groups (amplitudes with the same colour vector up
+    # to a sign, summed before the one update of J): next group = fewest new
+    # table entries (ties: plan order); members of a group stay adjacent
+    group_of, sign_of, group_terms, members = colour_groups(P)
+    if not group:  # one amplitude per unit: J updated after every amplitude
+        sign_of = [1] * len(P.amps)
+        group_terms = [tuple(P.amps[a][1]) for a in range(len(P.amps))]
+        members = [[a] for a in range(len(P.amps))]
+    unit_deps = [set().union(*(amp_deps[a] for a in m)) for m in members]
+    live, order, remaining = set(), [], set(range(len(members)))
     while remaining:
-        best = min(remaining, key=lambda i: (sum(size[o] for o in amp_deps[i] - live), i))
-        order.append(best)
+        best = min(remaining, key=lambda g: (sum(size[o] for o in unit_deps[g] - live), members[g][0]))
+        order += members[best]
         remaining.remove(best)
-        live |= amp_deps[best]
+        live |= unit_deps[best]
+    # the last member of each group carries the group's colour terms
+    flush = {members[g][-1]: group_terms[g] for g in range(len(members))}
 
     # stages and lifetimes
     stage_of_amp = {}
@@ -167,4 +179,4 @@ def build_interp(process: str, stage_amps: int = 48, amputated: bool = False) ->
                 last[o] = -99  # released
     supports = sorted({T.support[a] for ai, _ in P.amps for a in ops[ai].args}, key=lambda s: (len(s), s))
     tflops = sum(FLOPS[k] * len(t) for st in stages for k, t in st.rounds)
-    return InterpPlan(T, stages, slot, arena.peak, order, supports, tflops)
+    return InterpPlan(T, stages, slot, arena.peak, order, supports, tflops, sign_of, flush)

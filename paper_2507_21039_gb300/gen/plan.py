@@ -251,6 +251,33 @@ def _term_lines(d, gluon_ext) -> tuple:
     return tuple(sorted(lines))
 
 
+def colour_groups(P: Plan):
+    """Amplitudes whose colour-flow coefficient vectors are equal up to a sign.
+
+    The colour-flow vector is J_c = sum_a c_{a,c} A_a (Sec. 4.1).  If two
+    amplitudes have c_b = -c_a or c_b = c_a, their contribution to J is
+    c_a (A_a -+ A_b): the amplitudes are summed first and J is updated once per
+    group.  The normalised vector of a group has its lowest-flow coefficient
+    equal to +i or, for real coefficients, +1.
+    Returns (group of each amplitude, its sign in {+1, -1}, the terms of each
+    group, the amplitudes of each group in plan order)."""
+    key_of, group_of, sign_of, terms_of, members = {}, [], [], [], []
+    for ai, (_, terms) in enumerate(P.amps):
+        t = tuple(sorted(terms))
+        c0 = t[0][1]
+        s = -1 if (c0[1] < 0 or (c0[1] == 0 and c0[0] < 0)) else 1
+        key = tuple((f, (s * c[0], s * c[1])) for f, c in t)
+        if key not in key_of:
+            key_of[key] = len(terms_of)
+            terms_of.append(key)
+            members.append([])
+        g = key_of[key]
+        group_of.append(g)
+        sign_of.append(s)
+        members[g].append(ai)
+    return group_of, sign_of, terms_of, members
+
+
 def diagram_lines(P: Plan, d: int) -> tuple:
     """internal lines of diagram d (masks over the external particles)"""
     return P.diag_lines[d]

@@ -26,7 +26,7 @@ from __future__ import annotations
 
 from dataclasses import dataclass, field
 
-from .plan import FLOPS, Plan, amputate, build_plan
+from .plan import FLOPS, Plan, amputate, build_plan, colour_groups
 
 
 @dataclass
@@ -56,10 +56,18 @@ class TabPlan:
     def table_flops(self) -> int:
         return sum(FLOPS[r.kind] * len(r.tasks) for r in self.rounds)
 
-    def amplitude_flops_per_helicity(self) -> int:
+    def amplitude_flops_per_helicity(self, grouped: bool = True) -> int:
+        """amplitudes plus their accumulation into J; grouped: amplitudes with
+        the same colour vector up to a sign are summed (2 flops per member after
+        the first) and the group's terms are added once"""
         P = self.plan
         f = sum(FLOPS[P.ops[a].kind] for a, _ in P.amps)
-        for _, terms in P.amps:
+        if grouped:
+            _, _, terms_of, members = colour_groups(P)
+            f += sum(2 * (len(m) - 1) for m in members)
+        else:
+            terms_of = [terms for _, terms in P.amps]
+        for terms in terms_of:
             for _, c in terms:
                 f += 2 if (abs(c[0]) + abs(c[1]) == 1) else 4
         return f

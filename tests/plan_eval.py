@@ -189,6 +189,7 @@ def evaluate_staged(orc, I, p, h, mt):
         return sum(bits[q] << j for j, q in enumerate(S))
 
     J = np.zeros(P.ncol, dtype=complex)
+    gsum = 0.0
     ops = P.ops
     for st in I.stages:
         for kind, tasks in st.rounds:
@@ -230,6 +231,12 @@ def evaluate_staged(orc, I, p, h, mt):
                     dot(w[2], w[0]) * dot(k3 - k1, w[1])
             else:
                 x = dot(_v4(op.kind[:5], w[0], w[1], w[2]), w[3])
-            for col, c in terms:
-                J[col] += complex(c[0], c[1]) * x
+            # colour group: signed sum of its amplitudes, added into J with the
+            # group's terms by its last member
+            gsum += I.sign[ai] * x
+            if ai in I.flush:
+                for col, c in I.flush[ai]:
+                    J[col] += complex(c[0], c[1]) * gsum
+                gsum = 0.0
+    assert gsum == 0.0
     return J

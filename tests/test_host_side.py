@@ -126,6 +126,80 @@ def test_generator_flop_counts_positive():
         assert P.colour_flops_per_helicity() > 0
 
 
+@pytest.mark.parametrize("process", ["gg_ttx", "gg_ttxg", "gg_ttxgg", "gg_ttxggg"])
+def test_colour_groups_rebuild_every_amplitude_terms(orc, process):
+    """Each amplitude's colour terms are its sign times its group's normalised
+    terms, the groups are disjoint and cover every amplitude, and J built
+    from group sums is J built amplitude by amplitude (random amplitudes)."""
+    from paper_2507_21039_gb300.gen.plan import colour_groups
+
+    P = build_plan(process)
+    group_of, sign_of, terms_of, members = colour_groups(P)
+    assert sorted(a for m in members for a in m) == list(range(len(P.amps)))
+    for ai, (_, terms) in enumerate(P.amps):
+        g = group_of[ai]
+        assert ai in members[g] and sign_of[ai] in (1, -1)
+        assert sorted(terms) == sorted((f, (sign_of[ai] * c[0], sign_of[ai] * c[1])) for f, c in terms_of[g])
+    for t in terms_of:
+        c0 = t[0][1]
+        assert c0[1] > 0 or (c0[1] == 0 and c0[0] > 0)
+    rng = np.random.default_rng(5)
+    x = rng.normal(size=len(P.amps)) + 1j * rng.normal(size=len(P.amps))
+    J1 = np.zeros(P.ncol, complex)
+    for ai, (_, terms) in enumerate(P.amps):
+        for f, c in terms:
+            J1[f] += complex(*c) * x[ai]
+    J2 = np.zeros(P.ncol, complex)
+    for g, m in enumerate(members):
+        G = sum(sign_of[a] * x[a] for a in m)
+        for f, c in terms_of[g]:
+            J2[f] += complex(*c) * G
+    assert np.abs(J1 - J2).max() < 1e-12 * np.abs(J1).max()
+
+
+def test_colour_windows_replay_the_flow_updates():
+    """The slot-encoded colour updates of the descriptor kernel (per-thread
+    accumulator slots, first touch assigns, J += slots at each window's end)
+    give the same J as the flow-indexed updates, for random group sums."""
+    from paper_2507_21039_gb300.gen.emit import ACC_SLOTS, emit_interp_struct
+
+    src, I = emit_interp_struct("gg_ttxggg", 128, 16, colour_matrix(5)[0], 0)
+
+    def array(name):
+        body = re.search(r"\b" + name + r"\[\d+\] = \{(.*?)\};", src, re.S).group(1)
+        return [int(x) for x in re.findall(r"-?\d+", body)]
+
+    terms, sterms, wflow, wbegin = array("c_terms"), array("c_sterms"), array("c_wflow"), array("c_wbegin")
+    amps = re.search(r"c_amps\[\d+\] = \{(.*?)\n\};", src, re.S).group(1)
+    kinds_nterm = [(int(m[0]), int(m[1])) for m in re.findall(r"\}, (\d+), \d+, \d+, (\d+)\}", amps)]
+    assert len(kinds_nterm) == len(I.amp_order) and len(terms) == len(sterms)
+    rng = np.random.default_rng(9)
+    J1 = np.zeros(120, complex)
+    J2 = np.zeros(120, complex)
+    slots = np.full(ACC_SLOTS, np.nan + 0j)
+    t = win = 0
+    for kind, nterm in kinds_nterm:
+        G = complex(*rng.normal(size=2))
+        for _ in range(nterm):
+            ct, st = terms[t], sterms[t]
+            x = (-1j if ct & 0x8000 else 1j) * G
+            J1[ct & 0x7FFF] += x
+            assert (st & 0x8000) == (ct & 0x8000) and (st & 0x1F) < ACC_SLOTS
+            assert wflow[wbegin[win] + (st & 0x1F)] == ct & 0x7FFF
+            slots[st & 0x1F] = x if st & 0x4000 else slots[st & 0x1F] + x
+            t += 1
+        if kind & 0x40:
+            n = wbegin[win + 1] - wbegin[win]
+            assert len(set(wflow[wbegin[win]:wbegin[win + 1]])) == n <= ACC_SLOTS
+            for k in range(n):
+                assert not np.isnan(slots[k])
+                J2[wflow[wbegin[win] + k]] += slots[k]
+            slots[:] = np.nan
+            win += 1
+    assert win == len(wbegin) - 1 and t == len(terms)
+    assert np.abs(J1 - J2).max() < 1e-12 * np.abs(J1).max()
+
+
 # ---------------------------------------------------------------- C ABI
 def _declared_symbols(header="me.h"):
     src = open(os.path.join(ROOT, "include", header)).read()
