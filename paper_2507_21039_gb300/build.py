@@ -108,7 +108,8 @@ def _compile(src: str, obj: str) -> tuple[str, str]:
 def build(force: bool = False, verbose: bool = False, jobs: int | None = None) -> str:
     os.makedirs(OBJ, exist_ok=True)
     stamp = os.path.join(BUILD, "stamp")
-    dig = _digest(_inputs()) + ",".join(PROCESSES) + os.environ.get("ME_GEN_KERNEL", "") + " ".join(_extra_flags())
+    dig = (_digest(_inputs()) + ",".join(PROCESSES) + os.environ.get("ME_GEN_KERNEL", "") + " ".join(_extra_flags())
+           + os.environ.get("ME_INTERP_CONST", ""))
     if not force and os.path.exists(LIB) and os.path.exists(stamp) and open(stamp).read() == dig:
         return LIB
     gen_srcs = generate()

@@ -240,6 +240,17 @@ template <class T> __device__ __forceinline__ cx<T> sdot(const Wf<T>& a, const W
     s = cfma(a.c[3], b.c[3], s);
     return s;
 }
+// a += S b (S = +1 or -1), componentwise: the contractions are bilinear, so a
+// colour group's members sharing one operand are contracted once with the
+// signed sum of their other operands
+template <int S, class T> __device__ __forceinline__ void wf_acc(Wf<T>& a, const Wf<T>& b)
+{
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        if constexpr (S > 0) { a.c[i].re += b.c[i].re; a.c[i].im += b.c[i].im; }
+        else { a.c[i].re -= b.c[i].re; a.c[i].im -= b.c[i].im; }
+    }
+}
 template <class T> __device__ __forceinline__ cx<T> DOTV(const Wf<T>& a, const Wf<T>& b) { return mdot(a, b); }
 template <class T> __device__ __forceinline__ cx<T> DOTF(const Wf<T>& a, const Wf<T>& b) { return sdot(a, b); }
 

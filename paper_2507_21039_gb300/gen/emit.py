@@ -12,7 +12,7 @@ import math
 import struct
 
 from .colour import colour_matrix
-from .plan import Plan, build_plan, colour_groups
+from .plan import FLOPS, Plan, build_plan, colour_groups
 from .interp import AMP_KINDS, ROUTINES, build_interp
 from .tabplan import build_tabplan
 
@@ -22,9 +22,10 @@ EXT_KINDS = {"VIN": 0, "VOUT": 1, "FO_U": 2, "FO_V": 3, "FI_U": 4, "FI_V": 5}
 #             schedule mode, amplitudes per stage (0: one resident table),
 #             warp fence every n amplitudes in FP32, in FP64)
 # schedule mode: bit 0 = amplitudes as contractions of amputated vertex
-# objects, bit 1 = no colour groups (J updated after every amplitude)
+# objects, bit 1 = no colour groups (J updated after every amplitude), bit 2 =
+# no merged contractions (a group's members sharing an operand each contract)
 # (measured on GB300 over stage sizes, events per CTA and fence intervals)
-TAB_PROCESSES = {"gg_ttxg": (32, 1, 1, 1, 0, 1, 4), "gg_ttxgg": (64, 2, 2, 1, 60, 7, 4)}
+TAB_PROCESSES = {"gg_ttxg": (32, 1, 1, 1, 0, 1, 4), "gg_ttxgg": (64, 2, 2, 5, 60, 7, 4)}
 # processes evaluated with the staged descriptor kernel (me_kernel_interp.cuh)
 # process -> (threads per event, amplitudes per stage and schedule mode (as
 #             above) in FP32 / mixed, the same in FP64).  FP32 keeps J in shared
@@ -209,7 +210,7 @@ def emit_process(process: str) -> tuple[str, dict]:
 
     tab_src, TP, IP = ("", None, None)
     if process in TAB_PROCESSES:
-        tab_src, TP, tab_flops = emit_tab_struct(process, *TAB_PROCESSES[process], ncol, nlines, cbody)
+        tab_src, TP, tab_flops, tab_amp_flops = emit_tab_struct(process, *TAB_PROCESSES[process], ncol, nlines, cbody)
     elif process in INTERP_PROCESSES:
         nt_i, sa, amp_i, sa_d, amp_d = INTERP_PROCESSES[process]
         tab_src, IP = emit_interp_struct(process, nt_i, sa, num, amp_i)
@@ -223,7 +224,7 @@ def emit_process(process: str) -> tuple[str, dict]:
     launch_fn = "launch_tab" if TP else ("launch_interp" if IP else "launch_scalar")
     nhel_all = 1 << npar
     if TP:
-        flops_hel = TP.amplitude_flops_per_helicity(not TAB_PROCESSES[process][3] & 2) + -(-tab_flops // nhel_all)
+        flops_hel = tab_amp_flops + -(-tab_flops // nhel_all)
     elif IP:
         flops_hel = IP.tab.amplitude_flops_per_helicity(not INTERP_PROCESSES[process][2] & 2) + \
             -(-IP.table_flops // nhel_all)
@@ -379,6 +380,78 @@ def _amp_block(P, ai, terms, addr, n_amp, diag):
     return out
 
 
+def _shared_operand(P, run):
+    """For a colour group's members `run` (plan amplitude indices) that are all
+    two-operand contractions of one kind (DOTV or DOTF, both bilinear and
+    symmetric) sharing one operand: (kind, shared op, [other op of each
+    member]); else None."""
+    ops = [P.ops[P.amps[a][0]] for a in run]
+    if len(run) < 2 or ops[0].kind not in ("DOTV", "DOTF") or any(o.kind != ops[0].kind for o in ops):
+        return None
+    common = set(ops[0].args).intersection(*(set(o.args) for o in ops[1:]))
+    if not common:
+        return None
+    y = min(common)
+    others = [o.args[1] if o.args[0] == y else o.args[0] for o in ops]
+    return ops[0].kind, y, others
+
+
+def _merged_group_block(P, run, addr, n_amp, sign_of, terms, merge):
+    """A whole colour group in one block: sum_m s_m K(X_m, Y) = s_1 K(X_1 + sum_m s_1 s_m X_m, Y)
+    (K bilinear), one contraction instead of len(run); with single-diagram
+    enhancement every member's own amplitude is also formed."""
+    kind, y, others = merge
+    s1 = sign_of[run[0]]
+    out = [f"{{ Wf<T> S = tab.ld({addr(others[0])});"]
+    for a, x in zip(run[1:], others[1:]):
+        out.append(f"  wf_acc<{s1 * sign_of[a]}>(S, tab.ld({addr(x)}));")
+    out.append(f"  const cx<T> G = {kind}<T>(S, tab.ld({addr(y)}));")
+    for col, c in terms:
+        out.append(f"  jacc<{s1 * c[0]}, {s1 * c[1]}, T>(J[{col}], G);")
+    out.append("  if constexpr (SDE) {")
+    for a in run:
+        out.append(f"    {{ const cx<T> xm = {_amp_call(P, P.amps[a][0], addr)}; ME_SDE(xm, {P.amp_diag[a]}); }}")
+    out.append("  }")
+    out.append("}")
+    for k in range(len(run)):
+        out.append(f"ME_FENCE(T, {n_amp + k});")
+    return out
+
+
+_MERGED_FLOPS_SAVED = [0]   # amplitude flops per helicity removed by merged groups (current struct)
+
+
+def _amp_run_code(P, items, addr, n_amp, sign_of, flush, merging=True):
+    """code for consecutive amplitudes `items` [(plan index, first, last)] of one
+    stage: whole colour groups that share an operand are merged, the rest go
+    amplitude by amplitude"""
+    code, k = [], 0
+    while k < len(items):
+        pi, first, last = items[k]
+        run = [pi]
+        if first and not last:
+            j = k + 1
+            while j < len(items) and not items[j][1]:
+                run.append(items[j][0])
+                if items[j][2]:
+                    break
+                j += 1
+        merge = _shared_operand(P, run) if (merging and first and run[-1] in flush and len(run) > 1) else None
+        if merge:
+            code += _merged_group_block(P, run, addr, n_amp, sign_of, flush[run[-1]], merge)
+            # per merged member: one contraction and one complex add of the group
+            # sum fewer, one wavefunction add (8 flops) more
+            _MERGED_FLOPS_SAVED[0] += (len(run) - 1) * (FLOPS[merge[0]] + 2 - 8)
+            n_amp += len(run)
+            k += len(run)
+            continue
+        code += _grouped_amp_block(P, pi, P.amps[pi][0], addr, n_amp, P.amp_diag[pi], sign_of[pi], first, last,
+                                   flush.get(pi, ()))
+        n_amp += 1
+        k += 1
+    return code, n_amp
+
+
 def _group_positions(order, flush):
     """(first, last) flags of each amplitude of `order` within its colour group
     (the members of a group are adjacent in `order`; `flush` holds the last
@@ -426,6 +499,7 @@ def emit_tab_struct(process: str, nt: int, epc_f: int, epc_d: int, amputated: in
     schedule of gen/interp.py as straight-line code (`staged`): per stage, the
     table rounds of the objects that become live, then the stage's amplitudes,
     slots reused after each object's last reader; one helicity per thread."""
+    _MERGED_FLOPS_SAVED[0] = 0
     tasks = []
     # rounds of one level run without barriers between them; each round's
     # tasks start at the warp after the one where the previous round's ended,
@@ -460,10 +534,8 @@ def emit_tab_struct(process: str, nt: int, epc_f: int, epc_d: int, amputated: in
             members = [[a] for a in range(len(P.amps))]
         order = [a for m in members for a in m]
         flush = {m[-1]: group_terms[group_of[m[-1]]] for m in members}
-        acode = []
-        for n_amp, (pi, (first, last)) in enumerate(zip(order, _group_positions(order, flush))):
-            acode += _grouped_amp_block(P, pi, P.amps[pi][0], addr, n_amp, P.amp_diag[pi], sign_of[pi], first, last,
-                                        flush.get(pi, ()))
+        items = [(pi, f, l) for pi, (f, l) in zip(order, _group_positions(order, flush))]
+        acode, _ = _amp_run_code(P, items, addr, 0, sign_of, flush, not amputated & 4)
         used = {TP.support[a] for ai, _ in P.amps for a in P.ops[ai].args}
         body = f"""
     static constexpr bool STAGED = false;
@@ -502,11 +574,9 @@ def emit_tab_struct(process: str, nt: int, epc_f: int, epc_d: int, amputated: in
                 if ri in st.barriers:
                     code.append("__syncthreads();")
             code.append("__syncthreads();")
-            for ai in st.amps:
-                first, last = pos[ai]
-                code += _grouped_amp_block(P, ai, P.amps[ai][0], addr, n_amp, P.amp_diag[ai], I.sign[ai], first, last,
-                                           I.flush.get(ai, ()))
-                n_amp += 1
+            run_code, n_amp = _amp_run_code(P, [(ai, *pos[ai]) for ai in st.amps], addr, n_amp, I.sign, I.flush,
+                                            not amputated & 4)
+            code += run_code
             code.append("__syncthreads();  // the stage's dead slots are reused by the next one")
         used = {TP.support[a] for ai, _ in P.amps for a in ops[ai].args}
         body = f"""
@@ -522,6 +592,7 @@ def emit_tab_struct(process: str, nt: int, epc_f: int, epc_d: int, amputated: in
 {NL.join("        " + x for x in code)}
     }}"""
 
+    amp_flops = TP.amplitude_flops_per_helicity(not amputated & 2) - _MERGED_FLOPS_SAVED[0]
     task_init = ",\n    ".join("{%d, %d, %d, %d, %d, %d, %d, 0, 0}" % t for t in tasks)
     desc = (f"{'staged (' + str(stage) + ' amplitudes per stage)' if stage else 'resident'}"
             f"{', amputated vertex objects' if amputated & 1 else ''}{'' if amputated & 2 else ', colour groups'}")
@@ -531,7 +602,7 @@ __device__ const TabTask c_tasks[{max(len(tasks), 1)}] = {{
 }};
 
 // helicity-recycled evaluation, {desc}: {size} table entries, {len(tasks)} table tasks,
-// {table_flops} table flops per event, {TP.amplitude_flops_per_helicity(not amputated & 2)} amplitude flops per helicity
+// {table_flops} table flops per event, {amp_flops} amplitude flops per helicity
 struct ProcTab : Proc {{
     static constexpr int NT = {nt}, TAB = {(size + 7) // 8 * 8};
     // events per CTA (own shared-memory region each; CTA barriers keep their
@@ -541,18 +612,21 @@ struct ProcTab : Proc {{
     // anyway), FP64 <= 255 (its tables are twice as large)
     static constexpr int MIN_CTAS_F = {max(1, 65536 // (nt * epc_f * 128))}, MIN_CTAS_D = {max(1, 65536 // (nt * epc_d * 255))};
     static constexpr bool IS_TAB = true, IS_INTERP = false;
-    static constexpr long long TABLE_FLOPS = {table_flops}LL, AMP_FLOPS = {TP.amplitude_flops_per_helicity(not amputated & 2)}LL;
+    static constexpr long long TABLE_FLOPS = {table_flops}LL, AMP_FLOPS = {amp_flops}LL;
     // warp fence every n amplitudes (FP32, FP64)
     static constexpr int FENCE_F = {fence_f}, FENCE_D = {fence_d};
 {body}
 }};
 """
-    return src, TP, table_flops
+    return src, TP, table_flops, amp_flops
 
 
 NL = "\n"
 
 
+# uniform descriptors of the staged descriptor kernel in constant memory (build
+# option ME_INTERP_CONST=0 keeps them in global memory)
+CONST_DESCRIPTORS = __import__("os").environ.get("ME_INTERP_CONST", "1") != "0"
 # accumulator slots per thread for the colour windows of the staged descriptor
 # kernel (shared memory: ACC_SLOTS x 8 B per thread)
 ACC_SLOTS = 24
@@ -639,9 +713,21 @@ def emit_interp_struct(process: str, nt: int, stage_amps: int, num, mode: int = 
     n = len(num)
     cnum2 = [num[i][j] * (1 if i == j else 2) if j >= i else 0 for i in range(n) for j in range(n)]
 
+    # the descriptors every thread of a CTA reads at the same index (rounds,
+    # stages, amplitudes, colour terms, diagrams) go to constant memory when they
+    # fit its 64 KB (uniform reads through the constant cache), for the first
+    # struct of the unit only; per-thread data (table tasks) stays in global memory
+    uniform = ("c_rounds", "c_stages", "c_amps", "c_terms", "c_stage_term", "c_diag")
+    cbytes = 8 * len(rounds) + 8 * len(stages) + 16 * len(amps) + 2 * len(terms) + 4 * len(stage_term) + 2 * len(diags)
+    use_const = CONST_DESCRIPTORS and not prefix and cbytes <= 60 * 1024
+
     def arr(aname, ctype, rows, fmt, per_line=6):
         body = ",\n    ".join(", ".join(fmt(x) for x in rows[i:i + per_line]) for i in range(0, len(rows), per_line))
-        return f"__device__ const {ctype} {prefix}{aname}[{max(len(rows), 1)}] = {{\n    {body if rows else '0'}\n}};\n"
+        space = "__constant__" if use_const and aname in uniform else "__device__ const"
+        return f"{space} {ctype} {prefix}{aname}[{max(len(rows), 1)}] = {{\n    {body if rows else '0'}\n}};\n"
+
+    def rd(aname, index):  # read of a descriptor array
+        return f"{prefix}{aname}[{index}]" if use_const and aname in uniform else f"__ldg({prefix}{aname} + {index})"
 
     src = ""
     src += arr("c_itasks", "TabTask", tasks, lambda t: "{%d, %d, %d, %d, %d, %d, %d, 0, 0}" % t, 4)
@@ -668,7 +754,7 @@ struct {name} : Proc {{
     __device__ static __forceinline__ IRound round(int r) {{ return {prefix}c_rounds[r]; }}
     __device__ static __forceinline__ IStage stage(int s) {{ return {prefix}c_stages[s]; }}
     __device__ static __forceinline__ IAmp amp(int a) {{ return {prefix}c_amps[a]; }}
-    __device__ static __forceinline__ unsigned short term(int t) {{ return __ldg({prefix}c_terms + t); }}
+    __device__ static __forceinline__ unsigned short term(int t) {{ return {rd("c_terms", "t")}; }}
     __device__ static __forceinline__ int stage_term_begin(int s) {{ return {prefix}c_stage_term[s]; }}
     // colour windows: slot-encoded terms, the flows of each window in slot order
     static constexpr int NSLOT = {ACC_SLOTS}, NWIN = {len(wflows)};
@@ -677,7 +763,7 @@ struct {name} : Proc {{
     __device__ static __forceinline__ int wflow(int i) {{ return __ldg({prefix}c_wflow + i); }}
     __device__ static __forceinline__ unsigned support_mask(int s) {{ return {prefix}c_supmask[s]; }}
     __device__ static __forceinline__ int cnum2(int i, int j) {{ return __ldg({prefix}c_cnum2 + i * NCOL + j); }}
-    __device__ static __forceinline__ int diag(int a) {{ return __ldg({prefix}c_diag + a); }}
+    __device__ static __forceinline__ int diag(int a) {{ return {rd("c_diag", "a")}; }}
 }};
 """
     return src, I

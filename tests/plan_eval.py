@@ -154,10 +154,15 @@ def _v4(name, A, B, C):
     return dot(A, B) * C - dot(A, C) * B
 
 
-def evaluate_staged(orc, I, p, h, mt):
+def evaluate_staged(orc, I, p, h, mt, merge=False):
     """Run a staged interpreter schedule (gen/interp.py) in numpy: a slot table
     shared by all helicity variants, filled stage by stage, with slots reused
-    after their last reader -- the layout the CUDA kernel executes."""
+    after their last reader -- the layout the CUDA kernel executes.  merge:
+    colour groups whose members lie in one stage and share a contraction
+    operand are contracted once with the signed sum of the other operands, as
+    the straight-line table kernel does."""
+    from paper_2507_21039_gb300.gen.emit import _group_positions, _shared_operand
+
     T = I.tab
     P = T.plan
     npar = P.npar
@@ -191,6 +196,7 @@ def evaluate_staged(orc, I, p, h, mt):
     J = np.zeros(P.ncol, dtype=complex)
     gsum = 0.0
     ops = P.ops
+    pos = dict(zip(I.amp_order, _group_positions(I.amp_order, I.flush)))
     for st in I.stages:
         for kind, tasks in st.rounds:
             for out, ins, ln in tasks:
@@ -213,13 +219,36 @@ def evaluate_staged(orc, I, p, h, mt):
                 else:
                     inv = lines[ln[2]][1]
                     table[out] = inv * np.array([a[0] @ G[mu] @ a[1] for mu in range(4)])
-        for ai in st.amps:
+        def value(x):
+            base = I.slot[x] if (ops[x].out != "A" and not ops[x].kind.startswith("ext_")) else 2 * ops[x].ext
+            return table[base + var(T.support[x])]
+
+        amps, k = st.amps, 0
+        while k < len(amps):
+            ai = amps[k]
+            first, last = pos[ai]
+            run = [ai]
+            if first and not last:
+                for b in amps[k + 1:]:
+                    if pos[b][0]:
+                        break
+                    run.append(b)
+                    if pos[b][1]:
+                        break
+            mg = _shared_operand(P, run) if (merge and first and run[-1] in I.flush and len(run) > 1) else None
+            if mg:
+                kind, y, others = mg
+                S = sum(I.sign[a] * value(x) for a, x in zip(run, others))
+                gsum = _amputated(kind, [S, value(y)], lines, ())
+                for col, c in I.flush[run[-1]]:
+                    J[col] += complex(c[0], c[1]) * gsum
+                gsum = 0.0
+                k += len(run)
+                continue
+            k += 1
             aop, terms = P.amps[ai]
             op = ops[aop]
-            w = []
-            for x in op.args:
-                base = I.slot[x] if (ops[x].out != "A" and not ops[x].kind.startswith("ext_")) else 2 * ops[x].ext
-                w.append(table[base + var(T.support[x])])
+            w = [value(x) for x in op.args]
             if op.kind in ("DOTV", "DOTF"):
                 x = _amputated(op.kind, w, lines, op.mom)
             elif op.kind == "FFV1_0":

@@ -269,12 +269,13 @@ def test_abi_validation_without_device(lib):
 
 
 @pytest.mark.parametrize("process,stage,amputated", [("gg_ttxgg", 16, False), ("gg_ttxggg", 16, False),
-                                                     ("gg_ttxg", 4, True), ("gg_ttxgg", 16, True),
+                                                     ("gg_ttxg", 4, True), ("gg_ttxgg", 16, True), ("gg_ttxgg", 60, True),
                                                      ("gg_ttxggg", 16, True)])
 def test_staged_schedule_reproduces_oracle(orc, process, stage, amputated):
     """The staged schedules (slot reuse after each object's last reader,
-    variant indexing; with or without amputated vertex objects) give the
-    oracle's partial amplitudes."""
+    variant indexing, colour groups; with or without amputated vertex objects,
+    and with the groups that share a contraction operand contracted once) give
+    the oracle's partial amplitudes."""
     from paper_2507_21039_gb300.gen.interp import build_interp
     from plan_eval import evaluate_staged
 
@@ -285,6 +286,7 @@ def test_staged_schedule_reproduces_oracle(orc, process, stage, amputated):
     npar = I.tab.plan.npar
     scale = max(np.abs(orc.partial_amps(process, p, h)).max() for h in range(0, 1 << npar, 9))
     for h in (0b0110101 & ((1 << npar) - 1), (1 << npar) - 1 - 6):
-        J = evaluate_staged(orc, I, p, h, MT)
         A = orc.partial_amps(process, p, h)
-        assert np.abs(J - A).max() < 1e-12 * scale
+        for merge in ((False, True) if amputated else (False,)):
+            J = evaluate_staged(orc, I, p, h, MT, merge)
+            assert np.abs(J - A).max() < 1e-12 * scale
