@@ -67,6 +67,19 @@ struct Params {
 // generation cuts on the final particles selected by cutmask: pT > ptmin for
 // each, Delta R = sqrt(Delta eta^2 + Delta phi^2) > drmin for each pair.  The
 // pseudorapidity and azimuth of each particle are computed once.
+// Delta R = sqrt(Delta eta^2 + Delta phi^2) of two momenta in FP64, Delta phi
+// wrapped to [-pi, pi]
+__device__ double delta_r(const double* ki, const double* kj)
+{
+    const double Pi = sqrt(ki[1] * ki[1] + ki[2] * ki[2] + ki[3] * ki[3]);
+    const double Pj = sqrt(kj[1] * kj[1] + kj[2] * kj[2] + kj[3] * kj[3]);
+    const double de = 0.5 * log((Pi + ki[3]) / (Pi - ki[3])) - 0.5 * log((Pj + kj[3]) / (Pj - kj[3]));
+    double dphi = atan2(ki[2], ki[1]) - atan2(kj[2], kj[1]);
+    while (dphi > M_PI) dphi -= 2.0 * M_PI;
+    while (dphi < -M_PI) dphi += 2.0 * M_PI;
+    return sqrt(de * de + dphi * dphi);
+}
+
 __device__ bool passes(const double (*k)[4], int n, const Params& a)
 {
     if (!a.cutmask) return true;
@@ -75,22 +88,31 @@ __device__ bool passes(const double (*k)[4], int n, const Params& a)
         if (!(sqrt(k[i][1] * k[i][1] + k[i][2] * k[i][2]) > a.ptmin)) return false;
     }
     if (__popc(a.cutmask) < 2) return true;  // no pairs
-    double eta[kMaxFinal], phi[kMaxFinal];
+    // Delta R of each pair in FP32 (eta = asinh(pz / pT), well conditioned);
+    // a pair within a guard band of the cut, far wider than the FP32 error of
+    // Delta R, is decided in FP64 exactly as the definition states it
+    constexpr float kBand = 1e-3f;
+    float etf[kMaxFinal], phf[kMaxFinal];
     for (int i = 0; i < n; ++i) {
         if (!((a.cutmask >> i) & 1)) continue;
-        const double P = sqrt(k[i][1] * k[i][1] + k[i][2] * k[i][2] + k[i][3] * k[i][3]);
-        eta[i] = 0.5 * log((P + k[i][3]) / (P - k[i][3]));
-        phi[i] = atan2(k[i][2], k[i][1]);
+        const float px = (float)k[i][1], py = (float)k[i][2], pz = (float)k[i][3];
+        etf[i] = asinhf(pz / sqrtf(px * px + py * py));
+        phf[i] = atan2f(py, px);
     }
+    const float drf = (float)a.drmin;
+    const float lo2 = drf > kBand ? (drf - kBand) * (drf - kBand) : -1.0f, hi2 = (drf + kBand) * (drf + kBand);
     for (int i = 0; i < n; ++i) {
         if (!((a.cutmask >> i) & 1)) continue;
         for (int j = i + 1; j < n; ++j) {
             if (!((a.cutmask >> j) & 1)) continue;
-            const double de = eta[i] - eta[j];
-            double dphi = phi[i] - phi[j];
-            while (dphi > M_PI) dphi -= 2.0 * M_PI;
-            while (dphi < -M_PI) dphi += 2.0 * M_PI;
-            if (!(sqrt(de * de + dphi * dphi) > a.drmin)) return false;
+            const float de = etf[i] - etf[j];
+            float dphi = phf[i] - phf[j];
+            if (dphi > (float)M_PI) dphi -= 2.0f * (float)M_PI;
+            if (dphi < -(float)M_PI) dphi += 2.0f * (float)M_PI;
+            const float dr2 = de * de + dphi * dphi;
+            if (dr2 > hi2) continue;
+            if (dr2 < lo2) return false;
+            if (!(delta_r(k[i], k[j]) > a.drmin)) return false;  // near the cut (or not finite): FP64
         }
     }
     return true;
@@ -134,7 +156,23 @@ __device__ bool rambo_point(const Params& a, long long ev, int attempt, double (
     double P2[kMaxFinal];
     for (int j = 0; j < n; ++j) P2[j] = k[j][0] * k[j][0];
     const double r = a.msum / a.sqrt_s;
-    double xi = sqrt(1.0 - r * r);
+    // Newton for xi: first in FP32 (fast square roots and divisions) to about
+    // FP32 resolution, then in FP64 to the FP64 tolerance (one or two steps
+    // from there, as the convergence is quadratic)
+    float xf = sqrtf(1.0f - (float)(r * r));
+    const float sf = (float)a.sqrt_s;
+    for (int it = 0; it < 12; ++it) {
+        float f = -sf, fp = 0.0f;
+        for (int j = 0; j < n; ++j) {
+            const float p2 = (float)P2[j], m = (float)a.m[j];
+            const float e = sqrtf(fmaf(xf * xf, p2, m * m));
+            f += e;
+            fp += xf * p2 / e;
+        }
+        if (fabsf(f) <= 4e-7f * sf) break;
+        xf -= f / fp;
+    }
+    double xi = (xf > 0.0f && xf <= 1.0f) ? (double)xf : sqrt(1.0 - r * r);
     bool ok = false;
     for (int it = 0; it < 50; ++it) {
         double f = -a.sqrt_s, fp = 0.0;

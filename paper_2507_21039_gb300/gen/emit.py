@@ -418,14 +418,12 @@ def _merged_group_block(P, run, addr, n_amp, sign_of, terms, merge):
     return out
 
 
-_MERGED_FLOPS_SAVED = [0]   # amplitude flops per helicity removed by merged groups (current struct)
-
-
 def _amp_run_code(P, items, addr, n_amp, sign_of, flush, merging=True):
     """code for consecutive amplitudes `items` [(plan index, first, last)] of one
     stage: whole colour groups that share an operand are merged, the rest go
-    amplitude by amplitude"""
-    code, k = [], 0
+    amplitude by amplitude.  Returns (code, next amplitude number, amplitude
+    flops per helicity saved by the merges)."""
+    code, k, saved = [], 0, 0
     while k < len(items):
         pi, first, last = items[k]
         run = [pi]
@@ -441,7 +439,7 @@ def _amp_run_code(P, items, addr, n_amp, sign_of, flush, merging=True):
             code += _merged_group_block(P, run, addr, n_amp, sign_of, flush[run[-1]], merge)
             # per merged member: one contraction and one complex add of the group
             # sum fewer, one wavefunction add (8 flops) more
-            _MERGED_FLOPS_SAVED[0] += (len(run) - 1) * (FLOPS[merge[0]] + 2 - 8)
+            saved += (len(run) - 1) * (FLOPS[merge[0]] + 2 - 8)
             n_amp += len(run)
             k += len(run)
             continue
@@ -449,7 +447,7 @@ def _amp_run_code(P, items, addr, n_amp, sign_of, flush, merging=True):
                                    flush.get(pi, ()))
         n_amp += 1
         k += 1
-    return code, n_amp
+    return code, n_amp, saved
 
 
 def _group_positions(order, flush):
@@ -499,7 +497,7 @@ def emit_tab_struct(process: str, nt: int, epc_f: int, epc_d: int, amputated: in
     schedule of gen/interp.py as straight-line code (`staged`): per stage, the
     table rounds of the objects that become live, then the stage's amplitudes,
     slots reused after each object's last reader; one helicity per thread."""
-    _MERGED_FLOPS_SAVED[0] = 0
+    saved = 0
     tasks = []
     # rounds of one level run without barriers between them; each round's
     # tasks start at the warp after the one where the previous round's ended,
@@ -535,7 +533,7 @@ def emit_tab_struct(process: str, nt: int, epc_f: int, epc_d: int, amputated: in
         order = [a for m in members for a in m]
         flush = {m[-1]: group_terms[group_of[m[-1]]] for m in members}
         items = [(pi, f, l) for pi, (f, l) in zip(order, _group_positions(order, flush))]
-        acode, _ = _amp_run_code(P, items, addr, 0, sign_of, flush, not amputated & 4)
+        acode, _, saved = _amp_run_code(P, items, addr, 0, sign_of, flush, not amputated & 4)
         used = {TP.support[a] for ai, _ in P.amps for a in P.ops[ai].args}
         body = f"""
     static constexpr bool STAGED = false;
@@ -574,8 +572,9 @@ def emit_tab_struct(process: str, nt: int, epc_f: int, epc_d: int, amputated: in
                 if ri in st.barriers:
                     code.append("__syncthreads();")
             code.append("__syncthreads();")
-            run_code, n_amp = _amp_run_code(P, [(ai, *pos[ai]) for ai in st.amps], addr, n_amp, I.sign, I.flush,
-                                            not amputated & 4)
+            run_code, n_amp, sv = _amp_run_code(P, [(ai, *pos[ai]) for ai in st.amps], addr, n_amp, I.sign,
+                                                I.flush, not amputated & 4)
+            saved += sv
             code += run_code
             code.append("__syncthreads();  // the stage's dead slots are reused by the next one")
         used = {TP.support[a] for ai, _ in P.amps for a in ops[ai].args}
@@ -592,7 +591,7 @@ def emit_tab_struct(process: str, nt: int, epc_f: int, epc_d: int, amputated: in
 {NL.join("        " + x for x in code)}
     }}"""
 
-    amp_flops = TP.amplitude_flops_per_helicity(not amputated & 2) - _MERGED_FLOPS_SAVED[0]
+    amp_flops = TP.amplitude_flops_per_helicity(not amputated & 2) - saved
     task_init = ",\n    ".join("{%d, %d, %d, %d, %d, %d, %d, 0, 0}" % t for t in tasks)
     desc = (f"{'staged (' + str(stage) + ' amplitudes per stage)' if stage else 'resident'}"
             f"{', amputated vertex objects' if amputated & 1 else ''}{'' if amputated & 2 else ', colour groups'}")
