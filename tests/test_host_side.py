@@ -200,6 +200,37 @@ def test_colour_windows_replay_the_flow_updates():
     assert np.abs(J1 - J2).max() < 1e-12 * np.abs(J1).max()
 
 
+@pytest.mark.parametrize("process", ["gg_ttxgg", "gg_ttxggg"])
+def test_delta_r_guard_band_covers_fp32_error(orc, process):
+    """The sampler decides the Delta R cut in FP32 (eta = asinh(pz / pT)) and
+    re-decides in FP64 only pairs within 1e-3 of the cut; that band must be far
+    wider than the FP32 error of Delta R.  Checked on the oracle's accepted
+    momenta against the FP64 formula of the cut definition."""
+    w = WORKLOADS[process]
+    mom, _, _ = orc.rambo(w.seed, w.sqrt_s, w.masses_final, 0, 4000, w.cut_mask, 20.0, 0.4)
+    glu = [i for i, c in enumerate(w.cut_mask) if c]
+    k = mom[:, 2:, :][:, glu, :]
+    P = np.sqrt((k[..., 1:] ** 2).sum(-1))
+    eta64 = 0.5 * np.log((P + k[..., 3]) / (P - k[..., 3]))
+    phi64 = np.arctan2(k[..., 2], k[..., 1])
+    k32 = k.astype(np.float32)
+    eta32 = np.arcsinh(k32[..., 3] / np.sqrt(k32[..., 1] ** 2 + k32[..., 2] ** 2))
+    phi32 = np.arctan2(k32[..., 2], k32[..., 1])
+    worst = 0.0
+    for i in range(len(glu)):
+        for j in range(i + 1, len(glu)):
+            d64 = np.remainder(phi64[:, i] - phi64[:, j] + np.pi, 2 * np.pi) - np.pi
+            d32 = (phi32[:, i] - phi32[:, j]).astype(np.float32)
+            d32 = np.where(d32 > np.pi, d32 - 2 * np.pi, d32)
+            d32 = np.where(d32 < -np.pi, d32 + 2 * np.pi, d32)
+            dr64 = np.hypot(eta64[:, i] - eta64[:, j], d64)
+            dr32 = np.hypot((eta32[:, i] - eta32[:, j]).astype(np.float64), d32.astype(np.float64))
+            worst = max(worst, float(np.abs(dr32 - dr64).max()))
+            assert np.all(dr64 > 0.4)  # accepted events pass the FP64 cut
+    print(process, "largest FP32 error of Delta R", worst)
+    assert worst < 1e-4, worst
+
+
 # ---------------------------------------------------------------- C ABI
 def _declared_symbols(header="me.h"):
     src = open(os.path.join(ROOT, "include", header)).read()
