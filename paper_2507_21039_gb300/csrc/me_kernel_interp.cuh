@@ -355,6 +355,16 @@ template <class P, class T, bool TC = false, class C = T, bool SDE = false> cuda
     static size_t granted = 0;
     cudaError_t e = ensure_smem(me_kernel_interp<P, T, TC, C, SDE>, L::launch_bytes, granted);
     if (e != cudaSuccess) return e;
+    // the persistent grid is sized by the occupancy query, which takes the
+    // kernel's shared-memory carveout preference: ask for the largest carveout,
+    // so that it counts every CTA that fits the SM's shared memory
+    static bool carveout = false;
+    if (!carveout) {
+        e = cudaFuncSetAttribute(me_kernel_interp<P, T, TC, C, SDE>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 (int)cudaSharedmemCarveoutMaxShared);
+        if (e != cudaSuccess) return e;
+        carveout = true;
+    }
     int dev = 0, nsm = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
