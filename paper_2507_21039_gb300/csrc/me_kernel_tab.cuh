@@ -10,7 +10,9 @@
 //      particles into a shared-memory table, level by level, by all threads;
 //   4. each thread takes one good helicity (or several), evaluates that
 //      helicity's final amplitudes from table operands into the colour-flow
-//      vector J (registers), contracts J^+ C J, and accumulates in FP64;
+//      vector J (registers; amplitudes whose colour vectors agree up to a sign
+//      are summed first and added into J once), contracts J^+ C J, and
+//      accumulates in FP64;
 //   5. CTA reduction over helicities -> me2[event].
 // The per-thread live state is J plus the operands of the amplitudes in
 // flight, so the chain never spills.
