@@ -29,9 +29,10 @@ TAB_PROCESSES = {"gg_ttxg": (32, 1, 1, 1, 0, 1, 4), "gg_ttxgg": (64, 2, 2, 5, 60
 # processes evaluated with the staged descriptor kernel (me_kernel_interp.cuh)
 # process -> (threads per event, amplitudes per stage and schedule mode (as
 #             above) in FP32 / mixed, the same in FP64).  FP32 keeps J in shared
-#             memory, so its table must stay small (short stages); FP64 keeps J in
-#             a global scratch, its table alone fills shared memory.
-INTERP_PROCESSES = {"gg_ttxggg": (128, 16, 0, 16, 0)}
+#             memory, so the table peak of its stages must fit beside J; FP64
+#             keeps J in a global scratch.  One schedule for both precisions lets
+#             them share one descriptor set (in constant memory).
+INTERP_PROCESSES = {"gg_ttxggg": (128, 32, 0, 32, 0)}
 
 
 def _apply_kernel_overrides():
