@@ -157,6 +157,24 @@ def test_colour_groups_rebuild_every_amplitude_terms(orc, process):
     assert np.abs(J1 - J2).max() < 1e-12 * np.abs(J1).max()
 
 
+def test_descriptor_kernel_reads_its_descriptors_from_constant_memory():
+    """The default gg -> t t~ ggg schedule keeps its uniform descriptors within
+    the 64 KB constant bank (the emitter falls back to global memory, about 20%
+    slower, when they do not fit), one set for both precisions."""
+    from paper_2507_21039_gb300.gen.emit import INTERP_PROCESSES, emit_interp_struct
+
+    nt, sf, mf, sd, md = INTERP_PROCESSES["gg_ttxggg"]
+    assert (sf, mf) == (sd, md)
+    src, _ = emit_interp_struct("gg_ttxggg", nt, sf, colour_matrix(5)[0], mf)
+    for name in ("c_amps", "c_terms", "c_rounds", "c_stages", "c_stage_term", "c_diag"):
+        assert re.search(r"__constant__ \w+( \w+)? " + name + r"\[", src), name
+    sizes = {"IAmp": 16, "IRound": 8, "IStage": 8, "unsigned short": 2, "int": 4}
+    total = 0
+    for ctype, name, n in re.findall(r"__constant__ ([\w ]+?) (c_\w+)\[(\d+)\]", src):
+        total += sizes[ctype] * int(n)
+    assert total <= 64 * 1024, total
+
+
 def test_colour_windows_replay_the_flow_updates():
     """The slot-encoded colour updates of the descriptor kernel (per-thread
     accumulator slots, first touch assigns, J += slots at each window's end)
