@@ -80,6 +80,12 @@ def _load():
             lib.orc_iden.argtypes = [i]
             lib.orc_iden.restype = d
             lib.orc_max_threads.restype = i
+            lib.orc_dy_partial_amps.argtypes = [i, P, i, i, i, P]
+            lib.orc_dy_partial_amps.restype = i
+            lib.orc_dy_me2.argtypes = [i, P, i64, d, i, P]
+            lib.orc_dy_me2.restype = i
+            lib.orc_dy_lepton_currents.argtypes = [P, P, i, i, i, P]
+            lib.orc_bg_partial.argtypes = [i, P, P, P, P, d, P, P]
             _lib = lib
     return _lib
 
@@ -254,3 +260,49 @@ def su3():
 
 def max_threads() -> int:
     return _load().orc_max_threads()
+
+
+# ---------------------------------------------------------------- Drell-Yan
+# u(0) ubar(1) -> e+(2) e-(3) + n gluons (4..), photon and Z exchange; bosons:
+# bit 0 photon, bit 1 Z.
+
+def dy_partial_amps(n, p_event, helicity, gauge_gluon=-1, bosons=3) -> np.ndarray:
+    """Colour-ordered partial amplitudes of u ubar -> e+ e- + n g (gluon
+    couplings stripped, electroweak ones included), lexicographic gluon orders."""
+    import math
+    p = np.ascontiguousarray(p_event, dtype=np.float64)
+    out = np.zeros(math.factorial(n), dtype=np.complex128)
+    if _load().orc_dy_partial_amps(int(n), _ptr(p), int(helicity), int(gauge_gluon), int(bosons), _ptr(out)) < 0:
+        raise ValueError("oracle dy_partial_amps: n must be 0..4")
+    return out
+
+
+def dy_me2(n, momenta, alpha_s=0.118, bosons=3) -> np.ndarray:
+    """Spin- and colour-averaged |M|^2 of u ubar -> e+ e- + n g per event (FP64)."""
+    p = np.ascontiguousarray(momenta, dtype=np.float64)
+    out = np.zeros(p.shape[0])
+    if _load().orc_dy_me2(int(n), _ptr(p), p.shape[0], float(alpha_s), int(bosons), _ptr(out)) != 0:
+        raise ValueError("oracle dy_me2: n must be 0..4")
+    return out
+
+
+def dy_lepton_currents(p_ep, p_em, l_ep, l_em, bosons=3) -> np.ndarray:
+    """Lepton currents (photon, Z) of the e+ e- pair, each over its propagator."""
+    a = np.ascontiguousarray(p_ep, dtype=np.float64)
+    b = np.ascontiguousarray(p_em, dtype=np.float64)
+    out = np.zeros((2, 4), dtype=np.complex128)
+    _load().orc_dy_lepton_currents(_ptr(a), _ptr(b), int(l_ep), int(l_em), int(bosons), _ptr(out))
+    return out
+
+
+def bg_partial(eps, P, ubar, pt, mt, v) -> complex:
+    """Colour-ordered quark-line amplitude with k gluon wavefunctions eps[k][4]
+    of outgoing momenta P[k][4] (the gluon recursion on its own)."""
+    e = np.ascontiguousarray(eps, dtype=np.complex128)
+    m = np.ascontiguousarray(P, dtype=np.float64)
+    ub = np.ascontiguousarray(ubar, dtype=np.complex128)
+    q = np.ascontiguousarray(pt, dtype=np.float64)
+    vv = np.ascontiguousarray(v, dtype=np.complex128)
+    out = np.zeros(1, dtype=np.complex128)
+    _load().orc_bg_partial(e.shape[0], _ptr(e), _ptr(m), _ptr(ub), _ptr(q), float(mt), _ptr(vv), _ptr(out))
+    return complex(out[0])

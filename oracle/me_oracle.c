@@ -21,6 +21,9 @@
  *   - |M|^2 = (1/IDEN) sum_h g^{2k} A_h^dagger C A_h, with no helicity filter
  *     (Sec. 3.1 sums all non-vanishing spin configurations; summing all of them
  *     is the same number and catches a wrong GPU helicity mask).
+ * Drell-Yan u ubar -> e+ e- + n g (the paper's second standalone workload,
+ * Sec. 4) uses the same quark-line recursion with one colourless photon/Z
+ * insertion (section at the end of this file).
  * Extra pins live here too: a colour-dressed brute force (explicit colour
  * indices, full f^{abc} vertices, no colour decomposition), the closed forms for
  * e+e- -> mu+mu- (photon only) and gg -> t tbar (Combridge 1979), and
@@ -541,11 +544,10 @@ static void v3(const cx J1[4], const double k1[4], const cx J2[4], const double 
  * position i (already permuted).  ubar: outgoing-quark row spinor with momentum
  * pt; v: outgoing-antiquark column spinor.  Returns the partial amplitude with
  * couplings stripped (M = g^k sum S_sigma A_sigma). */
-static cx bg_partial(int k, cx eps[][4], double P[][4], const cx ubar[4], const double pt[4], double mt,
-                     const cx v[4])
+/* Off-shell gluon currents J[i][j] of every contiguous colour-ordered range
+ * i..j of the k gluons (Berends-Giele), with their summed momenta PS[i][j]. */
+static void gluon_currents(int k, cx eps[][4], double P[][4], cx J[MAXG][MAXG][4], double PS[MAXG][MAXG][4])
 {
-    cx J[MAXG][MAXG][4];
-    double PS[MAXG][MAXG][4];
     for (int len = 1; len <= k; ++len)
         for (int i = 0; i + len - 1 < k; ++i) {
             int j = i + len - 1;
@@ -573,6 +575,14 @@ static cx bg_partial(int k, cx eps[][4], double P[][4], const cx ubar[4], const 
             double p2 = mdot(PS[i][j], PS[i][j]);
             for (int mu = 0; mu < 4; ++mu) J[i][j][mu] = (-I / p2) * tmp[mu];
         }
+}
+
+static cx bg_partial(int k, cx eps[][4], double P[][4], const cx ubar[4], const double pt[4], double mt,
+                     const cx v[4])
+{
+    cx J[MAXG][MAXG][4];
+    double PS[MAXG][MAXG][4];
+    gluon_currents(k, eps, P, J, PS);
     /* quark line from the outgoing quark */
     cx U[MAXG + 1][4];
     memcpy(U[0], ubar, sizeof(cx) * 4);
@@ -1214,4 +1224,236 @@ int orc_sde(int proc, const double *p, double mt, const int *hels, int nh, doubl
         for (int d = 0; d < nd; ++d) w2_out[d] += sde_diagram_w2(&sde_diags[k][d], cur, PS, ubar, p + 8, mt, v);
     }
     return nd;
+}
+
+/* ------------------------------------------------------------------ */
+/* Drell-Yan u ubar -> e+ e- + n g through a photon and a Z             */
+/* ------------------------------------------------------------------ */
+/* Particles: 0 u (incoming), 1 ubar (incoming), 2 e+, 3 e-, 4.. gluons
+ * (outgoing).  Electroweak parameters fixed (G_F scheme values): alpha =
+ * 1/132.507, M_Z = 91.188, Gamma_Z = 2.441404, M_W = 80.419002, sin^2 theta_W
+ * = 1 - M_W^2/M_Z^2.  Vertices -i gamma^mu (gL P_L + gR P_R) with
+ * P_L = diag(1,1,0,0) (left-handed upper components): photon gL = gR = e Q;
+ * Z gL = e (T3 - Q sw^2)/(sw cw), gR = -e Q sw^2/(sw cw).  Propagators
+ * -i g_{mn}/s (photon) and -i g_{mn}/(s - M_Z^2 + i M_Z Gamma_Z) (Z; its
+ * k_m k_n term vanishes on the conserved massless lepton current).  The
+ * boson and the lepton pair enter the quark line as one colourless insertion
+ * i gamma^mu (gL^u P_L + gR^u P_R) L_mu (the three factors -i combine to i),
+ * L^mu = sum_V ubar(e-) gamma^mu (gL^e P_L + gR^e P_R) v(e+) / D_V.
+ * Colour: M = g^n sum_sigma (T^{a_s1}..T^{a_sn})_{i j} A_sigma, the string
+ * read along the quark line from the ubar end, n = 0 giving delta_ij. */
+static const double DY_ALPHA = 1.0 / 132.507, DY_MZ = 91.188, DY_WZ = 2.441404, DY_MW = 80.419002;
+
+static void dy_couplings(int boson, double t3, double q, double *gl, double *gr)
+{
+    const double e = sqrt(4.0 * M_PI * DY_ALPHA);
+    const double cw = DY_MW / DY_MZ, sw = sqrt(1.0 - cw * cw);
+    if (boson == 0) {
+        *gl = *gr = e * q;
+    } else {
+        *gl = e * (t3 - q * sw * sw) / (sw * cw);
+        *gr = -e * q * sw * sw / (sw * cw);
+    }
+}
+
+/* lepton currents L_V^mu (upper index) of the photon (V = 0) and the Z (V = 1),
+ * each divided by its propagator denominator; bosons: bit 0 photon, bit 1 Z
+ * (a boson left out gets a zero current) */
+void orc_dy_lepton_currents(const double *p_ep, const double *p_em, int l_ep, int l_em, int bosons, cx L[2][4])
+{
+    init_gamma();
+    cx v[4], u[4], ub[4];
+    orc_spinor_v(p_ep, 0.0, l_ep, v);
+    orc_spinor_u(p_em, 0.0, l_em, u);
+    orc_bar(u, ub);
+    double q[4];
+    for (int mu = 0; mu < 4; ++mu) q[mu] = p_ep[mu] + p_em[mu];
+    const double s = mdot(q, q);
+    for (int b = 0; b < 2; ++b) {
+        for (int mu = 0; mu < 4; ++mu) L[b][mu] = 0;
+        if (!((bosons >> b) & 1)) continue;
+        double gl, gr;
+        dy_couplings(b, -0.5, -1.0, &gl, &gr);
+        const cx den = b == 0 ? (cx)s : s - DY_MZ * DY_MZ + I * DY_MZ * DY_WZ;
+        const cx vc[4] = {gl * v[0], gl * v[1], gr * v[2], gr * v[3]}; /* (gL P_L + gR P_R) v */
+        for (int mu = 0; mu < 4; ++mu) {
+            cx t[4];
+            row_times(ub, GAM[mu], t);
+            L[b][mu] = (t[0] * vc[0] + t[1] * vc[1] + t[2] * vc[2] + t[3] * vc[3]) / den;
+        }
+    }
+}
+
+/* colour-ordered partial amplitude of u ubar -> e+ e- + n g for the gluons
+ * in colour order eps[0..n-1] (outgoing momenta P): the quark line runs from
+ * the ubar row spinor vb (fermion flow outgoing with momentum -p_ubar) to the
+ * u column spinor u; the colourless insertion of the lepton currents L
+ * (momentum qL) is placed at every position along the line */
+static cx dy_partial(int n, cx eps[][4], double P[][4], const cx vb[4], const double p_ubar[4], const cx u[4],
+                     cx L[2][4], const double qL[4])
+{
+    cx J[MAXG][MAXG][4];
+    double PS[MAXG][MAXG][4];
+    if (n > 0) gluon_currents(n, eps, P, J, PS);
+    /* insertion matrix without its factor i: sum_V gamma^mu L_V,mu (gL^u P_L + gR^u P_R) */
+    cx M[4][4];
+    memset(M, 0, sizeof M);
+    for (int b = 0; b < 2; ++b) {
+        double gl, gr;
+        dy_couplings(b, 0.5, 2.0 / 3.0, &gl, &gr);
+        cx S[4][4];
+        slash_c(L[b], S);
+        for (int r = 0; r < 4; ++r)
+            for (int c = 0; c < 4; ++c) M[r][c] += S[r][c] * (c < 2 ? gl : gr);
+    }
+    /* U0[j]: gluons 0..j-1 attached, no insertion; U1[j]: gluons 0..j-1 and
+     * the insertion attached; both carry their propagator */
+    cx U0[MAXG + 1][4], U1[MAXG + 1][4];
+    memcpy(U0[0], vb, sizeof(cx) * 4);
+    cx amp = 0;
+    for (int j = 0; j <= n; ++j) {
+        double q0[4];
+        for (int mu = 0; mu < 4; ++mu) q0[mu] = -p_ubar[mu] + (j > 0 ? PS[0][j - 1][mu] : 0.0);
+        if (j > 0) { /* the gluon range m..j-1 attached last, no insertion yet */
+            cx X[4] = {0, 0, 0, 0};
+            for (int m = 0; m < j; ++m) {
+                cx S[4][4], t[4];
+                slash_c(J[m][j - 1], S);
+                row_times(U0[m], S, t);
+                for (int c = 0; c < 4; ++c) X[c] += I * t[c];
+            }
+            cx S[4][4], t[4];
+            slash_r(q0, S);
+            row_times(X, S, t);
+            const double d0 = mdot(q0, q0);
+            for (int c = 0; c < 4; ++c) U0[j][c] = I * t[c] / d0;
+        }
+        /* the insertion attached last (after gluons 0..j-1), or a gluon range
+         * m..j-1 attached after it */
+        cx Y[4], t[4];
+        row_times(U0[j], M, t);
+        for (int c = 0; c < 4; ++c) Y[c] = I * t[c];
+        for (int m = 0; m < j; ++m) {
+            cx S[4][4];
+            slash_c(J[m][j - 1], S);
+            row_times(U1[m], S, t);
+            for (int c = 0; c < 4; ++c) Y[c] += I * t[c];
+        }
+        if (j == n) {
+            for (int c = 0; c < 4; ++c) amp += Y[c] * u[c];
+        } else {
+            double q1[4];
+            for (int mu = 0; mu < 4; ++mu) q1[mu] = q0[mu] + qL[mu];
+            cx S[4][4];
+            slash_r(q1, S);
+            row_times(Y, S, t);
+            const double d1 = mdot(q1, q1);
+            for (int c = 0; c < 4; ++c) U1[j][c] = I * t[c] / d1;
+        }
+    }
+    return amp;
+}
+
+/* external states of u ubar -> e+ e- + n g for helicity index h (bit
+ * (npar-1-i) set: particle i has helicity +1); gauge_gluon >= 0 replaces that
+ * gluon's polarisation by its momentum */
+static void dy_externals(int n, const double *p, int h, int gauge_gluon, int bosons, cx eps[][4], double P[][4],
+                         cx vb[4], cx u[4], cx L[2][4], double qL[4])
+{
+    const int npar = 4 + n;
+    int l[4 + MAXG];
+    for (int i = 0; i < npar; ++i) l[i] = ((h >> (npar - 1 - i)) & 1) ? 1 : -1;
+    orc_spinor_u(p + 0, 0.0, l[0], u);
+    cx v[4];
+    orc_spinor_v(p + 4, 0.0, l[1], v);
+    orc_bar(v, vb);
+    orc_dy_lepton_currents(p + 8, p + 12, l[2], l[3], bosons, L);
+    for (int mu = 0; mu < 4; ++mu) qL[mu] = p[8 + mu] + p[12 + mu];
+    for (int g = 0; g < n; ++g) {
+        const double *pe = p + 4 * (4 + g);
+        if (g == gauge_gluon) {
+            for (int mu = 0; mu < 4; ++mu) eps[g][mu] = pe[mu];
+        } else {
+            orc_polvec(pe, l[4 + g], eps[g]);
+            for (int mu = 0; mu < 4; ++mu) eps[g][mu] = conj(eps[g][mu]);
+        }
+        for (int mu = 0; mu < 4; ++mu) P[g][mu] = pe[mu];
+    }
+}
+
+/* all n! partial amplitudes (gluon orders lexicographic) of one event and helicity */
+int orc_dy_partial_amps(int n, const double *p, int h, int gauge_gluon, int bosons, cx *A_out)
+{
+    if (n < 0 || n > 4) return -1;
+    init_gamma();
+    cx eps[MAXG][4], vb[4], u[4], L[2][4];
+    double P[MAXG][4], qL[4];
+    dy_externals(n, p, h, gauge_gluon, bosons, eps, P, vb, u, L, qL);
+    if (n == 0) {
+        A_out[0] = dy_partial(0, eps, P, vb, p + 4, u, L, qL);
+        return 1;
+    }
+    int perms[MAXPERM * MAXG];
+    const int np = orc_perms(n, perms);
+    for (int s = 0; s < np; ++s) {
+        cx e2[MAXG][4];
+        double P2[MAXG][4];
+        for (int i = 0; i < n; ++i) {
+            memcpy(e2[i], eps[perms[s * n + i]], sizeof(cx) * 4);
+            memcpy(P2[i], P[perms[s * n + i]], sizeof(double) * 4);
+        }
+        A_out[s] = dy_partial(n, e2, P2, vb, p + 4, u, L, qL);
+    }
+    return np;
+}
+
+/* the colour-ordered Berends-Giele amplitude of one quark line and k gluons
+ * with given external wavefunctions (exposed for the identities that relate
+ * the Drell-Yan recursion to the gluon recursion) */
+void orc_bg_partial(int k, const cx *eps /*[k][4]*/, const double *P /*[k][4]*/, const cx ubar[4], const double pt[4],
+                    double mt, const cx v[4], cx *out)
+{
+    init_gamma();
+    cx e2[MAXG][4];
+    double P2[MAXG][4];
+    for (int i = 0; i < k; ++i) {
+        memcpy(e2[i], eps + 4 * i, sizeof(cx) * 4);
+        memcpy(P2[i], P + 4 * i, sizeof(double) * 4);
+    }
+    *out = bg_partial(k, e2, P2, ubar, pt, mt, v);
+}
+
+/* |M|^2 of u ubar -> e+ e- + n g per event: sum over all 2^(4+n) helicities
+ * and colours, averaged over the initial spins (4) and colours (9), divided
+ * by n! for the identical gluons; alpha_s for the gluon couplings */
+int orc_dy_me2(int n, const double *mom, int64_t nevt, double alpha_s, int bosons, double *me2_out)
+{
+    if (n < 0 || n > 4) return -1;
+    init_gamma();
+    init_su3();
+    const double *C = n > 0 ? colour_matrix_cached(n) : NULL;
+    const int npar = 4 + n, nhel = 1 << npar, np = (int)factorial(n);
+    const double gs2n = pow(4.0 * M_PI * alpha_s, n);
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int64_t e = 0; e < nevt; ++e) {
+        const double *p = mom + (size_t)e * npar * 4;
+        double tot = 0;
+        cx A[MAXPERM];
+        for (int h = 0; h < nhel; ++h) {
+            orc_dy_partial_amps(n, p, h, -1, bosons, A);
+            double s = 0;
+            if (n == 0) {
+                s = 3.0 * creal(A[0] * conj(A[0])); /* sum_ij |delta_ij|^2 = 3 */
+            } else {
+                for (int a = 0; a < np; ++a) {
+                    cx row = 0;
+                    for (int b = 0; b < np; ++b) row += C[a * np + b] * A[b];
+                    s += creal(conj(A[a]) * row);
+                }
+            }
+            tot += gs2n * s;
+        }
+        me2_out[e] = tot / (4.0 * 9.0 * factorial(n));
+    }
+    return 0;
 }

@@ -2,8 +2,8 @@
 
 Each case plants one mistake in a copy of the oracle (a dropped term, a
 wrong sign, a transposed operand, a wrong constant or factor), builds the copy
-in a scratch directory and runs the pin suite (tests/test_oracle_pins.py)
-against it in a subprocess; at least one pin must fail.  The unmodified copy
+in a scratch directory and runs the pin suites (tests/test_oracle_pins.py,
+tests/test_oracle_dy.py) against it in a subprocess; at least one pin must fail.  The unmodified copy
 must pass, so a failure is the mistake's doing.  CPU only."""
 import os
 import shutil
@@ -40,6 +40,12 @@ MUTATIONS = [
     ("SU(3) generator sign", "TG[1][0][1] = -0.5 * I; TG[1][1][0] = 0.5 * I;",
      "TG[1][0][1] = 0.5 * I; TG[1][1][0] = 0.5 * I;"),
     ("identical-gluon factor", "return 4.0 * 64.0 * factorial(proc - 1);", "return 4.0 * 64.0 * factorial(proc);"),
+    ("Drell-Yan: Z right-handed coupling sign", "*gr = -e * q * sw * sw / (sw * cw);",
+     "*gr = e * q * sw * sw / (sw * cw);"),
+    ("Drell-Yan: quark chiralities swapped at the insertion", "M[r][c] += S[r][c] * (c < 2 ? gl : gr);",
+     "M[r][c] += S[r][c] * (c < 2 ? gr : gl);"),
+    ("Drell-Yan: insertion propagator misses the lepton-pair momentum",
+     "for (int mu = 0; mu < 4; ++mu) q1[mu] = q0[mu] + qL[mu];", "for (int mu = 0; mu < 4; ++mu) q1[mu] = q0[mu];"),
 ]
 
 # the heaviest pins are not needed to catch these mistakes
@@ -49,7 +55,8 @@ PIN_SELECTION = "not k5 and not some_helicities and not ttxggg"
 def run_pins(workdir):
     env = dict(os.environ, PYTHONPATH=ROOT)
     cmd = [sys.executable, "-m", "pytest", "-q", "-x", "-p", "no:cacheprovider",
-           os.path.join(ROOT, "tests", "test_oracle_pins.py"), "-k", PIN_SELECTION]
+           os.path.join(ROOT, "tests", "test_oracle_pins.py"), os.path.join(ROOT, "tests", "test_oracle_dy.py"),
+           "-k", PIN_SELECTION]
     r = subprocess.run(cmd, cwd=workdir, env=env, capture_output=True, text=True, timeout=600)
     return r.returncode, r.stdout[-2000:]
 
