@@ -231,3 +231,43 @@ def diagram_phase(d):
 def permutation_index(k: int):
     """lexicographic permutation order of range(k) -> index"""
     return {p: i for i, p in enumerate(itertools.permutations(range(k)))}
+
+
+# ---------------------------------------------------------------- Drell-Yan
+# u ubar -> e+ e- + n g: the quark line (read from the ubar end) carries the
+# gluon trees and one colourless element EW, the photon/Z coupling to the
+# lepton pair.  The EW element has no colour and no gluon leaves.
+EW = Tree("ew")
+
+
+def dy_diagrams(k: int):
+    """Amplitude terms of u ubar -> e+ e- + k g: every sequence of gluon trees
+    along the quark line (as in `diagrams`) with EW inserted at each position."""
+    out = []
+    seqs = diagrams(k) if k else [()]
+    for d in seqs:
+        for pos in range(len(d) + 1):
+            out.append(d[:pos] + (EW,) + d[pos:])
+    return out
+
+
+def dy_diagram_colour(d):
+    """colour of a Drell-Yan term: that of its gluon trees (EW is colourless)"""
+    return diagram_colour(tuple(t for t in d if t.kind != "ew"))
+
+
+def dy_diagram_phase(d):
+    """i per quark-line vertex (gluon or EW), i per quark propagator, -i per
+    gluon propagator and per four-gluon vertex (the EW element's own factors,
+    two vertices and the boson propagator, combine to i and are counted as its
+    quark-line vertex)"""
+    m = len(d)
+    ph = ONE
+    for _ in range(2 * m - 1):
+        ph = cmul(ph, (0, 1))
+    for t in d:
+        if t.kind == "ew":
+            continue
+        for _ in range(t.n_internal() + t.n_v4()):
+            ph = cmul(ph, (0, -1))
+    return ph

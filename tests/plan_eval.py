@@ -269,3 +269,88 @@ def evaluate_staged(orc, I, p, h, mt, merge=False):
                 gsum = 0.0
     assert gsum == 0.0
     return J
+
+
+# Drell-Yan electroweak parameters (the same values the oracle states)
+_DY_ALPHA, _DY_MZ, _DY_MW = 1.0 / 132.507, 91.188, 80.419002
+
+
+def _dy_quark_couplings():
+    """(gL, gR) of the u quark to the photon and to the Z"""
+    e = np.sqrt(4 * np.pi * _DY_ALPHA)
+    cw = _DY_MW / _DY_MZ
+    sw = np.sqrt(1 - cw * cw)
+    q, t3 = 2 / 3, 0.5
+    return (e * q, e * q), (e * (t3 - q * sw * sw) / (sw * cw), -e * q * sw * sw / (sw * cw))
+
+
+def evaluate_dy(orc, plan, p, h):
+    """Colour-flow amplitudes J (gluon couplings stripped) of a Drell-Yan plan
+    (gen/plan.py build_plan_dy) for event p, helicity h.  The lepton currents
+    over their propagators come from the pinned oracle; the quark-side chiral
+    couplings are applied here."""
+    npar = plan.npar
+    lam = [1 if (h >> (npar - 1 - i)) & 1 else -1 for i in range(npar)]
+    qL = p[2] + p[3]
+    lines = []
+    for ln in plan.lines:
+        if ln.kind == "g":
+            q = sum(p[plan.gluon_ext[g]] for g in ln.gluons)
+            lines.append((q, 1.0 / dot(q, q) if len(ln.gluons) > 1 else 0.0))
+        else:
+            q = -p[1] + sum((p[plan.gluon_ext[g]] for g in ln.gluons), np.zeros(4)) + (qL if ln.kind == "qe" else 0)
+            lines.append((q, 1.0 / dot(q, q)))
+    Lv = orc.dy_lepton_currents(p[2], p[3], lam[2], lam[3])
+    cq = _dy_quark_couplings()
+    LL = cq[0][0] * Lv[0] + cq[1][0] * Lv[1]
+    LR = cq[0][1] * Lv[0] + cq[1][1] * Lv[1]
+    PL, PR = np.diag([1.0, 1.0, 0.0, 0.0]), np.diag([0.0, 0.0, 1.0, 1.0])
+
+    def mlr(a, b):  # the chiral vertex slash(L_L) P_L + slash(L_R) P_R
+        return slash(a) @ PL + slash(b) @ PR
+
+    vals = []
+    for op in plan.ops:
+        a = [vals[i] for i in op.args]
+        k = op.kind
+        if k == "ext_v":
+            vals.append(np.conj(orc.polvec(p[op.ext], lam[op.ext])))
+        elif k == "ext_fo":
+            vals.append(orc.bar(orc.spinor_v(p[1], 0.0, lam[1])))
+        elif k == "ext_fi":
+            vals.append(orc.spinor_u(p[0], 0.0, lam[0]))
+        elif k == "ext_lepL":
+            vals.append(LL)
+        elif k == "ext_lepR":
+            vals.append(LR)
+        elif k == "VVV1P0_1":
+            A, B = a
+            PA, PB = lines[op.mom[0]][0], lines[op.mom[1]][0]
+            k1, k2, k3 = -PA, -PB, PA + PB
+            v = dot(A, B) * (k1 - k2) + B * dot(k2 - k3, A) + A * dot(k3 - k1, B)
+            vals.append(lines[op.line][1] * v)
+        elif k.startswith("VVVV") and k.endswith("P0_1"):
+            vals.append(lines[op.line][1] * _v4(k[:5], *a))
+        elif k == "FFV1_2":
+            q, inv = lines[op.line]
+            vals.append(inv * (a[0] @ slash(a[1]) @ slash(q)))
+        elif k == "FFV1_1":
+            q, inv = lines[op.line]
+            vals.append(inv * (slash(q) @ slash(a[0]) @ a[1]))
+        elif k == "FFVLR_2":
+            q, inv = lines[op.line]
+            vals.append(inv * (a[0] @ mlr(a[1], a[2]) @ slash(q)))
+        elif k == "FFVLR_1":
+            q, inv = lines[op.line]
+            vals.append(inv * (slash(q) @ mlr(a[0], a[1]) @ a[2]))
+        elif k == "FFV1_0":
+            vals.append(a[0] @ slash(a[1]) @ a[2])
+        elif k == "FFVLR_0":
+            vals.append(a[0] @ mlr(a[1], a[2]) @ a[3])
+        else:
+            raise ValueError(k)
+    J = np.zeros(plan.ncol, dtype=complex)
+    for ai, terms in plan.amps:
+        for col, c in terms:
+            J[col] += complex(c[0], c[1]) * vals[ai]
+    return J

@@ -126,6 +126,25 @@ def test_generator_flop_counts_positive():
         assert P.colour_flops_per_helicity() > 0
 
 
+@pytest.mark.parametrize("k", [0, 1, 2, 3])
+def test_drell_yan_plan_reproduces_oracle_partial_amplitudes(orc, k):
+    """The generator's Drell-Yan plans (quark-line diagrams with one photon/Z
+    insertion, chiral vertices, colour and phases) give the oracle's
+    colour-ordered partial amplitudes of u ubar -> e+ e- + k g."""
+    from paper_2507_21039_gb300.gen.plan import build_plan_dy
+    from plan_eval import evaluate_dy
+
+    P = build_plan_dy(k)
+    assert P.ncol == max(1, math.factorial(k))
+    cut = [0, 0] + [1] * k if k else None
+    mom, _, _ = orc.rambo(5, 200.0, [0.0] * (2 + k), 0, 2, cut, 20.0, 0.4)
+    for p in mom:
+        scale = max(np.abs(orc.dy_partial_amps(k, p, h)).max() for h in range(0, 1 << (4 + k), 3))
+        for h in range(0, 1 << (4 + k), 5):
+            J = evaluate_dy(orc, P, p, h)
+            assert np.abs(J - orc.dy_partial_amps(k, p, h)).max() < 1e-12 * scale
+
+
 @pytest.mark.parametrize("process", ["gg_ttx", "gg_ttxg", "gg_ttxgg", "gg_ttxggg"])
 def test_colour_groups_rebuild_every_amplitude_terms(orc, process):
     """Each amplitude's colour terms are its sign times its group's normalised
