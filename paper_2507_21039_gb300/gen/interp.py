@@ -3,8 +3,9 @@
 The helicity-recycled tables of tabplan.py hold every off-shell object for
 every configuration of its support; for 7 external particles that is 12750
 wavefunctions per event, far beyond shared memory.  Here the amplitudes are
-ordered greedily (each next amplitude needs the fewest new table entries) and
-cut into stages.  A stage first computes the objects its amplitudes need that
+ordered greedily by colour group (amplitudes whose colour vectors agree up to
+a sign are summed before one update of J; each next group needs the fewest new
+table entries, its members stay adjacent) and cut into stages.  A stage first computes the objects its amplitudes need that
 are not yet in the table (cooperatively, level by level), then every thread
 evaluates the stage's amplitudes for its own helicity.  A table object lives
 from the stage that computes it to the last stage that reads it; its slots are
