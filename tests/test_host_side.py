@@ -194,6 +194,33 @@ def test_descriptor_kernel_reads_its_descriptors_from_constant_memory():
     assert total <= 64 * 1024, total
 
 
+def test_interpreter_descriptors_encode_the_colour_groups():
+    """The emitted amplitude descriptors of gg -> t t~ ggg carry, in stage
+    order, each amplitude's sign in its colour group (kind bit 7) and, on the
+    group's last member only, the group's colour terms (flow, sign of i)."""
+    from paper_2507_21039_gb300.gen.emit import INTERP_PROCESSES, emit_interp_struct
+    from paper_2507_21039_gb300.gen.interp import AMP_KINDS
+
+    nt, sf, mf, _, _ = INTERP_PROCESSES["gg_ttxggg"]
+    src, I = emit_interp_struct("gg_ttxggg", nt, sf, colour_matrix(5)[0], mf)
+    amps = re.search(r"c_amps\[\d+\] = \{(.*?)\n\};", src, re.S).group(1)
+    rows = [(int(a), int(b)) for a, b in re.findall(r"\}, (\d+), \d+, \d+, (\d+)\}", amps)]
+    terms = [int(x) for x in re.findall(r"-?\d+", re.search(r"\bc_terms\[\d+\] = \{(.*?)\};", src, re.S).group(1))]
+    order = [ai for st in I.stages for ai in st.amps]
+    assert len(rows) == len(order) == len(I.tab.plan.amps)
+    P = I.tab.plan
+    t = 0
+    for (kind, nterm), ai in zip(rows, order):
+        assert AMP_KINDS[kind & 0x3F] == P.ops[P.amps[ai][0]].kind
+        assert bool(kind & 0x80) == (I.sign[ai] < 0)
+        flush = I.flush.get(ai, ())
+        assert nterm == len(flush)
+        for col, c in flush:
+            assert terms[t] == col | (0x8000 if c == (0, -1) else 0)
+            t += 1
+    assert t == len(terms)
+
+
 def test_colour_windows_replay_the_flow_updates():
     """The slot-encoded colour updates of the descriptor kernel (per-thread
     accumulator slots, first touch assigns, J += slots at each window's end)
