@@ -46,6 +46,12 @@ MUTATIONS = [
      "M[r][c] += S[r][c] * (c < 2 ? gr : gl);"),
     ("Drell-Yan: insertion propagator misses the lepton-pair momentum",
      "for (int mu = 0; mu < 4; ++mu) q1[mu] = q0[mu] + qL[mu];", "for (int mu = 0; mu < 4; ++mu) q1[mu] = q0[mu];"),
+    ("diagram weights: four-gluon structure repeated",
+     "cur[t][v + 1][mu] = inv * (ab * C[mu] - bc * A[mu]);", "cur[t][v + 1][mu] = inv * (ab * C[mu] - ac * B[mu]);"),
+    ("diagram weights: three-gluon vertex legs' momenta swapped",
+     "v3(cur[a][va], ka, cur[b][vb], kb, o);", "v3(cur[a][va], kb, cur[b][vb], ka, o);"),
+    ("diagram weights: sign of the top mass in the propagator denominator",
+     "const double den = mdot(q, q) - mt * mt;", "const double den = mdot(q, q) + mt * mt;"),
 ]
 
 # the heaviest pins are not needed to catch these mistakes

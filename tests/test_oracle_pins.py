@@ -537,6 +537,179 @@ def test_sde_gg_ttx_diagrams_by_traces(orc):
             assert abs(by[key] / ref[key] - 1) < 1e-12, (key, by[key], ref[key])
 
 
+# ---------------------------------------------------------------- diagrams one by one, any gluon count
+def _dirac_rep_gammas():
+    """Dirac representation (gamma^0 = diag(1, 1, -1, -1)): traces do not depend
+    on the representation, so this pin shares no spinor or matrix convention
+    with the oracle (which works in the chiral representation)."""
+    pauli = [np.array([[0, 1], [1, 0]]), np.array([[0, -1j], [1j, 0]]), np.array([[1, 0], [0, -1]])]
+    g0 = np.zeros((4, 4), dtype=complex)
+    g0[:2, :2], g0[2:, 2:] = np.eye(2), -np.eye(2)
+    out = [g0]
+    for s in pauli:
+        g = np.zeros((4, 4), dtype=complex)
+        g[:2, 2:], g[2:, :2] = s, -s
+        out.append(g)
+    return out
+
+
+def _linear_polarisations(k3):
+    """Two real unit vectors (0, e) transverse to the spatial momentum k3 (Gram-
+    Schmidt from fixed reference directions): sum over them of e^mu e^nu is the
+    same transverse projector as the sum over the two helicity vectors."""
+    n = k3 / np.linalg.norm(k3)
+    ref = np.array([0.3, 0.2, 1.0]) if abs(n[2]) < 0.9 else np.array([1.0, 0.4, 0.1])
+    e1 = ref - np.dot(ref, n) * n
+    e1 /= np.linalg.norm(e1)
+    e2 = np.cross(n, e1)
+    return [np.concatenate(([0.0], e1)), np.concatenate(([0.0], e2))]
+
+
+def _trees(leaves):
+    """Every tree of three- and four-gluon vertices whose external gluons are
+    `leaves` (a sorted tuple of external indices): ('leaf', e), ('v3', a, b) or
+    ('v4', a, b, c), each split counted once."""
+    if len(leaves) == 1:
+        return [("leaf", leaves[0])]
+    out = []
+    first, rest = leaves[0], leaves[1:]
+    for r in range(len(rest)):               # {first} + some of the rest | the others
+        for extra in itertools.combinations(rest, r):
+            a = (first,) + extra
+            b = tuple(x for x in rest if x not in extra)
+            out += [("v3", ta, tb) for ta in _trees(a) for tb in _trees(b)]
+    for r in range(len(rest)):               # three parts, each split counted once
+        for extra in itertools.combinations(rest, r):
+            a = (first,) + extra
+            others = tuple(x for x in rest if x not in extra)
+            if len(others) < 2:
+                continue
+            second, rest2 = others[0], others[1:]
+            for r2 in range(len(rest2)):
+                for extra2 in itertools.combinations(rest2, r2):
+                    b = (second,) + extra2
+                    c = tuple(x for x in rest2 if x not in extra2)
+                    out += [("v4", ta, tb, tc) for ta in _trees(a) for tb in _trees(b) for tc in _trees(c)]
+    return out
+
+
+def _ordered_partitions(items):
+    """Ordered lists of non-empty blocks covering `items` (the trees met along the
+    quark line, from the top end)."""
+    if not items:
+        yield []
+        return
+    for r in range(1, len(items) + 1):
+        for block in itertools.combinations(items, r):
+            rest = tuple(x for x in items if x not in block)
+            for tail in _ordered_partitions(rest):
+                yield [block] + tail
+
+
+def _leaves_mask(t):
+    return 1 << t[1] if t[0] == "leaf" else sum(_leaves_mask(c) for c in t[1:])
+
+
+def _internal_masks(t):
+    return [] if t[0] == "leaf" else [_leaves_mask(t)] + [m for c in t[1:] for m in _internal_masks(c)]
+
+
+# Feynman-rule tensors with upper indices, contracted with lowered vectors
+_V4_STRUCTURES = [np.einsum("ac,bd->abcd", MINK, MINK) - np.einsum("ad,bc->abcd", MINK, MINK),
+                  np.einsum("ab,cd->abcd", MINK, MINK) - np.einsum("ad,bc->abcd", MINK, MINK),
+                  np.einsum("ab,cd->abcd", MINK, MINK) - np.einsum("ac,bd->abcd", MINK, MINK)]
+
+
+def _v3_tensor(k1, k2, k3):
+    """g^{mn}(k1-k2)^r + g^{nr}(k2-k3)^m + g^{rm}(k3-k1)^n, momenta incoming."""
+    return (np.einsum("mn,r->mnr", MINK, k1 - k2) + np.einsum("nr,m->mnr", MINK, k2 - k3)
+            + np.einsum("rm,n->mnr", MINK, k3 - k1))
+
+
+def _tree_currents(t, pol, mom):
+    """(currents, outgoing momentum) of tree t: one current per choice of
+    four-gluon structure in it, each with its propagator 1/P^2 and no couplings."""
+    if t[0] == "leaf":
+        return [pol[t[1]].astype(complex)], mom[t[1]]
+    subs = [_tree_currents(c, pol, mom) for c in t[1:]]
+    P = sum(s[1] for s in subs)
+    inv = 1.0 / mdot(P, P)
+    lower = lambda j: MINK @ j
+    out = []
+    if t[0] == "v3":
+        V = _v3_tensor(-subs[0][1], -subs[1][1], P)
+        for ja in subs[0][0]:
+            for jb in subs[1][0]:
+                out.append(inv * np.einsum("mnr,m,n->r", V, lower(ja), lower(jb)))
+    else:
+        for ja in subs[0][0]:
+            for jb in subs[1][0]:
+                for jc in subs[2][0]:
+                    for X in _V4_STRUCTURES:
+                        out.append(inv * np.einsum("abcd,a,b,c->d", X, lower(ja), lower(jb), lower(jc)))
+    return out, P
+
+
+def _diagram_weights_by_traces(p, gluons, mt):
+    """Per Feynman diagram of g g -> t t~ + gluons: the sum over every helicity of
+    |amp_d|^2 (bare vertices, propagators 1/(q^2 - m^2) and 1/P^2), keyed by the
+    diagram's internal lines (masks of external particles on the side away from
+    the t~).  Top spins are summed as Tr[(pt + m) G (ptb - m) Gbar], gluon
+    polarisations over a real transverse basis; a four-gluon vertex gives three
+    amplitudes (its Lorentz structures) whose |amp|^2 add."""
+    gam = _dirac_rep_gammas()
+    sl = lambda v: gam[0] * v[0] - gam[1] * v[1] - gam[2] * v[2] - gam[3] * v[3]
+    eye = np.eye(4)
+    pt, ptb = p[2], p[3]
+    Pt, Pb = sl(pt) + mt * eye, sl(ptb) - mt * eye
+    mom = {g: (-p[g] if g < 2 else p[g]) for g in gluons}   # outgoing momenta
+    bases = {g: _linear_polarisations(p[g][1:]) for g in gluons}
+    diagrams = []
+    for blocks in _ordered_partitions(tuple(gluons)):
+        for seq in itertools.product(*[_trees(b) for b in blocks]):
+            lines, side = [], 1 << 2
+            for i, t in enumerate(seq):
+                lines += _internal_masks(t)
+                side |= _leaves_mask(t)
+                if i < len(seq) - 1:
+                    lines.append(side)
+            diagrams.append((tuple(sorted(lines)), seq))
+    out = {key: 0.0 for key, _ in diagrams}
+    for choice in itertools.product(*[bases[g] for g in gluons]):
+        pol = dict(zip(gluons, choice))
+        for key, seq in diagrams:
+            cur = [_tree_currents(t, pol, mom) for t in seq]
+            for variant in itertools.product(*[c[0] for c in cur]):
+                G_ = np.eye(4, dtype=complex)
+                q = pt.copy()
+                for i, (j, (_, P)) in enumerate(zip(variant, cur)):
+                    G_ = G_ @ sl(j)
+                    if i < len(seq) - 1:
+                        q = q + P
+                        G_ = G_ @ (sl(q) + mt * eye) / (mdot(q, q) - mt * mt)
+                Gbar = gam[0] @ G_.conj().T @ gam[0]
+                out[key] += np.trace(Pt @ G_ @ Pb @ Gbar).real
+    return out
+
+
+@pytest.mark.parametrize("name,nev", [("gg_ttxg", 6), ("gg_ttxgg", 2)])
+def test_sde_diagrams_by_traces(orc, name, nev):
+    """Every Feynman diagram of g g -> t t~ g (16, one with a four-gluon vertex)
+    and g g -> t t~ g g (123, with four-gluon vertices inside larger trees):
+    the oracle's per-diagram helicity sum of |amp_d|^2 equals an independent
+    evaluation -- diagrams enumerated here from the vertex rules, three- and
+    four-gluon vertices as Feynman-rule tensors, top spins summed as traces in
+    the Dirac representation, gluon polarisations over a linear basis."""
+    npar = WORKLOADS[name].npar
+    gluons = [0, 1] + list(range(4, npar))
+    for p in events(orc, name, nev):
+        w2, lines = orc.sde(name, p, list(range(1 << npar)), MT)
+        ref = _diagram_weights_by_traces(p, gluons, MT)
+        assert set(ref) == set(lines) and len(ref) == len(lines)
+        for key, val in zip(lines, w2):
+            assert abs(val / ref[key] - 1) < 1e-10, (key, val, ref[key])
+
+
 # ---------------------------------------------------------------- normalisation
 @pytest.mark.parametrize("name,iden", [("ee_mumu", 4), ("gg_ttx", 256), ("gg_ttxg", 256), ("gg_ttxgg", 512),
                                        ("gg_ttxggg", 1536)])
