@@ -104,10 +104,14 @@ int me_filter_helicities(me_handle* h, const double* momenta, int64_t nevt, int*
  * library, present on every device that loads the library until the process
  * exits.  The probe events are all nevt events of `momenta`, which must be
  * device memory; scratch needed = 8 * nevt * (nhel + 1) bytes plus a little,
- * so nevt <= 8000 for 64 helicities and <= 4000 for 128; larger batches are
- * rejected with ME_ETOOLARGE (pass fewer probe events).  The first call on each
- * device looks up that device's copy of the array (cudaGetSymbolAddress) with
- * the device current; make that first call before any stream capture.  All
+ * so nevt <= 8000 for 64 helicities.  For gg_ttxggg the FP64 kernel also keeps
+ * each resident CTA's colour-flow vectors (240 KB) in the array: it runs with as
+ * many resident CTAs as the rest of the array holds (about 12 at 1000 probe
+ * events, one at 3800; fewer probe events run faster), so nevt <= 3800 there.
+ * Larger batches are rejected with ME_ETOOLARGE (pass fewer probe events).
+ * The first call on each device looks up that device's copy of the array
+ * (cudaGetSymbolAddress) with the device current; make that first call before
+ * any stream capture.  All
  * calls share the one array and overwrite it: calls that overlap on the same
  * device (from several host threads) race and must be serialised by the
  * caller.  Synchronous.  Errors: ME_EINVAL (null handle or momenta, host
@@ -196,20 +200,27 @@ int me_hsample_probabilities(const me_handle* h, double* p, int cap, int* n);
 int me_diagram_lines(const me_handle* h, int diagram, int* masks, int cap, int* n);
 
 /*
- * me_info -- process sizes.  Any output pointer may be NULL.
+ * me_info -- process sizes: the numbers of external particles, helicity
+ * configurations, colour flows (the dimension of the colour matrix of Sec. 4.1)
+ * and Feynman diagrams (Sec. 3.1 counts 3 for gg -> t t~), and the helicity mask
+ * found by the filter of Sec. 3.1.  Any output pointer may be NULL.
  *   good_mask_words: 2 words; bit h of word h/64 set iff helicity h is kept
- *   (all set before filtering).  nhel <= 128.
+ *   (all set before filtering).  nhel <= 128.  Host-only.  Errors: ME_EINVAL.
  */
 int me_info(const me_handle* h, int* npar, int* nhel, int* ncol, int* ndiag, uint64_t* good_mask_words);
 
-/* me_good_helicities -- kept helicity indices (host array of capacity cap);
- * *n receives their number.  Helicity index h: particle i has helicity +1 iff
- * bit (npar-1-i) of h is set. */
+/* me_good_helicities -- the helicity configurations the filter of Sec. 3.1
+ * kept, in ascending order (host array of capacity cap; at most cap are
+ * written); *n receives their number.  Helicity index h: particle i has
+ * helicity +1 iff bit (npar-1-i) of h is set.  Host-only.  Errors: ME_EINVAL. */
 int me_good_helicities(const me_handle* h, int* out, int cap, int* n);
 
 /* me_flops_per_event -- algorithmic work per event of the current mask, as
- * counted by the process generator: chain flops (FP32/FP64 pipe) and colour
- * quadratic-form flops, each = kept helicities x per-helicity count. */
+ * counted by the process generator (the per-event cost the throughput of
+ * Sec. 4 divides): chain flops (Sec. 3.1 wavefunctions, currents, amplitudes;
+ * FP32/FP64 pipe) and colour quadratic-form flops (Sec. 4.1), each = kept
+ * helicities x per-helicity count.  Either pointer may be NULL.  Host-only.
+ * Errors: ME_EINVAL. */
 int me_flops_per_event(const me_handle* h, double* chain_flops, double* colour_flops);
 
 /* options */
@@ -221,7 +232,10 @@ int me_flops_per_event(const me_handle* h, double* chain_flops, double* colour_f
                                     helicities; 0 (default): adaptive (me_sigmakin_hsample) */
 int me_set_option(me_handle* h, int option, int value);
 
-/* me_free -- destroy a handle (NULL is a no-op).  Synchronises its work. */
+/* me_free -- destroy a handle: the Bridge's destructor of Sec. 3.2 (create,
+ * execute, destroy).  Waits for the device to finish (cudaDeviceSynchronize),
+ * then releases the handle's device state and streams.  NULL is a no-op.  No
+ * status is returned; the handle must not be used afterwards. */
 void me_free(me_handle* h);
 
 /* Cuts of the seeded sampler: final-state particle j is subject to the cuts
@@ -256,10 +270,14 @@ int rambo_sample(uint64_t seed, int64_t ev0, int64_t nevt, double sqrt_s, const 
                  const me_cuts* cuts, double* momenta_out, double* weights_out, int64_t* nfail_out,
                  void* cuda_stream);
 
-/* me_strerror -- static description of a status code. */
+/* me_strerror -- static description of a status code returned by any call
+ * here (the error reporting of the Bridge interface of Sec. 3.2, which returns
+ * status codes rather than throwing across the language boundary).  Never NULL;
+ * unknown codes give "unknown status".  The string is owned by the library. */
 const char* me_strerror(int status);
 
-/* me_version -- library version string. */
+/* me_version -- library version string (static, owned by the library).  The
+ * paper has no counterpart. */
 const char* me_version(void);
 
 #ifdef __cplusplus

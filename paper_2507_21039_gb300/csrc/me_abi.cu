@@ -133,7 +133,8 @@ __global__ void hsample_select(const double* __restrict__ u, long long n, const 
 
 int launch_me(me_handle* h, int precision, const double* d_mom, int64_t nevt, double* d_me2, double* d_hel_out,
               const short* d_list, int nlist, cudaStream_t st, double* d_sde_w = nullptr, int sde_channel = 0,
-              const short* d_hel_ev = nullptr, const double* d_w_ev = nullptr)
+              const short* d_hel_ev = nullptr, const double* d_w_ev = nullptr, void* d_jscratch = nullptr,
+              size_t jscratch_bytes = 0)
 {
     LaunchArgs a{};
     a.mom = d_mom;
@@ -152,6 +153,8 @@ int launch_me(me_handle* h, int precision, const double* d_mom, int64_t nevt, do
     a.hel_ev = d_hel_ev;
     a.w_ev = d_w_ev;
     if (d_hel_ev) a.slots = 1;
+    a.jscratch = d_jscratch;
+    a.jscratch_bytes = jscratch_bytes;
     cudaError_t e = h->proc->launch(precision, a);
     return e == cudaSuccess ? ME_OK : ME_ECUDA;
 }
@@ -241,7 +244,10 @@ int check_finite(const double* d_mom, int64_t n, cudaStream_t st)
     int rc = ME_OK;
     if (cudaMemsetAsync(d_bad, 0, sizeof(unsigned long long), st) != cudaSuccess) rc = ME_ECUDA;
     if (rc == ME_OK) {
-        count_nonfinite<<<152 * 4, 256, 0, st>>>(d_mom, n, d_bad);
+        int dev = 0, nsm = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm < 1) nsm = 1;
+        count_nonfinite<<<nsm * 4, 256, 0, st>>>(d_mom, n, d_bad);
         if (cudaGetLastError() != cudaSuccess) rc = ME_ECUDA;
     }
     if (rc == ME_OK && cudaMemcpyAsync(&bad, d_bad, sizeof(bad), cudaMemcpyDeviceToHost, st) != cudaSuccess) rc = ME_ECUDA;
@@ -674,7 +680,12 @@ extern "C" int me_filter_helicities_noalloc(me_handle* h, const double* momenta,
     const size_t b_me2 = align256(sizeof(double) * (size_t)nevt);
     const size_t b_ratio = align256(sizeof(double) * 2 * nhel);
     const size_t b_list = align256(sizeof(short) * nhel);
-    if ((size_t)nevt > kStaticScratchBytes || b_hel + b_me2 + b_ratio + b_list > kStaticScratchBytes)
+    const size_t used = b_hel + b_me2 + b_ratio + b_list;
+    // the FP64 kernel of the largest process keeps its colour-flow vectors in
+    // global memory: they come from the rest of the array, one CTA's worth at
+    // least (fewer resident CTAs than a full launch when less is left)
+    const size_t per_cta = h->proc->jscratch_per_cta(me::PREC_FP64);
+    if ((size_t)nevt > kStaticScratchBytes || used > kStaticScratchBytes || kStaticScratchBytes - used < per_cta)
         return ME_ETOOLARGE;
     void* base = nullptr;
     int rc = scratch_address(&base);
@@ -686,12 +697,15 @@ extern "C" int me_filter_helicities_noalloc(me_handle* h, const double* momenta,
     short* d_all = reinterpret_cast<short*>(sp + b_hel + b_me2 + b_ratio);
     // every scratch word read below is written first in this call: the
     // per-helicity values and totals by the |M|^2 kernel, the ratios by the
-    // reduction, the helicity list by the copy; nothing needs clearing
+    // reduction, the helicity list by the copy, the colour-flow vectors by the
+    // kernel's own zeroing at the start of every event; nothing needs clearing
     short all[128];
     for (int i = 0; i < nhel; ++i) all[i] = (short)i;
     if (cudaDeviceSynchronize() != cudaSuccess) return ME_ECUDA;
     if (cudaMemcpy(d_all, all, sizeof(short) * nhel, cudaMemcpyHostToDevice) != cudaSuccess) return ME_ECUDA;
-    rc = launch_me(h, me::PREC_FP64, momenta, nevt, d_me2, d_hel_out, d_all, nhel, 0);
+    void* d_j = per_cta ? static_cast<void*>(sp + used) : nullptr;
+    rc = launch_me(h, me::PREC_FP64, momenta, nevt, d_me2, d_hel_out, d_all, nhel, 0, nullptr, 0, nullptr, nullptr,
+                   d_j, per_cta ? kStaticScratchBytes - used : 0);
     if (rc != ME_OK) return rc;
     filter_reduce<<<nhel, 256>>>(d_hel_out, d_me2, (int)nevt, nhel, d_ratio);
     if (cudaGetLastError() != cudaSuccess) return ME_ECUDA;

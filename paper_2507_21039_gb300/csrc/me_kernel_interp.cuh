@@ -346,18 +346,23 @@ __global__ void __launch_bounds__(P::NT) me_kernel_interp(LaunchArgs a, cx<T>* _
     }
 }
 
-template <class P, class T, bool TC = false, class C = T, bool SDE = false> cudaError_t launch_interp(const LaunchArgs& a)
+// global-memory J scratch of one resident CTA (0 when J stays on chip)
+template <class P, class T> constexpr size_t interp_jscratch_per_cta()
 {
     using L = InterpLayout<P, T>;
-    static_assert(!TC || sizeof(T) == 4, "tensor-core colour sum is the mixed-precision path");
-    static_assert(L::launch_bytes <= 232448, "interpreter shared memory exceeds 227 KB");
-    if (a.nlist > P::NT) return cudaErrorInvalidValue;
+    return (!L::J_IN_SMEM && !L::J_IN_TMEM) ? sizeof(cx<T>) * (size_t)P::NCOL * P::NT : 0;
+}
+
+// One-time kernel attributes and the number of resident CTAs per SM of the
+// persistent grid.  The grid is sized by the occupancy query, which takes the
+// kernel's shared-memory carveout preference: ask for the largest carveout, so
+// that it counts every CTA that fits the SM's shared memory.
+template <class P, class T, bool TC, class C, bool SDE> cudaError_t interp_residency(int& nsm, int& per_sm)
+{
+    using L = InterpLayout<P, T>;
     static size_t granted = 0;
     cudaError_t e = ensure_smem(me_kernel_interp<P, T, TC, C, SDE>, L::launch_bytes, granted);
     if (e != cudaSuccess) return e;
-    // the persistent grid is sized by the occupancy query, which takes the
-    // kernel's shared-memory carveout preference: ask for the largest carveout,
-    // so that it counts every CTA that fits the SM's shared memory
     static bool carveout = false;
     if (!carveout) {
         e = cudaFuncSetAttribute(me_kernel_interp<P, T, TC, C, SDE>, cudaFuncAttributePreferredSharedMemoryCarveout,
@@ -365,7 +370,9 @@ template <class P, class T, bool TC = false, class C = T, bool SDE = false> cuda
         if (e != cudaSuccess) return e;
         carveout = true;
     }
-    int dev = 0, nsm = 0, per_sm = 0;
+    int dev = 0;
+    nsm = 0;
+    per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, me_kernel_interp<P, T, TC, C, SDE>, P::NT,
@@ -375,16 +382,46 @@ template <class P, class T, bool TC = false, class C = T, bool SDE = false> cuda
         per_sm = 1;
     }
     if (L::J_IN_TMEM && per_sm > (int)(512 / L::TMEM_COLS)) per_sm = 512 / L::TMEM_COLS;
+    return cudaSuccess;
+}
+
+// resident CTAs of a full launch (the J scratch it allocates is this x interp_jscratch_per_cta)
+template <class P, class T, bool TC = false, class C = T, bool SDE = false> int interp_resident_ctas()
+{
+    int nsm = 0, per_sm = 0;
+    if (interp_residency<P, T, TC, C, SDE>(nsm, per_sm) != cudaSuccess) return 0;
+    return nsm * per_sm;
+}
+
+template <class P, class T, bool TC = false, class C = T, bool SDE = false> cudaError_t launch_interp(const LaunchArgs& a)
+{
+    using L = InterpLayout<P, T>;
+    static_assert(!TC || sizeof(T) == 4, "tensor-core colour sum is the mixed-precision path");
+    static_assert(L::launch_bytes <= 232448, "interpreter shared memory exceeds 227 KB");
+    if (a.nlist > P::NT) return cudaErrorInvalidValue;
+    int nsm = 0, per_sm = 0;
+    cudaError_t e = interp_residency<P, T, TC, C, SDE>(nsm, per_sm);
+    if (e != cudaSuccess) return e;
     const long long slots = (long long)nsm * per_sm;  // resident CTAs, persistent over events
-    const long long grid = a.nevt < slots ? a.nevt : slots;
+    long long grid = a.nevt < slots ? a.nevt : slots;
     cx<T>* jg = nullptr;
-    if constexpr (!L::J_IN_SMEM && !L::J_IN_TMEM) {
-        e = cudaMallocAsync(&jg, sizeof(cx<T>) * (size_t)grid * P::NCOL * P::NT, a.stream);
-        if (e != cudaSuccess) return e;
+    bool own = false;
+    if constexpr (interp_jscratch_per_cta<P, T>() > 0) {
+        constexpr size_t per = interp_jscratch_per_cta<P, T>();
+        if (a.jscratch) {  // caller's scratch: fewer resident CTAs if it holds fewer, no allocation
+            const long long fit = (long long)(a.jscratch_bytes / per);
+            if (fit < 1 || (reinterpret_cast<uintptr_t>(a.jscratch) & 15)) return cudaErrorInvalidValue;
+            if (grid > fit) grid = fit;
+            jg = static_cast<cx<T>*>(a.jscratch);
+        } else {
+            e = cudaMallocAsync(&jg, per * (size_t)grid, a.stream);
+            if (e != cudaSuccess) return e;
+            own = true;
+        }
     }
     me_kernel_interp<P, T, TC, C, SDE><<<(unsigned)grid, P::NT, L::launch_bytes, a.stream>>>(a, jg);
     e = cudaGetLastError();
-    if (jg) cudaFreeAsync(jg, a.stream);
+    if (own) cudaFreeAsync(jg, a.stream);
     return e;
 }
 

@@ -22,6 +22,9 @@ struct LaunchArgs {
     int sde_channel;
     const short* hel_ev;    // optional [nevt]: one sampled helicity per event (with nlist = 1, slots = 1)
     const double* w_ev;     // [nevt] with hel_ev: 1 / probability of the sampled helicity
+    void* jscratch;         // optional: device memory for a launch's colour-flow scratch (kernels that
+    size_t jscratch_bytes;  // keep J in global memory); the launch then allocates nothing and runs at
+                            // most jscratch_bytes / jscratch_per_cta resident CTAs
 };
 
 enum Precision : int { PREC_FP64 = 0, PREC_FP32 = 1, PREC_MIXED = 2, PREC_MIXED64 = 3 };
@@ -38,6 +41,11 @@ struct ProcDesc {
     cudaError_t (*launch)(int precision, const LaunchArgs&);
     const int* diag_lines;     // [ndiag][4] internal-line masks of each diagram (host), 0-padded
     const int* diag_nlines;    // [ndiag]
+    // bytes of global-memory colour-flow scratch one resident CTA of a launch in
+    // this precision needs (0: the kernel keeps J on chip and allocates nothing)
+    size_t (*jscratch_per_cta)(int precision);
+    // resident CTAs of such a launch on the current device (its scratch is this x jscratch_per_cta)
+    int (*jscratch_ctas)(int precision);
 };
 
 const ProcDesc* find_process(const char* name);

@@ -240,6 +240,16 @@ def emit_process(process: str) -> tuple[str, dict]:
         tc_members = (f"\n    static constexpr bool NSPLIT = {'true' if nsplit else 'false'};"
                       f"\n    __device__ static __forceinline__ const uint2* bfrag() {{ return c_bfrag; }}")
     ns = f"p_{process}"
+    if IP:  # FP64 chains (FP64, paper-mixed, FP64 channel weights) keep J in global memory
+        jscratch_body = ("    return (precision == PREC_FP64 || precision == PREC_MIXED64)\n"
+                         "               ? interp_jscratch_per_cta<ProcInterpD, double>()\n"
+                         "               : interp_jscratch_per_cta<ProcInterp, float>();")
+        jscratch_ctas_body = ("    return (precision == PREC_FP64 || precision == PREC_MIXED64)\n"
+                              "               ? interp_resident_ctas<ProcInterpD, double>()\n"
+                              "               : interp_resident_ctas<ProcInterp, float>();")
+    else:
+        jscratch_body = "    (void)precision;\n    return 0;"
+        jscratch_ctas_body = "    (void)precision;\n    return 0;"
     cnum_flat = ", ".join(str(x) for row in num for x in row)
     src = f"""// Generated by paper_2507_21039_gb300/gen/emit.py for {process}: do not edit.
 // {P.ndiagrams} Feynman diagrams, {len(P.amps)} amplitudes, {len(P.ops)} routine calls,
@@ -305,6 +315,16 @@ static cudaError_t launch(int precision, const LaunchArgs& a)
     }}
 }}
 
+static size_t jscratch_per_cta(int precision)
+{{
+{jscratch_body}
+}}
+
+static int jscratch_ctas(int precision)
+{{
+{jscratch_ctas_body}
+}}
+
 }}  // namespace {ns}
 
 const ProcDesc* procdesc_{process}()
@@ -312,7 +332,7 @@ const ProcDesc* procdesc_{process}()
     static const ProcDesc d = {{"{process}", {npar}, {1 << npar}, {ncol}, {P.ndiagrams}, {len(P.amps)}, {k}, {nlines},
                                {threads}, {iden!r}, {den}, {ns}::h_cnum, {flops_hel}LL,
                                {P.colour_flops_per_helicity()}LL, {cpow}, &{ns}::launch, {ns}::h_diag_lines,
-                               {ns}::h_diag_nlines}};
+                               {ns}::h_diag_nlines, &{ns}::jscratch_per_cta, &{ns}::jscratch_ctas}};
     return &d;
 }}
 
