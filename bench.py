@@ -36,7 +36,13 @@ KERNELS = {"ee_mumu": "me_kernel_scalar<ee_mumu, float>", "gg_ttx": "me_kernel_s
 PROCESS_LABEL = {"ee_mumu": "e+ e- -> mu+ mu-", "gg_ttx": "g g -> t t~", "gg_ttxg": "g g -> t t~ g",
                  "gg_ttxgg": "g g -> t t~ g g", "gg_ttxggg": "g g -> t t~ g g g"}
 FP32_LANES_PER_SM = 128     # FP32 FMA lanes per SM (4 SMSPs x 32)
-N_SM = 152
+
+
+def n_sm() -> int:
+    """SM count of the current device (152 on GB300), queried, not assumed."""
+    import torch
+
+    return torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
 
 
 def parse():
@@ -316,12 +322,13 @@ def run_ours(args):
     flops = (chain_f + colour_f) * n
     peaks, peak_src = measured_peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    fp32_peak = N_SM * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    nsm = n_sm()
+    fp32_peak = nsm * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
     achieved = flops / (me_ms / 1e3) / 1e12
     roofline = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
                 "frac": achieved / fp32_peak, "traffic": None,
                 "kernel": KERNELS[name],
-                "peak_source": f"derived: {N_SM} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 flops x "
+                "peak_source": f"derived: {nsm} SMs (queried) x {FP32_LANES_PER_SM} FP32 lanes x 2 flops x "
                                f"{sm_max:.0f} MHz ({peak_src} sm_max_mhz)",
                 "flops_per_event": chain_f + colour_f, "me_kernel_ms": me_ms}
     # DRAM bytes of one launch from the committed ncu summary, if it was taken on
@@ -390,7 +397,7 @@ def run_small():
 
     peaks, _ = measured_peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    fp32_peak = N_SM * FP32_LANES_PER_SM * 2 * sm_max * 1e6
+    fp32_peak = n_sm() * FP32_LANES_PER_SM * 2 * sm_max * 1e6
     out = {}
     for name in ("ee_mumu", "gg_ttx"):
         w = WORKLOADS[name]

@@ -220,8 +220,9 @@ def test_rambo_full_size_sampled(orc):
         assert np.abs(g[i] - mom[0]).max() < 1e-9 * w.sqrt_s
 
 
-@pytest.mark.parametrize("name,prec", [("gg_ttxgg", "mixed"), ("gg_ttxgg", "fp64"), ("gg_ttx", "fp64"),
-                                       ("gg_ttxggg", "mixed")])
+@pytest.mark.parametrize("name,prec", [("gg_ttxgg", "mixed"), ("gg_ttxgg", "fp64"), ("gg_ttxgg", "fp32"),
+                                       ("gg_ttx", "fp64"), ("gg_ttxg", "fp32"), ("gg_ttxg", "mixed"),
+                                       ("gg_ttxggg", "mixed"), ("gg_ttxggg", "fp64")])
 def test_full_size_sampled_parity(orc, name, prec):
     """Full-size batch in the benchmark's launch configuration; sampled
     events checked one by one against the oracle."""
