@@ -59,16 +59,12 @@ template <class T, int STRIDE> struct JSmem {
     __device__ __forceinline__ cx<T>& operator[](int c) const { return base[c * STRIDE]; }
 };
 
-// External wavefunction `item` = 2 e + b (particle e, helicity bit b), computed
-// in the amplitude precision T from the FP64 momenta
+// External wavefunction of particle e with helicity bit b from its momentum pe
+// and mass m, both in the amplitude precision T
 template <class P, class T>
-__device__ __forceinline__ Wf<T> ext_wavefunction(const double* __restrict__ p, int item, double mt, int gauge_ext)
+__device__ __forceinline__ Wf<T> ext_wavefunction_at(const T (&pe)[4], int e, int b, T m, int gauge_ext)
 {
-    const int e = item >> 1, b = item & 1, lam = b ? 1 : -1;
-    T pe[4];
-#pragma unroll
-    for (int mu = 0; mu < 4; ++mu) pe[mu] = (T)p[4 * e + mu];
-    const T m = P::ext_massive(e) ? (T)mt : T(0);
+    const int lam = b ? 1 : -1;
     Wf<T> o;
     if (e == gauge_ext) {  // diagnostic: gluon polarisation replaced by its momentum
         for (int mu = 0; mu < 4; ++mu) o.c[mu] = {pe[mu], T(0)};
@@ -83,6 +79,18 @@ __device__ __forceinline__ Wf<T> ext_wavefunction(const double* __restrict__ p, 
     default: ixxxxx<T>(pe, m, lam, -1, o.c); break;
     }
     return o;
+}
+
+// External wavefunction `item` = 2 e + b (particle e, helicity bit b), computed
+// in the amplitude precision T from the FP64 momenta
+template <class P, class T>
+__device__ __forceinline__ Wf<T> ext_wavefunction(const double* __restrict__ p, int item, double mt, int gauge_ext)
+{
+    const int e = item >> 1;
+    T pe[4];
+#pragma unroll
+    for (int mu = 0; mu < 4; ++mu) pe[mu] = (T)p[4 * e + mu];
+    return ext_wavefunction_at<P, T>(pe, e, item & 1, P::ext_massive(e) ? (T)mt : T(0), gauge_ext);
 }
 
 // Line l: momentum (signed sum of external momenta, FP64) and 1/(p^2 - m^2)
@@ -109,6 +117,148 @@ template <class P, class T> __device__ __forceinline__ Ln<T> line_data(const dou
 #pragma unroll
     for (int mu = 0; mu < 4; ++mu) o.p[mu] = (T)q[mu];
     return o;
+}
+
+// ---------------------------------------------------------------------------
+// FP32 kernels: per-event FP64 work only where cancellation needs it.
+//
+// GB300 runs FP64 at 1/64 of the FP32 rate.  In the FP32 and mixed kernels the
+// per-event setup therefore keeps FP64 for the propagator denominators p^2 - m^2
+// alone, and forms them from few FP64 instructions:
+//   * every momentum component is split once into FP32 hi + lo (hi the FP32
+//     rounding of p, lo the rounding of the remainder: p = hi + lo to 2^-48
+//     relative).  hi feeds the external wavefunctions; each line momentum is a
+//     compensated FP32 sum of the hi and lo parts (the rounding of every hi
+//     addition is recovered exactly and added back), i.e. the FP32 rounding of
+//     its FP64 value up to the last bit;
+//   * the Gram matrix p_i.p_j (i <= j) is formed once per event in FP64, and a
+//     line's p^2 - m^2 is the FP64 sum of c_a c_b p_a.p_b over the particles of
+//     the line's shorter side (at most three for up to seven particles: six
+//     FP64 fused multiply-adds), which is the same quantity as the square of the
+//     FP64 momentum sum, rounded differently.
+// ---------------------------------------------------------------------------
+template <int NPAR> struct Gram {
+    static constexpr int N = NPAR * (NPAR + 1) / 2;
+    // entry of p_i.p_j for i <= j (rows of the upper triangle)
+    __host__ __device__ static constexpr int idx(int i, int j) { return i * NPAR - i * (i - 1) / 2 + (j - i); }
+};
+
+// setup item `it` of the first phase: it < 4 NPAR splits momentum component it
+// into pf[it] = {hi, lo}; otherwise the Gram entry it - 4 NPAR (row order)
+template <int NPAR>
+__device__ __forceinline__ void split_or_gram(const double* __restrict__ p, int it, float2* __restrict__ pf,
+                                              double* __restrict__ gram)
+{
+    if (it < 4 * NPAR) {
+        const double x = p[it];
+        const float hi = __double2float_rn(x);
+        pf[it] = make_float2(hi, __double2float_rn(x - (double)hi));
+    } else {
+        int k = it - 4 * NPAR, i = 0;
+        while (k >= NPAR - i) {
+            k -= NPAR - i;
+            ++i;
+        }
+        const double* a = p + 4 * i;
+        const double* b = p + 4 * (i + k);
+        gram[it - 4 * NPAR] = fma(-a[3], b[3], fma(-a[2], b[2], fma(-a[1], b[1], a[0] * b[0])));
+    }
+}
+
+// Line l in FP32 from the split momenta and the FP64 Gram matrix (m2 = mt^2)
+template <class P>
+__device__ __forceinline__ Ln<float> line_data_split(const float2* __restrict__ pf, const double* __restrict__ gram,
+                                                     int l, double m2)
+{
+    constexpr int S = P::SIDE;
+    const unsigned sd = P::line_side(l);
+    const int k = (int)(sd & 7u);
+    int id[S];
+    float sf[S];
+#pragma unroll
+    for (int a = 0; a < S; ++a) {  // terms past k: particle 0 with coefficient 0
+        const unsigned t = sd >> (4 * a + 4);
+        id[a] = a < k ? (int)(t & 7u) : 0;
+        sf[a] = a < k ? ((t & 8u) ? -1.0f : 1.0f) : 0.0f;
+    }
+    Ln<float> o;
+#pragma unroll
+    for (int mu = 0; mu < 4; ++mu) {
+        float s = 0.0f, c = 0.0f;
+#pragma unroll
+        for (int a = 0; a < S; ++a) {
+            const float2 v = pf[4 * id[a] + mu];
+            const float x = sf[a] * v.x;          // exact (a sign or zero)
+            const float t = s + x;                // two-sum: s + x = t + err exactly
+            const float z = t - s;
+            c += ((s - (t - z)) + (x - z)) + sf[a] * v.y;
+            s = t;
+        }
+        o.p[mu] = s + c;
+    }
+    o.inv = 0.0f;
+    const unsigned kind = P::line_kind(l);
+    if (kind != L_EXT) {
+        double d = kind == L_MASSIVE ? -m2 : 0.0;
+#pragma unroll
+        for (int a = 0; a < S; ++a)
+#pragma unroll
+            for (int b = a; b < S; ++b) {
+                const bool neg = ((sd >> (4 * a + 4)) ^ (sd >> (4 * b + 4))) & 8u;
+                const double cab = b < k ? (a == b ? 1.0 : (neg ? -2.0 : 2.0)) : 0.0;
+                const int i = min(id[a], id[b]), j = max(id[a], id[b]);
+                d = fma(cab, gram[Gram<P::NPAR>::idx(i, j)], d);
+            }
+        o.inv = 1.0f / __double2float_rn(d);
+    }
+    return o;
+}
+
+// External wavefunction `item` = 2 e + b in FP32 from the split momenta
+template <class P>
+__device__ __forceinline__ Wf<float> ext_wavefunction_split(const float2* __restrict__ pf, int item, float mt,
+                                                            int gauge_ext)
+{
+    const int e = item >> 1;
+    float pe[4];
+#pragma unroll
+    for (int mu = 0; mu < 4; ++mu) pe[mu] = pf[4 * e + mu].x;
+    return ext_wavefunction_at<P, float>(pe, e, item & 1, P::ext_massive(e) ? mt : 0.0f, gauge_ext);
+}
+
+// Item of the first setup phase taken by thread tid of an NT-thread event group
+// in a single pass: splits on the first warp, Gram entries on the second, so
+// that neither warp diverges between the two; -1 = none.  Groups of one warp
+// loop over all items instead (split_items_one_pass false).
+template <int NPAR, int NT> __host__ __device__ constexpr bool split_items_one_pass()
+{
+    return NT >= 64 && 4 * NPAR <= 32 && Gram<NPAR>::N <= NT - 32;
+}
+template <int NPAR> __device__ __forceinline__ int split_item_of(int tid)
+{
+    if (tid < 32) return tid < 4 * NPAR ? tid : -1;
+    return tid - 32 < Gram<NPAR>::N ? 4 * NPAR + tid - 32 : -1;
+}
+
+// Compensated FP32 sum (s + c): the helicity sum of the FP32 kernels, formed
+// without FP64 until the per-event total
+struct FSum {
+    float s, c;
+};
+__device__ __forceinline__ FSum fsum_add(FSum a, FSum b)
+{
+    const float t = a.s + b.s;
+    const float z = t - a.s;
+    return {t, a.c + b.c + ((a.s - (t - z)) + (b.s - z))};
+}
+__device__ __forceinline__ FSum fsum_warp(FSum v)
+{
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        const FSum o{__shfl_xor_sync(0xffffffffu, v.s, off), __shfl_xor_sync(0xffffffffu, v.c, off)};
+        v = fsum_add(v, o);
+    }
+    return v;
 }
 
 template <class P, class T>

@@ -54,7 +54,10 @@ constexpr unsigned char AMP_NEG = 0x80, AMP_WINDOW_END = 0x40;
 
 template <class P, class T> struct InterpLayout {
     static constexpr size_t mom = 0;
-    static constexpr size_t lines = mom + P::NPAR * 4 * sizeof(double);
+    // T = float: split momenta and FP64 Gram matrix of the FP32 setup (me_kernel.cuh)
+    static constexpr size_t pf = mom + P::NPAR * 4 * sizeof(double);
+    static constexpr size_t gram = pf + (sizeof(T) == 4 ? P::NPAR * 4 * sizeof(float2) : 0);
+    static constexpr size_t lines = gram + (sizeof(T) == 4 ? Gram<P::NPAR>::N * sizeof(double) : 0);
     static constexpr size_t vsup = (lines + P::NLINES * sizeof(Ln<T>) + 15) / 16 * 16;
     static constexpr size_t table = (vsup + (size_t)P::NSUP * P::NT + 15) / 16 * 16;
     static constexpr size_t jsm = table + (size_t)P::TAB * sizeof(Wf<T>);
@@ -118,7 +121,13 @@ __global__ void __launch_bounds__(P::NT) me_kernel_interp(LaunchArgs a, cx<T>* _
     if constexpr (L::J_IN_SMEM) jp = reinterpret_cast<cx<T>*>(smem + L::jsm) + threadIdx.x;
     else if constexpr (!L::J_IN_TMEM) jp = jglobal + (size_t)blockIdx.x * NCOL * NT + threadIdx.x;
     __shared__ double red[NT / 32];
+    __shared__ FSum fred[NT / 32];
     __shared__ double red_sde[SDE ? 2 : 1][NT / 32];
+    constexpr bool F32 = sizeof(T) == 4;
+    float2* spf = reinterpret_cast<float2*>(smem + L::pf);
+    double* sgram = reinterpret_cast<double*>(smem + L::gram);
+    const double m2 = a.mt * a.mt;
+    const float mtf = (float)a.mt;
     __shared__ float rowv[NT];
     __shared__ uint32_t tmem_base;
     const int tid = threadIdx.x;
@@ -158,9 +167,23 @@ __global__ void __launch_bounds__(P::NT) me_kernel_interp(LaunchArgs a, cx<T>* _
             for (int c = 0; c < NCOL; ++c) jp[c * NT] = {T(0), T(0)};
         }
         __syncthreads();
-        for (int it = tid; it < 2 * NPAR + NL; it += NT) {
-            if (it < 2 * NPAR) tab.st(it, ext_wavefunction<P, T>(smom, it, a.mt, a.gauge_ext));
-            else sln[it - 2 * NPAR] = line_data<P, T>(smom, it - 2 * NPAR, a.mt);
+        if constexpr (F32) {  // split momenta and FP64 Gram matrix, then lines and external states in FP32
+            if constexpr (split_items_one_pass<NPAR, NT>()) {
+                const int it = split_item_of<NPAR>(tid);
+                if (it >= 0) split_or_gram<NPAR>(smom, it, spf, sgram);
+            } else {
+                for (int it = tid; it < 4 * NPAR + Gram<NPAR>::N; it += NT) split_or_gram<NPAR>(smom, it, spf, sgram);
+            }
+            __syncthreads();
+            for (int it = tid; it < NL + 2 * NPAR; it += NT) {
+                if (it < NL) sln[it] = line_data_split<P>(spf, sgram, it, m2);
+                else tab.st(it - NL, ext_wavefunction_split<P>(spf, it - NL, mtf, a.gauge_ext));
+            }
+        } else {
+            for (int it = tid; it < 2 * NPAR + NL; it += NT) {
+                if (it < 2 * NPAR) tab.st(it, ext_wavefunction<P, T>(smom, it, a.mt, a.gauge_ext));
+                else sln[it - 2 * NPAR] = line_data<P, T>(smom, it - 2 * NPAR, a.mt);
+            }
         }
         __syncthreads();
         const T mt = (T)a.mt;
@@ -299,23 +322,27 @@ __global__ void __launch_bounds__(P::NT) me_kernel_interp(LaunchArgs a, cx<T>* _
             v = colour_scalar(jp, NT);
         }
         double acc = 0.0, dn = 0.0, dd = 0.0;
+        FSum facc{0.0f, 0.0f};
         if (act) {
-            acc = (double)v;
+            if constexpr (F32) facc.s = (float)v;
+            else acc = (double)v;
             if constexpr (SDE) {
                 dn = (double)snum;
                 dd = (double)sden;
             }
             if (a.hel_out) a.hel_out[e * a.nlist + tid] = (double)v * a.norm;
         }
+        if constexpr (F32) facc = fsum_warp(facc);
         for (int off = 16; off > 0; off >>= 1) {
-            acc += __shfl_xor_sync(0xffffffffu, acc, off);
+            if constexpr (!F32) acc += __shfl_xor_sync(0xffffffffu, acc, off);
             if constexpr (SDE) {
                 dn += __shfl_xor_sync(0xffffffffu, dn, off);
                 dd += __shfl_xor_sync(0xffffffffu, dd, off);
             }
         }
         if ((tid & 31) == 0) {
-            red[tid >> 5] = acc;
+            if constexpr (F32) fred[tid >> 5] = facc;
+            else red[tid >> 5] = acc;
             if constexpr (SDE) {
                 red_sde[0][tid >> 5] = dn;
                 red_sde[1][tid >> 5] = dd;
@@ -324,8 +351,13 @@ __global__ void __launch_bounds__(P::NT) me_kernel_interp(LaunchArgs a, cx<T>* _
         __syncthreads();
         if (tid == 0) {
             double s = 0.0, sn = 0.0, sd = 0.0;
+            if constexpr (F32) {  // one conversion per event
+                FSum f = fred[0];
+                for (int w = 1; w < NT / 32; ++w) f = fsum_add(f, fred[w]);
+                s = (double)f.s + (double)f.c;
+            }
             for (int w = 0; w < NT / 32; ++w) {
-                s += red[w];
+                if constexpr (!F32) s += red[w];
                 if constexpr (SDE) {
                     sn += red_sde[0][w];
                     sd += red_sde[1][w];

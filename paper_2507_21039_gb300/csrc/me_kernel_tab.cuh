@@ -95,9 +95,19 @@ template <class T, int TAB> struct TabRef {
     }
 };
 
-template <class P, class T> __host__ __device__ constexpr size_t tab_line_offset()
+// per-event shared memory: FP64 momenta; for T = float the split momenta and
+// the Gram matrix (FP32 setup, see me_kernel.cuh); lines; table
+template <class P, class T> __host__ __device__ constexpr size_t tab_pf_offset()
 {
     return (size_t)P::NPAR * 4 * sizeof(double);
+}
+template <class P, class T> __host__ __device__ constexpr size_t tab_gram_offset()
+{
+    return tab_pf_offset<P, T>() + (std::is_same<T, float>::value ? (size_t)P::NPAR * 4 * sizeof(float2) : 0);
+}
+template <class P, class T> __host__ __device__ constexpr size_t tab_line_offset()
+{
+    return tab_gram_offset<P, T>() + (std::is_same<T, float>::value ? (size_t)Gram<P::NPAR>::N * sizeof(double) : 0);
 }
 template <class P, class T> __host__ __device__ constexpr size_t tab_table_offset()
 {
@@ -134,7 +144,13 @@ __global__ void __launch_bounds__(P::NT * tab_epc<P, T>(), is_fp64<T>() ? P::MIN
     Ln<T>* sln = reinterpret_cast<Ln<T>*>(smem + tab_line_offset<P, T>());
     const TabRef<T, P::TAB> tab{reinterpret_cast<uint4*>(smem + tab_table_offset<P, T>())};
     __shared__ double red[EPC][NT / 32 > 0 ? NT / 32 : 1];
+    __shared__ FSum fred[EPC][NT / 32 > 0 ? NT / 32 : 1];
     __shared__ double red_sde[SDE ? EPC : 1][2][NT / 32 > 0 ? NT / 32 : 1];
+    constexpr bool F32 = !is_fp64<T>();
+    float2* spf = reinterpret_cast<float2*>(smem + tab_pf_offset<P, T>());
+    double* sgram = reinterpret_cast<double*>(smem + tab_gram_offset<P, T>());
+    const double m2 = a.mt * a.mt;
+    const float mtf = (float)a.mt;
 
     for (long long e0 = (long long)blockIdx.x * EPC; e0 < a.nevt; e0 += (long long)gridDim.x * EPC) {
         const long long e = e0 + grp;
@@ -152,7 +168,24 @@ __global__ void __launch_bounds__(P::NT * tab_epc<P, T>(), is_fp64<T>() ? P::MIN
         __syncthreads();
         // (a2, a3 denominators) per-event data; external wavefunctions are the
         // first 2*NPAR table entries
-        if (live) {
+        if constexpr (F32) {
+            // split momenta and FP64 Gram matrix, then lines and external states in FP32
+            if (live) {
+                if constexpr (split_items_one_pass<NPAR, NT>()) {
+                    const int it = split_item_of<NPAR>(tid);
+                    if (it >= 0) split_or_gram<NPAR>(smom, it, spf, sgram);
+                } else {
+                    for (int it = tid; it < 4 * NPAR + Gram<NPAR>::N; it += NT) split_or_gram<NPAR>(smom, it, spf, sgram);
+                }
+            }
+            __syncthreads();
+            if (live) {
+                for (int it = tid; it < NL + 2 * NPAR; it += NT) {
+                    if (it < NL) sln[it] = line_data_split<P>(spf, sgram, it, m2);
+                    else tab.st(it - NL, ext_wavefunction_split<P>(spf, it - NL, mtf, a.gauge_ext));
+                }
+            }
+        } else if (live) {
             for (int it = tid; it < 2 * NPAR + NL; it += NT) {
                 if (it < 2 * NPAR) tab.st(it, ext_wavefunction<P, T>(smom, it, a.mt, a.gauge_ext));
                 else sln[it - 2 * NPAR] = line_data<P, T>(smom, it - 2 * NPAR, a.mt);
@@ -172,6 +205,7 @@ __global__ void __launch_bounds__(P::NT * tab_epc<P, T>(), is_fp64<T>() ? P::MIN
         // process computes its table objects stage by stage between its
         // amplitudes, in one pass (nlist <= NT).
         double acc = 0.0, snum = 0.0, sden = 0.0;
+        FSum facc{0.0f, 0.0f};
         for (int base = 0; base < a.nlist; base += NT) {
             const int i = base + tid;
             const bool act = live && i < a.nlist;
@@ -207,7 +241,8 @@ __global__ void __launch_bounds__(P::NT * tab_epc<P, T>(), is_fp64<T>() ? P::MIN
                 v = colour_as<P, T, C>(J);
             }
             if (act) {
-                acc += (double)v;
+                if constexpr (F32) facc = fsum_add(facc, FSum{(float)v, 0.0f});
+                else acc += (double)v;
                 if constexpr (SDE) {
                     snum += (double)sde.num;
                     sden += (double)sde.den;
@@ -215,8 +250,9 @@ __global__ void __launch_bounds__(P::NT * tab_epc<P, T>(), is_fp64<T>() ? P::MIN
                 if (a.hel_out) a.hel_out[e * a.nlist + i] = (double)v * a.norm;
             }
         }
+        if constexpr (F32) facc = fsum_warp(facc);
         for (int off = 16; off > 0; off >>= 1) {
-            acc += __shfl_xor_sync(0xffffffffu, acc, off);
+            if constexpr (!F32) acc += __shfl_xor_sync(0xffffffffu, acc, off);
             if constexpr (SDE) {
                 snum += __shfl_xor_sync(0xffffffffu, snum, off);
                 sden += __shfl_xor_sync(0xffffffffu, sden, off);
@@ -224,7 +260,8 @@ __global__ void __launch_bounds__(P::NT * tab_epc<P, T>(), is_fp64<T>() ? P::MIN
         }
         if constexpr (NT > 32) {
             if ((tid & 31) == 0) {
-                red[grp][tid >> 5] = acc;
+                if constexpr (F32) fred[grp][tid >> 5] = facc;
+                else red[grp][tid >> 5] = acc;
                 if constexpr (SDE) {
                     red_sde[grp][0][tid >> 5] = snum;
                     red_sde[grp][1][tid >> 5] = sden;
@@ -233,8 +270,13 @@ __global__ void __launch_bounds__(P::NT * tab_epc<P, T>(), is_fp64<T>() ? P::MIN
             __syncthreads();
             if (tid == 0 && live) {
                 double s = 0.0, sn = 0.0, sd = 0.0;
+                if constexpr (F32) {  // one conversion per event
+                    FSum f = fred[grp][0];
+                    for (int w = 1; w < NT / 32; ++w) f = fsum_add(f, fred[grp][w]);
+                    s = (double)f.s + (double)f.c;
+                }
                 for (int w = 0; w < NT / 32; ++w) {
-                    s += red[grp][w];
+                    if constexpr (!F32) s += red[grp][w];
                     if constexpr (SDE) {
                         sn += red_sde[grp][0][w];
                         sd += red_sde[grp][1][w];
@@ -244,6 +286,7 @@ __global__ void __launch_bounds__(P::NT * tab_epc<P, T>(), is_fp64<T>() ? P::MIN
                 if constexpr (SDE) a.sde_w[e] = sd > 0.0 ? sn / sd : 0.0;
             }
         } else {
+            if constexpr (F32) acc = (double)facc.s + (double)facc.c;
             if (tid == 0 && live) {
                 a.me2[e] = acc * a.norm * (a.w_ev ? a.w_ev[e] : 1.0);
                 if constexpr (SDE) a.sde_w[e] = sden > 0.0 ? snum / sden : 0.0;

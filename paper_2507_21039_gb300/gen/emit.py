@@ -96,6 +96,36 @@ def _line_tables(P: Plan):
     return plus, minus, kind
 
 
+def _line_sides(plus, minus, npar):
+    """Per line, the shortest signed sum of external momenta equal to its momentum.
+
+    A line's momentum is q = sum_plus p - sum_minus p (physical momenta).  The
+    external momenta satisfy sum_i sigma_i p_i = 0 with sigma = -1 for the two
+    incoming particles and +1 for the outgoing ones, so q - lam * sum sigma_i p_i
+    (lam = +-1) is the same vector written over the other side of the line.  The
+    shorter form has at most floor(npar / 2) terms.  Packed per line: bits 0-2
+    the number of terms k; term a at bits 4a+4 .. 4a+7 (particle index in bits
+    4a+4 .. 4a+6, bit 4a+7 set for a minus sign).  Returns (packed, max k)."""
+    sigma = [-1, -1] + [1] * (npar - 2)
+    out, kmax = [], 0
+    for pm, mm in zip(plus, minus):
+        c = [((pm >> i) & 1) - ((mm >> i) & 1) for i in range(npar)]
+        best = None
+        for lam in (0, 1, -1):
+            cc = [ci - lam * si for ci, si in zip(c, sigma)]
+            if all(x in (-1, 0, 1) for x in cc):
+                n = sum(1 for x in cc if x)
+                if best is None or n < best[0]:
+                    best = (n, cc)
+        n, cc = best
+        word = n
+        for a, (i, x) in enumerate((i, x) for i, x in enumerate(cc) if x):
+            word |= (i | (8 if x < 0 else 0)) << (4 * a + 4)
+        out.append(word)
+        kmax = max(kmax, n)
+    return out, kmax
+
+
 def _bf16_bits(x: float) -> int:
     """float -> bfloat16 bits, round to nearest even"""
     f = struct.unpack("<I", struct.pack("<f", float(x)))[0]
@@ -151,6 +181,7 @@ def emit_process(process: str) -> tuple[str, dict]:
     k = len(P.gluon_ext)
     kinds, massive = _ext_table(process)
     plus, minus, lkind = _line_tables(P)
+    sides, side_max = _line_sides(plus, minus, npar)
     if process == "ee_mumu":
         num, den = [[1]], 1
         iden, cpow = 4.0, 2
@@ -267,6 +298,7 @@ __constant__ unsigned char c_ext_massive[{npar}] = {{{", ".join(str(x) for x in 
 __constant__ unsigned short c_line_plus[{nlines}] = {{{", ".join(str(x) for x in plus)}}};
 __constant__ unsigned short c_line_minus[{nlines}] = {{{", ".join(str(x) for x in minus)}}};
 __constant__ unsigned char c_line_kind[{nlines}] = {{{", ".join(str(x) for x in lkind)}}};
+__constant__ unsigned int c_line_side[{nlines}] = {{{", ".join(str(x) for x in sides)}}};
 static const int h_cnum[{ncol * ncol}] = {{{cnum_flat}}};
 static const int h_diag_lines[{4 * P.ndiagrams}] = {{{", ".join(str(x) for key in P.diag_lines for x in (list(key) + [0] * (4 - len(key))))}}};
 static const int h_diag_nlines[{P.ndiagrams}] = {{{", ".join(str(len(key)) for key in P.diag_lines)}}};
@@ -274,6 +306,8 @@ static const int h_diag_nlines[{P.ndiagrams}] = {{{", ".join(str(len(key)) for k
 struct Proc {{
     static constexpr int NPAR = {npar}, NCOL = {ncol}, NLINES = {nlines}, THREADS = {threads};
     static constexpr int CDEN = {den};
+    // most terms of a line momentum written over its shorter side (line_side)
+    static constexpr int SIDE = {max(side_max, 1)};
     static constexpr bool J_SMEM = {"true" if j_smem else "false"};
     static constexpr bool IS_TAB = false, IS_INTERP = false;{tc_members}
     __device__ static __forceinline__ unsigned ext_kind(int e) {{ return c_ext_kind[e]; }}
@@ -281,6 +315,7 @@ struct Proc {{
     __device__ static __forceinline__ unsigned line_plus(int l) {{ return c_line_plus[l]; }}
     __device__ static __forceinline__ unsigned line_minus(int l) {{ return c_line_minus[l]; }}
     __device__ static __forceinline__ unsigned line_kind(int l) {{ return c_line_kind[l]; }}
+    __device__ static __forceinline__ unsigned line_side(int l) {{ return c_line_side[l]; }}
 
     template <class T, bool SDE, class JT>
     __device__ static __forceinline__ void chain(const Wf<T>* __restrict__ ext, int hel, const Ln<T>* __restrict__ ln,

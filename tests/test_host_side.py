@@ -264,6 +264,46 @@ def test_colour_windows_replay_the_flow_updates():
     assert np.abs(J1 - J2).max() < 1e-12 * np.abs(J1).max()
 
 
+
+@pytest.mark.parametrize("process", ["ee_mumu", "gg_ttx", "gg_ttxg", "gg_ttxgg", "gg_ttxggg"])
+def test_line_sides_and_gram_denominators(orc, process):
+    """The FP32 kernels' per-event setup: each line's momentum written over its
+    shorter side (the generator's packed table) equals the line's defining sum
+    sum_plus p - sum_minus p, with at most three terms; the FP32 hi + lo split of
+    the momenta holds them to 2^-48; and p^2 - m^2 as the FP64 sum of Gram
+    entries c_a c_b p_a.p_b over that side equals the square of the FP64
+    momentum sum minus m^2 within FP64 rounding of the largest term."""
+    from paper_2507_21039_gb300.gen import emit
+
+    P = build_plan(process)
+    plus, minus, kind = emit._line_tables(P)
+    sides, kmax = emit._line_sides(plus, minus, P.npar)
+    assert kmax <= 3
+    w = WORKLOADS[process]
+    mom, _, _ = orc.rambo(w.seed, w.sqrt_s, w.masses_final, 0, 64, w.cut_mask, 20.0, 0.4)
+    mt = 0.0 if process == "ee_mumu" else MT
+    hi = mom.astype(np.float32)
+    lo = (mom - hi.astype(np.float64)).astype(np.float32)
+    assert np.all(np.abs(hi.astype(np.float64) + lo - mom) <= 2.0**-48 * np.abs(mom) + 1e-300)
+    mink = np.array([1.0, -1.0, -1.0, -1.0])
+    gram = np.einsum("emu,efu,u->emf", mom, mom, mink)
+    for pm, mm, kd, word in zip(plus, minus, kind, sides):
+        c = np.array([((pm >> i) & 1) - ((mm >> i) & 1) for i in range(P.npar)], dtype=float)
+        k = word & 7
+        terms = [((word >> (4 * a + 4)) & 7, -1.0 if (word >> (4 * a + 7)) & 1 else 1.0) for a in range(k)]
+        q = np.einsum("i,eiu->eu", c, mom)
+        q_side = sum(sg * mom[:, i, :] for i, sg in terms)
+        scale = mom[:, :, 0].sum(1)[:, None]
+        assert np.abs(q_side - q).max() <= 1e-10 * scale.max()
+        if kd == 0:
+            continue
+        m2 = mt * mt if kd == 2 else 0.0
+        direct = q[:, 0] ** 2 - (q[:, 1:] ** 2).sum(1) - m2
+        via_gram = -m2 + sum((1.0 if a == b else 2.0) * ta[1] * tb[1] * gram[:, ta[0], tb[0]]
+                             for a, ta in enumerate(terms) for b, tb in enumerate(terms) if b >= a)
+        assert np.all(np.abs(via_gram - direct) <= 1e-9 * scale[:, 0] ** 2)
+
+
 @pytest.mark.parametrize("process", ["gg_ttxgg", "gg_ttxggg"])
 def test_delta_r_guard_band_covers_fp32_error(orc, process):
     """The sampler decides the Delta R cut in FP32 (eta = asinh(pz / pT)) and
