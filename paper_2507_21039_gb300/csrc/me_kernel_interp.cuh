@@ -7,23 +7,43 @@
 // amplitudes into stages: each stage first computes, cooperatively and level by
 // level, the table objects its amplitudes need that are not yet resident (into
 // slots freed by objects whose last reader has passed), then every thread
-// evaluates the stage's amplitudes for its helicity from compact descriptors
-// and adds them into its colour-flow vector J.  Amplitudes with the same colour
-// vector up to a sign form a colour group: their signed sum G is added into J
-// once, by the group's last member.  In FP32, J lives in shared memory (or, as a
-// build option, in tensor memory: one TMEM lane per thread, two columns per
-// flow, updated from per-thread accumulator slots at the end of each colour
-// window, which leaves shared memory to the table so that two CTAs share an
-// SM); in FP64 it lives in a global scratch (L2-resident), whose tables alone
-// fill shared memory.
+// evaluates the stage's amplitudes for its helicity from compact descriptors.
+// Amplitudes with the same colour vector up to a sign form a colour group:
+// their signed sum G is added into the colour-flow vector J once, as +-i G on
+// each flow of the group.
+//
+// Where J lives:
+//   * FP32 (default): in tensor memory, accumulated by the tensor cores.  The
+//     group sums of one stage (at most 16) form, per helicity, the rows of
+//     A = [Re G | Im G] (128 helicities x 16); with the stage's sign matrix B
+//     (flow x group, entries +-1 / 0, built by the generator), one stage adds
+//     Re J += Im G . B and Im J += Re G . (-B).  G is split exactly into three
+//     BF16 parts (8 + 8 + 8 significant bits), B is exact in BF16, the tensor
+//     cores accumulate in FP32 in TMEM (columns 0-127 Re J, 128-255 Im J of the
+//     thread's lane): six tcgen05.mma (M = 128, N = 128, K = 16) per stage,
+//     issued by one thread after the CTA barrier that ends the stage.  J then
+//     needs no shared memory, so two CTAs share an SM.
+//   * FP32, build option ME_INTERP_J_MMA=0: in shared memory, updated flow by
+//     flow by each group's last member (one CTA per SM).
+//   * FP64: in a global scratch (L2-resident), updated flow by flow; its tables
+//     alone fill shared memory.
 #pragma once
+#include <algorithm>
+
 #include "me_kernel_tab.cuh"
 #include "me_tmem.cuh"
 
-// Build option ME_INTERP_J_TMEM: FP32 colour-flow vector in tensor memory (1)
-// or in shared memory (0, measured faster)
-#ifndef ME_INTERP_J_TMEM
-#define ME_INTERP_J_TMEM 0
+// Build option ME_INTERP_J_MMA: FP32 colour-flow vector accumulated by the
+// tensor cores in tensor memory (1, default) or updated in shared memory (0)
+#ifndef ME_INTERP_J_MMA
+#define ME_INTERP_J_MMA 1
+#endif
+
+// Bound on each wait for the tensor cores (clock cycles, about a second):
+// a wait that runs out marks the thread's events as failed (|M|^2 = NaN) and
+// the kernel stops waiting instead of hanging the GPU
+#ifndef ME_WAIT_LIMIT_CYCLES
+#define ME_WAIT_LIMIT_CYCLES (1LL << 31)
 #endif
 
 namespace me {
@@ -48,9 +68,9 @@ enum IRoutine : unsigned char {
     R_FFV1A_3, R_FFV1A_2, R_FFV1A_1, R_VVV1A_1, R_VVV1A_2, R_VVV1A_3, R_VVVV1A, R_VVVV3A, R_VVVV4A
 };
 enum IAmpKind : unsigned char { A_FFV1_0 = 0, A_VVV1_0, A_VVVV1_0, A_VVVV3_0, A_VVVV4_0, A_DOTV, A_DOTF };
-// IAmp.kind flags above the kind: the amplitude enters its colour group's sum
-// with a minus sign; the amplitude closes a colour window
-constexpr unsigned char AMP_NEG = 0x80, AMP_WINDOW_END = 0x40;
+// IAmp.kind flag above the kind: the amplitude enters its colour group's sum
+// with a minus sign
+constexpr unsigned char AMP_NEG = 0x80;
 
 template <class P, class T> struct InterpLayout {
     static constexpr size_t mom = 0;
@@ -61,21 +81,20 @@ template <class P, class T> struct InterpLayout {
     static constexpr size_t vsup = (lines + P::NLINES * sizeof(Ln<T>) + 15) / 16 * 16;
     static constexpr size_t table = (vsup + (size_t)P::NSUP * P::NT + 15) / 16 * 16;
     static constexpr size_t jsm = table + (size_t)P::TAB * sizeof(Wf<T>);
-    // TMEM: 4 warps = 128 lanes, 2 FP32 columns per flow in a 256-column allocation
-    static constexpr bool J_IN_TMEM = sizeof(T) == 4 && ME_INTERP_J_TMEM && P::NT == 128 && 2 * P::NCOL <= 256 &&
-                                      (2 * P::NCOL) % 16 == 0;
-    static constexpr bool J_IN_SMEM = sizeof(T) == 4 && !J_IN_TMEM;
+    // J accumulated by the tensor cores: 128 lanes x (128 + 128) FP32 columns
+    static constexpr bool J_MMA = sizeof(T) == 4 && ME_INTERP_J_MMA;
+    static constexpr bool J_IN_SMEM = sizeof(T) == 4 && !J_MMA;
     static constexpr uint32_t TMEM_COLS = 256;
-    // J in TMEM: the colour windows' accumulator slots, [slot][thread] FP32 complex
-    static constexpr size_t acc = jsm;
-    static constexpr size_t bytes = jsm + (J_IN_SMEM ? (size_t)P::NCOL * P::NT * sizeof(cx<T>) : 0) +
-                                    (J_IN_TMEM ? (size_t)P::NSLOT * P::NT * sizeof(cx<float>) : 0);
+    // J_MMA operands: six A matrices (BF16 hi / mid / lo of Im G and Re G, 128 x 16
+    // each) and the stage's sign matrix B (128 flows x 16), 4096 bytes each
+    static constexpr size_t amat = (jsm + 1023) / 1024 * 1024;
+    static constexpr size_t bmat = amat + 6 * 4096;
+    static constexpr size_t bytes = J_MMA ? bmat + 4096
+                                          : jsm + (J_IN_SMEM ? (size_t)P::NCOL * P::NT * sizeof(cx<T>) : 0);
     // colour sum from TMEM: per warp, J as [flow][lane] FP32 and 32 floats of row
     // totals, two warps at a time over the (then dead) table
     static constexpr size_t WJ = (size_t)P::NCOL * 32 * sizeof(cx<float>) + 32 * sizeof(float);
-    // at most 512 / TMEM_COLS CTAs may share an SM: shared memory is requested so
-    // that no third one fits (228 KB per SM, 1 KB reserved per CTA)
-    static constexpr size_t launch_bytes = J_IN_TMEM && bytes < 78 * 1024 ? 78 * 1024 : bytes;
+    static constexpr size_t launch_bytes = bytes;
 };
 
 template <class T, int TAB>
@@ -104,22 +123,32 @@ __device__ __forceinline__ void run_task(const TabRef<T, TAB>& tab, const Ln<T>*
     tab.st(k.out, o);
 }
 
+// Three-way exact BF16 split of x (x = hi + mid + lo for finite x in the
+// normal range: each part takes the next 8 significant bits)
+__device__ __forceinline__ void bf16_split3(float x, __nv_bfloat16& hi, __nv_bfloat16& mid, __nv_bfloat16& lo)
+{
+    hi = __float2bfloat16_rn(x);
+    const float r = x - __bfloat162float(hi);
+    mid = __float2bfloat16_rn(r);
+    lo = __float2bfloat16_rn(r - __bfloat162float(mid));
+}
+
 // TC: colour sum on BF16 tensor cores (T = float); otherwise scalar in C
 template <class P, class T, bool TC, class C = T, bool SDE = false>
 __global__ void __launch_bounds__(P::NT) me_kernel_interp(LaunchArgs a, cx<T>* __restrict__ jglobal)
 {
     using L = InterpLayout<P, T>;
-    extern __shared__ __align__(16) unsigned char smem[];
+    extern __shared__ __align__(1024) unsigned char smem[];
     constexpr int NPAR = P::NPAR, NL = P::NLINES, NT = P::NT, NCOL = P::NCOL;
     double* smom = reinterpret_cast<double*>(smem + L::mom);
     Ln<T>* sln = reinterpret_cast<Ln<T>*>(smem + L::lines);
     unsigned char* vsup = smem + L::vsup;
     const TabRef<T, P::TAB> tab{reinterpret_cast<uint4*>(smem + L::table)};
     // this thread's colour-flow vector: J[c] at jp[c * NT] (shared or global
-    // memory), or TMEM columns 2c, 2c+1 of its lane from tj
+    // memory), or TMEM columns c (Re) and 128 + c (Im) of its lane from tj
     cx<T>* jp = nullptr;
     if constexpr (L::J_IN_SMEM) jp = reinterpret_cast<cx<T>*>(smem + L::jsm) + threadIdx.x;
-    else if constexpr (!L::J_IN_TMEM) jp = jglobal + (size_t)blockIdx.x * NCOL * NT + threadIdx.x;
+    else if constexpr (!L::J_MMA) jp = jglobal + (size_t)blockIdx.x * NCOL * NT + threadIdx.x;
     __shared__ double red[NT / 32];
     __shared__ FSum fred[NT / 32];
     __shared__ double red_sde[SDE ? 2 : 1][NT / 32];
@@ -130,15 +159,29 @@ __global__ void __launch_bounds__(P::NT) me_kernel_interp(LaunchArgs a, cx<T>* _
     const float mtf = (float)a.mt;
     __shared__ float rowv[NT];
     __shared__ uint32_t tmem_base;
+    __shared__ __align__(8) uint64_t mma_bar;
     const int tid = threadIdx.x;
     const bool act = tid < a.nlist;
     uint32_t tj = 0;
-    if constexpr (L::J_IN_TMEM) {
+    uint32_t ncommit = 0;  // tensor-core commits so far (the same count in every thread)
+    bool failed = false;   // a wait for the tensor cores ran out: this thread stops waiting
+    if constexpr (L::J_MMA) {
+        static_assert(NT == 128 && NCOL <= 128, "one TMEM lane per helicity, one column per flow");
+        static_assert(P::MAXFLUSH <= 16, "at most 16 colour-group updates per stage (one K = 16 step)");
         static_assert(2 * L::WJ <= (size_t)P::TAB * sizeof(Wf<T>), "colour staging exceeds the table");
         if (tid < 32) {
             tmem_alloc(&tmem_base, L::TMEM_COLS);
             tmem_relinquish();
         }
+        if (tid == 0) {
+            mbar_init(&mma_bar, 1);
+            mbar_init_fence();
+        }
+        // operands start at zero: a slot no group of a stage uses is multiplied by
+        // a zero column of B and must hold a finite value
+        uint4* z = reinterpret_cast<uint4*>(smem + L::amat);
+        for (int i = tid; i < 7 * 4096 / 16; i += NT) z[i] = make_uint4(0u, 0u, 0u, 0u);
+        fence_proxy_async_smem();
         tmem_fence_before_sync();
         __syncthreads();
         tmem_fence_after_sync();
@@ -156,14 +199,16 @@ __global__ void __launch_bounds__(P::NT) me_kernel_interp(LaunchArgs a, cx<T>* _
         }
     };
     if (!a.hel_ev) variants(a.hel_list[act ? tid : 0]);
+    // wait for the tensor cores' commit number c (its mbarrier phase parity is c & 1)
+    auto wait_commit = [&](uint32_t c) {
+        if (!failed && !mbar_wait_bounded(&mma_bar, c & 1u, ME_WAIT_LIMIT_CYCLES)) failed = true;
+    };
 
     for (long long e = blockIdx.x; e < a.nevt; e += gridDim.x) {
         if (a.hel_ev) variants(a.hel_ev[e]);  // helicity sampling: one helicity per event (nlist = 1)
         const double* g = a.mom + e * NPAR * 4;
         for (int i = tid; i < NPAR * 4; i += NT) smom[i] = __ldg(g + i);
-        if constexpr (L::J_IN_TMEM) {
-            for (int c = 0; c < 2 * NCOL; c += 16) tmem_zero_16(tj + c);
-        } else {
+        if constexpr (!L::J_MMA) {
             for (int c = 0; c < NCOL; ++c) jp[c * NT] = {T(0), T(0)};
         }
         __syncthreads();
@@ -189,7 +234,7 @@ __global__ void __launch_bounds__(P::NT) me_kernel_interp(LaunchArgs a, cx<T>* _
         const T mt = (T)a.mt;
         T snum = T(0), sden = T(0);
         cx<T> G = {T(0), T(0)};  // open colour group: sum of its amplitudes with their signs
-        int win = 0;              // current colour window (J in TMEM)
+        bool nonfinite = false;   // a group sum was not finite (it enters J as 0; |M|^2 = NaN)
         for (int s = 0; s < P::NSTAGE; ++s) {
             const IStage st = P::stage(s);
             for (int r = st.round_begin; r < st.round_end; ++r) {
@@ -199,6 +244,17 @@ __global__ void __launch_bounds__(P::NT) me_kernel_interp(LaunchArgs a, cx<T>* _
             }
             __syncthreads();
             int term = P::stage_term_begin(s);
+            int slot = 0;  // J_MMA: the stage's next group update (column of A)
+            if constexpr (L::J_MMA) {
+                // the previous stage's tensor-core work has read A and B: they may be rewritten;
+                // this stage's sign matrix is copied in while the amplitudes are evaluated
+                if (ncommit > 0) wait_commit(ncommit - 1);
+                const uint4* bsrc = P::bmat(s);
+                uint4* bsm = reinterpret_cast<uint4*>(smem + L::bmat);
+                cp_async16(bsm + tid, bsrc + tid);
+                cp_async16(bsm + tid + NT, bsrc + tid + NT);
+                cp_async_commit();
+            }
             for (int ai = st.amp_begin; ai < st.amp_end; ++ai) {
                 const IAmp d = P::amp(ai);
                 const int kind = d.kind & 0x3f;
@@ -230,16 +286,22 @@ __global__ void __launch_bounds__(P::NT) me_kernel_interp(LaunchArgs a, cx<T>* _
                 else { G.re += x.re; G.im += x.im; }
                 // the group's last member: every colour coefficient is +-i, J_c += +-i G
                 if (d.nterm) {
-                    if constexpr (L::J_IN_TMEM) {
-                        // into this window's accumulator slots (first touch assigns)
-                        cx<float>* accp = reinterpret_cast<cx<float>*>(smem + L::acc) + tid;
-                        for (int k = 0; k < d.nterm; ++k, ++term) {
-                            const unsigned short ct = P::sterm(term);
-                            cx<float>& s = accp[(ct & 0x1f) * NT];
-                            const cx<float> x = (ct & 0x8000) ? cx<float>{(float)G.im, -(float)G.re}
-                                                               : cx<float>{-(float)G.im, (float)G.re};
-                            s = (ct & 0x4000) ? x : cx<float>{s.re + x.re, s.im + x.im};
+                    if constexpr (L::J_MMA) {
+                        // row tid, column `slot` of the six A matrices: BF16 parts of Im G, Re G
+                        float gr = (float)G.re, gi = (float)G.im;
+                        if (!(isfinite(gr) && isfinite(gi))) {
+                            nonfinite = true;
+                            gr = gi = 0.0f;
                         }
+                        __nv_bfloat16 q[6];
+                        bf16_split3(gi, q[0], q[1], q[2]);
+                        bf16_split3(gr, q[3], q[4], q[5]);
+                        const uint32_t off = umma_k16_offset(tid, slot);
+#pragma unroll
+                        for (int m = 0; m < 6; ++m)
+                            *reinterpret_cast<__nv_bfloat16*>(smem + L::amat + (size_t)m * 4096 + off) = q[m];
+                        ++slot;
+                        term += d.nterm;
                     } else {
                         for (int k = 0; k < d.nterm; ++k, ++term) {
                             const unsigned short ct = P::term(term);
@@ -250,30 +312,29 @@ __global__ void __launch_bounds__(P::NT) me_kernel_interp(LaunchArgs a, cx<T>* _
                     }
                     G = {T(0), T(0)};
                 }
-                if constexpr (L::J_IN_TMEM) {
-                    if (d.kind & AMP_WINDOW_END) {  // J += the window's slots, eight flows per TMEM round trip
-                        const cx<float>* accp = reinterpret_cast<const cx<float>*>(smem + L::acc) + tid;
-                        const int f0 = P::wbegin(win), n = P::wbegin(win + 1) - f0;
-                        __syncwarp();  // the TMEM accesses are warp-collective
-                        for (int k0 = 0; k0 < n; k0 += 8) {
-                            uint32_t ad[8], v[16];
-#pragma unroll
-                            for (int q = 0; q < 8; ++q) ad[q] = tj + 2u * (uint32_t)P::wflow(f0 + min(k0 + q, n - 1));
-                            tmem_ld_8x2(ad, v);
-#pragma unroll
-                            for (int q = 0; q < 8; ++q) {
-                                if (k0 + q < n) {  // a short last round repeats its last flow and stores nothing for it
-                                    const cx<float> sl = accp[(k0 + q) * NT];
-                                    tmem_st_2(ad[q], __float_as_uint(__uint_as_float(v[2 * q]) + sl.re),
-                                              __float_as_uint(__uint_as_float(v[2 * q + 1]) + sl.im));
-                                }
-                            }
-                        }
-                        ++win;
-                    }
-                }
+            }
+            if constexpr (L::J_MMA) {
+                cp_async_wait_all();
+                fence_proxy_async_smem();  // A and B writes -> the tensor cores' view of shared memory
             }
             __syncthreads();  // stage done: its dead table slots are reused by the next stage
+            if constexpr (L::J_MMA) {
+                if (tid == 0 && !failed) {
+                    tmem_fence_after_sync();
+                    const uint64_t bdesc = umma_smem_desc(smem + L::bmat, 128, 256);
+                    constexpr uint32_t ID_POS = umma_idesc_bf16_f32(128, 128, false);
+                    constexpr uint32_t ID_NEG = umma_idesc_bf16_f32(128, 128, true);
+#pragma unroll
+                    for (int m = 0; m < 3; ++m) {  // the first update of an event overwrites J
+                        const bool acc = s > 0 || m > 0;
+                        umma_bf16(tmem_base, umma_smem_desc(smem + L::amat + (size_t)m * 4096, 128, 256), bdesc, ID_POS, acc);
+                        umma_bf16(tmem_base + 128, umma_smem_desc(smem + L::amat + (size_t)(3 + m) * 4096, 128, 256),
+                                  bdesc, ID_NEG, acc);
+                    }
+                    umma_commit(&mma_bar);
+                }
+                ++ncommit;
+            }
         }
         // colour quadratic form sum_ij N_ij Re(conj J_i J_j)
         T v = T(0);
@@ -292,19 +353,21 @@ __global__ void __launch_bounds__(P::NT) me_kernel_interp(LaunchArgs a, cx<T>* _
             }
             return (T)w;
         };
-        if constexpr (L::J_IN_TMEM) {
-            __syncthreads();  // every warp has finished its amplitudes: the table is dead
+        if constexpr (L::J_MMA) {
+            wait_commit(ncommit - 1);  // this event's last tensor-core update is in J
+            tmem_fence_after_sync();
             const int w = tid >> 5, lane = tid & 31;
             unsigned char* stage = smem + L::table + (size_t)(w & 1) * L::WJ;
             cx<float>* js = reinterpret_cast<cx<float>*>(stage);
-            for (int r = 0; r < 2; ++r) {   // warps 0, 1 then warps 2, 3
+            for (int r = 0; r < 2; ++r) {   // warps 0, 1 then warps 2, 3 over the dead table
                 if ((w >> 1) == r) {
-                    for (int c = 0; c < 2 * NCOL; c += 16) {
-                        uint32_t q16[16];
-                        tmem_ld_16(tj + c, q16);
+                    for (int c = 0; c < NCOL; c += 16) {
+                        uint32_t qr[16], qi[16];
+                        tmem_ld_16(tj + (uint32_t)c, qr);
+                        tmem_ld_16(tj + 128u + (uint32_t)c, qi);
 #pragma unroll
-                        for (int q = 0; q < 8; ++q)
-                            js[(c / 2 + q) * 32 + lane] = {__uint_as_float(q16[2 * q]), __uint_as_float(q16[2 * q + 1])};
+                        for (int q = 0; q < 16; ++q)
+                            if (c + q < NCOL) js[(c + q) * 32 + lane] = {__uint_as_float(qr[q]), __uint_as_float(qi[q])};
                     }
                     __syncwarp();
                     if constexpr (TC)
@@ -315,6 +378,7 @@ __global__ void __launch_bounds__(P::NT) me_kernel_interp(LaunchArgs a, cx<T>* _
                 }
                 __syncthreads();
             }
+            if (nonfinite || failed) v = T(NAN);
         } else if constexpr (TC) {
             v = colour_tc_smem<NCOL, NT, P::NSPLIT>(reinterpret_cast<const cx<float>*>(smem + L::jsm), P::bfrag(),
                                                     rowv, tid);
@@ -366,9 +430,13 @@ __global__ void __launch_bounds__(P::NT) me_kernel_interp(LaunchArgs a, cx<T>* _
             a.me2[e] = s * a.norm * (a.w_ev ? a.w_ev[e] : 1.0);
             if constexpr (SDE) a.sde_w[e] = sd > 0.0 ? sn / sd : 0.0;
         }
+        tmem_fence_before_sync();  // this event's TMEM loads are done before the next event's first update
         __syncthreads();
     }
-    if constexpr (L::J_IN_TMEM) {   // every load was waited for; the allocating warp releases the columns
+    if constexpr (L::J_MMA) {
+        // the last commit was waited for by every thread (unless a wait ran out:
+        // then wait once more, bounded, before the columns are released)
+        if (ncommit > 0 && failed) mbar_wait_bounded(&mma_bar, (ncommit - 1) & 1u, ME_WAIT_LIMIT_CYCLES);
         tmem_fence_before_sync();
         __syncthreads();
         if (tid < 32) {
@@ -382,7 +450,7 @@ __global__ void __launch_bounds__(P::NT) me_kernel_interp(LaunchArgs a, cx<T>* _
 template <class P, class T> constexpr size_t interp_jscratch_per_cta()
 {
     using L = InterpLayout<P, T>;
-    return (!L::J_IN_SMEM && !L::J_IN_TMEM) ? sizeof(cx<T>) * (size_t)P::NCOL * P::NT : 0;
+    return (!L::J_IN_SMEM && !L::J_MMA) ? sizeof(cx<T>) * (size_t)P::NCOL * P::NT : 0;
 }
 
 // One-time kernel attributes and the number of resident CTAs per SM of the
@@ -413,7 +481,24 @@ template <class P, class T, bool TC, class C, bool SDE> cudaError_t interp_resid
         cudaGetLastError();
         per_sm = 1;
     }
-    if (L::J_IN_TMEM && per_sm > (int)(512 / L::TMEM_COLS)) per_sm = 512 / L::TMEM_COLS;
+    if constexpr (L::J_MMA) {
+        // The occupancy query counts one CTA per SM for a kernel that allocates
+        // tensor memory; the SM takes another CTA once the resident one has
+        // given up its allocation permit (right after its allocation here), so
+        // the residency is what shared memory, registers and TMEM columns allow
+        int smem_sm = 0, reserved = 0;
+        cudaFuncAttributes fa{};
+        if (cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) == cudaSuccess &&
+            cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev) == cudaSuccess &&
+            cudaFuncGetAttributes(&fa, me_kernel_interp<P, T, TC, C, SDE>) == cudaSuccess && fa.numRegs > 0) {
+            const int by_smem = (int)((size_t)smem_sm / (L::launch_bytes + fa.sharedSizeBytes + (size_t)reserved));
+            const int regs = (fa.numRegs + 7) / 8 * 8;
+            const int by_regs = 65536 / (regs * P::NT);
+            per_sm = std::max(1, std::min({by_smem, by_regs, (int)(512 / L::TMEM_COLS)}));
+        } else {
+            cudaGetLastError();
+        }
+    }
     return cudaSuccess;
 }
 

@@ -88,4 +88,102 @@ __device__ __forceinline__ void tmem_zero_16(uint32_t addr)
         :: "r"(addr), "r"(z) : "memory");
 }
 
+// ---------------------------------------------------------------------------
+// tcgen05.mma with operands in shared memory and the accumulator in TMEM.
+//
+// Operand layout (both A [M x K] and B [N x K], K-major, no swizzle): the
+// matrix is cut into core matrices of 8 rows x 16 bytes (8 BF16 along K),
+// each stored as 128 contiguous bytes (row r at byte 16 r).  Core matrix
+// (row group i, K group j) starts at i * SBO + j * LBO.  Here LBO = 128 and
+// SBO = 256 for a K = 16 operand: the two K groups of a row group are adjacent,
+// row groups follow each other.  Element (row, k) of a K = 16 operand is at
+// byte (row / 8) * 256 + (k / 8) * 128 + (row % 8) * 16 + (k % 8) * 2.
+// ---------------------------------------------------------------------------
+__host__ __device__ constexpr uint32_t umma_k16_offset(int row, int k)
+{
+    return (uint32_t)((row >> 3) * 256 + (k >> 3) * 128 + (row & 7) * 16 + (k & 7) * 2);
+}
+
+// shared-memory matrix descriptor: start address, leading-dimension (K)
+// byte offset, stride-dimension (M/N) byte offset, each in 16-byte units;
+// bit 46 set (descriptor version of the sm_100 family); no swizzle, base offset 0
+__device__ __forceinline__ uint64_t umma_smem_desc(const void* smem_ptr, uint32_t lbo, uint32_t sbo)
+{
+    const uint32_t a = (uint32_t)__cvta_generic_to_shared(smem_ptr);
+    return (uint64_t)((a >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
+// instruction descriptor of kind::f16: FP32 accumulator (bits 4-5 = 1), BF16 A
+// and B (bits 7-9, 10-12 = 1), B optionally negated (bit 14), both K-major
+// (bits 15, 16 = 0), N / 8 at bits 17-22, M / 16 at bits 24-28
+__host__ __device__ constexpr uint32_t umma_idesc_bf16_f32(int m, int n, bool neg_b)
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | (neg_b ? (1u << 14) : 0u) | ((uint32_t)(n >> 3) << 17) |
+           ((uint32_t)(m >> 4) << 24);
+}
+
+// D[tmem] (+)= A * B for one M x N x 16 step, issued by a single thread;
+// accumulate = false overwrites D
+__device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t idesc,
+                                          bool accumulate)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+        :: "r"(d_tmem), "l"(a_desc), "l"(b_desc), "r"(idesc), "r"((uint32_t)accumulate)
+        : "memory");
+}
+
+// the mbarrier at `bar` receives one arrival once every tcgen05.mma this
+// thread issued before has completed
+__device__ __forceinline__ void umma_commit(uint64_t* bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                 :: "r"((uint32_t)__cvta_generic_to_shared(bar)) : "memory");
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"((uint32_t)__cvta_generic_to_shared(bar)), "r"(count)
+                 : "memory");
+}
+__device__ __forceinline__ void mbar_init_fence() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+
+// generic-proxy shared-memory writes of this thread become visible to the
+// async proxy (the tensor cores reading operands)
+__device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// 16-byte copy global -> shared that completes in the background
+// (cp.async; both addresses 16-byte aligned), and the wait for this thread's copies
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;"
+                 :: "r"((uint32_t)__cvta_generic_to_shared(smem_dst)), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok) : "r"((uint32_t)__cvta_generic_to_shared(bar)), "r"(parity) : "memory");
+    return ok != 0;
+}
+
+// Wait for the completion of the phase with the given parity, for at most
+// `limit` clock cycles.  Returns false if the limit passed first.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, long long limit)
+{
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity))
+        if (clock64() - t0 > limit) return false;
+    return true;
+}
+
 }  // namespace me

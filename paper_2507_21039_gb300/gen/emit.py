@@ -32,7 +32,7 @@ TAB_PROCESSES = {"gg_ttxg": (32, 1, 1, 1, 0, 1, 4), "gg_ttxgg": (64, 2, 2, 5, 60
 #             memory, so the table peak of its stages must fit beside J; FP64
 #             keeps J in a global scratch.  One schedule for both precisions lets
 #             them share one descriptor set (in constant memory).
-INTERP_PROCESSES = {"gg_ttxggg": (128, 32, 0, 32, 0)}
+INTERP_PROCESSES = {"gg_ttxggg": (128, 16, 0, 16, 0)}
 
 
 def _apply_kernel_overrides():
@@ -124,6 +124,12 @@ def _line_sides(plus, minus, npar):
         out.append(word)
         kmax = max(kmax, n)
     return out, kmax
+
+
+def umma_k16_offset(row: int, k: int) -> int:
+    """Byte offset of element (row, k) in a K = 16 BF16 tensor-core operand,
+    K-major core matrices of 8 rows x 16 bytes (me_tmem.cuh: umma_k16_offset)."""
+    return (row >> 3) * 256 + (k >> 3) * 128 + (row & 7) * 16 + (k & 7) * 2
 
 
 def _bf16_bits(x: float) -> int:
@@ -683,8 +689,6 @@ NL = "\n"
 # option ME_INTERP_CONST=0 keeps them in global memory)
 CONST_DESCRIPTORS = __import__("os").environ.get("ME_INTERP_CONST", "1") != "0"
 # accumulator slots per thread for the colour windows of the staged descriptor
-# kernel (shared memory: ACC_SLOTS x 8 B per thread)
-ACC_SLOTS = 24
 
 
 def emit_interp_struct(process: str, nt: int, stage_amps: int, num, mode: int = 0,
@@ -698,28 +702,13 @@ def emit_interp_struct(process: str, nt: int, stage_amps: int, num, mode: int = 
     npar = P.npar
     ops = P.ops
     tasks, rounds, stages, amps, terms, stage_term, diags = [], [], [], [], [], [], []
-    # colour windows (J in tensor memory): consecutive group updates that touch
-    # at most ACC_SLOTS distinct flows go to per-thread accumulator slots; the
-    # last update of a window adds the slots into J.  A window closes before
-    # the update that would exceed the slots.
-    wend, wflows, cur = set(), [], []
-    last_flush = None
-    for ai in I.amp_order:
-        if ai in I.flush:
-            fl = [f for f, _ in I.flush[ai]]
-            assert len(fl) <= ACC_SLOTS
-            if len(set(cur) | set(fl)) > ACC_SLOTS:
-                wend.add(last_flush)
-                wflows.append(cur)
-                cur = []
-            cur += [f for f in fl if f not in cur]
-            last_flush = ai
-    wend.add(last_flush)
-    wflows.append(cur)
-    wbegin = [0]
-    for w in wflows:
-        wbegin.append(wbegin[-1] + len(w))
-    sterms, wi, assigned = [], 0, set()
+    # per stage, the colour-group updates as a tensor-core operand (J accumulated
+    # by tcgen05.mma in FP32 kernels): B[n][k] = sigma of flow n in the stage's
+    # k-th group update, where that update adds -i G (sigma = +1) or +i G
+    # (sigma = -1) to J_n; Re J += Im G . B and Im J += Re G . (-B).  BF16
+    # +-1 / 0 in the K-major core-matrix layout of a 128 x 16 operand
+    # (me_tmem.cuh: umma_k16_offset), one 4096-byte image per stage.
+    bmat, maxflush = [], 0
     for st in I.stages:
         r0 = len(rounds)
         for ri, (kind, tl) in enumerate(st.rounds):
@@ -747,17 +736,18 @@ def emit_interp_struct(process: str, nt: int, stage_amps: int, num, mode: int = 
             # (kind bit 7 = minus); the group's last member carries the terms
             gterms = I.flush.get(ai, ())
             assert len(op.args) <= 4 and len(gterms) < 256 and all(c in ((0, 1), (0, -1)) for _, c in coefs + gterms)
-            kind = AMP_KINDS.index(op.kind) | (0x80 if I.sign[ai] < 0 else 0) | (0x40 if ai in wend else 0)
+            kind = AMP_KINDS.index(op.kind) | (0x80 if I.sign[ai] < 0 else 0)
             amps.append((bases, sups, kind, la, lb, len(gterms)))
             for col, c in gterms:
                 terms.append(col | (0x8000 if c == (0, -1) else 0))
-                # the same term as (slot of the flow in its window, assign on first touch, sign)
-                slot = wflows[wi].index(col)
-                sterms.append(slot | (0x4000 if slot not in assigned else 0) | (0x8000 if c == (0, -1) else 0))
-                assigned.add(slot)
-            if ai in wend:
-                wi += 1
-                assigned = set()
+        img = [0] * 2048   # BF16 halves of one stage's 128 x 16 operand
+        flushes = [ai for ai in st.amps if ai in I.flush]
+        maxflush = max(maxflush, len(flushes))
+        for k, ai in enumerate(flushes[:16]):
+            for col, c in I.flush[ai]:
+                assert col < 128
+                img[umma_k16_offset(col, k) // 2] = 0x3F80 if c == (0, -1) else 0xBF80
+        bmat += [img[i] | (img[i + 1] << 16) for i in range(0, 2048, 2)]
         stages.append((r0, len(rounds), a0, len(amps)))
     masks = []
     for S in I.supports:
@@ -792,9 +782,8 @@ def emit_interp_struct(process: str, nt: int, stage_amps: int, num, mode: int = 
         *a[0], *a[1], a[2], a[3], a[4], a[5]), 3)
     src += arr("c_terms", "unsigned short", terms, lambda x: "%d" % x, 16)
     src += arr("c_stage_term", "int", stage_term, lambda x: "%d" % x, 16)
-    src += arr("c_sterms", "unsigned short", sterms, lambda x: "%d" % x, 16)
-    src += arr("c_wflow", "unsigned char", [f for w in wflows for f in w], lambda x: "%d" % x, 24)
-    src += arr("c_wbegin", "unsigned short", wbegin, lambda x: "%d" % x, 16)
+    src += (f"__device__ __align__(128) const unsigned int {prefix}c_bmat[{len(bmat)}] = {{\n    "
+            + ",\n    ".join(", ".join("%du" % x for x in bmat[i:i + 12]) for i in range(0, len(bmat), 12)) + "\n};\n")
     src += arr("c_supmask", "unsigned short", masks, lambda x: "%d" % x, 16)
     src += arr("c_cnum2", "short", cnum2, lambda x: "%d" % x, 24)
     src += arr("c_diag", "unsigned short", diags, lambda x: "%d" % x, 16)
@@ -811,11 +800,10 @@ struct {name} : Proc {{
     __device__ static __forceinline__ IAmp amp(int a) {{ return {prefix}c_amps[a]; }}
     __device__ static __forceinline__ unsigned short term(int t) {{ return {rd("c_terms", "t")}; }}
     __device__ static __forceinline__ int stage_term_begin(int s) {{ return {prefix}c_stage_term[s]; }}
-    // colour windows: slot-encoded terms, the flows of each window in slot order
-    static constexpr int NSLOT = {ACC_SLOTS}, NWIN = {len(wflows)};
-    __device__ static __forceinline__ unsigned short sterm(int t) {{ return __ldg({prefix}c_sterms + t); }}
-    __device__ static __forceinline__ int wbegin(int w) {{ return __ldg({prefix}c_wbegin + w); }}
-    __device__ static __forceinline__ int wflow(int i) {{ return __ldg({prefix}c_wflow + i); }}
+    // colour-group updates per stage as tensor-core operands (4096 bytes each);
+    // most group updates in one stage (the tensor-core path takes at most 16)
+    static constexpr int MAXFLUSH = {maxflush};
+    __device__ static __forceinline__ const uint4* bmat(int s) {{ return reinterpret_cast<const uint4*>({prefix}c_bmat) + 256 * s; }}
     __device__ static __forceinline__ unsigned support_mask(int s) {{ return {prefix}c_supmask[s]; }}
     __device__ static __forceinline__ int cnum2(int i, int j) {{ return __ldg({prefix}c_cnum2 + i * NCOL + j); }}
     __device__ static __forceinline__ int diag(int a) {{ return {rd("c_diag", "a")}; }}

@@ -221,11 +221,14 @@ def test_interpreter_descriptors_encode_the_colour_groups():
     assert t == len(terms)
 
 
-def test_colour_windows_replay_the_flow_updates():
-    """The slot-encoded colour updates of the descriptor kernel (per-thread
-    accumulator slots, first touch assigns, J += slots at each window's end)
-    give the same J as the flow-indexed updates, for random group sums."""
-    from paper_2507_21039_gb300.gen.emit import ACC_SLOTS, emit_interp_struct
+def test_stage_sign_matrices_replay_the_flow_updates():
+    """The FP32 descriptor kernel accumulates J on the tensor cores: per stage,
+    Re J += Im G . B and Im J += Re G . (-B), G the stage's group sums in update
+    order (at most 16), B the generator's sign matrix of the stage decoded from
+    its BF16 image in the K-major core-matrix operand layout.  For random group
+    sums this gives the same J as the flow-by-flow updates J_c += -i G (flag set)
+    or +i G, and nothing in the padding flows 120..127."""
+    from paper_2507_21039_gb300.gen.emit import emit_interp_struct, umma_k16_offset
 
     src, I = emit_interp_struct("gg_ttxggg", 128, 16, colour_matrix(5)[0], 0)
 
@@ -233,36 +236,36 @@ def test_colour_windows_replay_the_flow_updates():
         body = re.search(r"\b" + name + r"\[\d+\] = \{(.*?)\};", src, re.S).group(1)
         return [int(x) for x in re.findall(r"-?\d+", body)]
 
-    terms, sterms, wflow, wbegin = array("c_terms"), array("c_sterms"), array("c_wflow"), array("c_wbegin")
-    amps = re.search(r"c_amps\[\d+\] = \{(.*?)\n\};", src, re.S).group(1)
-    kinds_nterm = [(int(m[0]), int(m[1])) for m in re.findall(r"\}, (\d+), \d+, \d+, (\d+)\}", amps)]
-    assert len(kinds_nterm) == len(I.amp_order) and len(terms) == len(sterms)
+    terms, words = array("c_terms"), array("c_bmat")
+    assert len(words) == 1024 * len(I.stages)
+    halves = np.array([(w >> sh) & 0xFFFF for w in words for sh in (0, 16)], dtype=np.uint32)
+    values = ((halves << 16).astype(np.uint32)).view(np.float32).astype(float)   # BF16 -> float
+    assert set(np.unique(values)) <= {-1.0, 0.0, 1.0}
     rng = np.random.default_rng(9)
     J1 = np.zeros(120, complex)
-    J2 = np.zeros(120, complex)
-    slots = np.full(ACC_SLOTS, np.nan + 0j)
-    t = win = 0
-    for kind, nterm in kinds_nterm:
-        G = complex(*rng.normal(size=2))
-        for _ in range(nterm):
-            ct, st = terms[t], sterms[t]
-            x = (-1j if ct & 0x8000 else 1j) * G
-            J1[ct & 0x7FFF] += x
-            assert (st & 0x8000) == (ct & 0x8000) and (st & 0x1F) < ACC_SLOTS
-            assert wflow[wbegin[win] + (st & 0x1F)] == ct & 0x7FFF
-            slots[st & 0x1F] = x if st & 0x4000 else slots[st & 0x1F] + x
-            t += 1
-        if kind & 0x40:
-            n = wbegin[win + 1] - wbegin[win]
-            assert len(set(wflow[wbegin[win]:wbegin[win + 1]])) == n <= ACC_SLOTS
-            for k in range(n):
-                assert not np.isnan(slots[k])
-                J2[wflow[wbegin[win] + k]] += slots[k]
-            slots[:] = np.nan
-            win += 1
-    assert win == len(wbegin) - 1 and t == len(terms)
-    assert np.abs(J1 - J2).max() < 1e-12 * np.abs(J1).max()
-
+    Jre, Jim = np.zeros(128), np.zeros(128)
+    t = 0
+    for si, st in enumerate(I.stages):
+        img = values[2048 * si:2048 * (si + 1)]
+        B = np.array([[img[umma_k16_offset(n, k) // 2] for k in range(16)] for n in range(128)])
+        Gs = np.zeros(16, complex)
+        k = 0
+        for ai in st.amps:
+            if ai not in I.flush:
+                continue
+            G = complex(*rng.normal(size=2))
+            for col, c in I.flush[ai]:
+                assert terms[t] == col | (0x8000 if c == (0, -1) else 0)
+                J1[col] += (-1j if terms[t] & 0x8000 else 1j) * G
+                t += 1
+            Gs[k] = G
+            k += 1
+        assert k <= 16
+        Jre += B @ Gs.imag
+        Jim += -(B @ Gs.real)
+    assert t == len(terms)
+    assert np.all(Jre[120:] == 0) and np.all(Jim[120:] == 0)
+    assert np.abs(J1 - (Jre[:120] + 1j * Jim[:120])).max() < 1e-12 * np.abs(J1).max()
 
 
 @pytest.mark.parametrize("process", ["ee_mumu", "gg_ttx", "gg_ttxg", "gg_ttxgg", "gg_ttxggg"])
