@@ -235,11 +235,18 @@ __global__ void __launch_bounds__(P::NT) me_kernel_interp(LaunchArgs a, cx<T>* _
         T snum = T(0), sden = T(0);
         cx<T> G = {T(0), T(0)};  // open colour group: sum of its amplitudes with their signs
         bool nonfinite = false;   // a group sum was not finite (it enters J as 0; |M|^2 = NaN)
+        // table rounds start at the warp after the previous round's last task, so
+        // that the many small rounds spread over all warps instead of piling onto the
+        // first ones (a warp still runs the tasks of one round only)
+        static_assert((NT & (NT - 1)) == 0 && NT % 32 == 0, "round rotation assumes a power-of-two CTA of whole warps");
+        int rot = 0;
         for (int s = 0; s < P::NSTAGE; ++s) {
             const IStage st = P::stage(s);
             for (int r = st.round_begin; r < st.round_end; ++r) {
                 const IRound rd = P::round(r);
-                for (int t = tid; t < rd.ntask; t += NT) run_task<T, P::TAB>(tab, sln, mt, rd.kind, ld_task(P::tasks() + rd.task_begin + t));
+                for (int t = (tid - rot) & (NT - 1); t < rd.ntask; t += NT)
+                    run_task<T, P::TAB>(tab, sln, mt, rd.kind, ld_task(P::tasks() + rd.task_begin + t));
+                rot = (rot + ((rd.ntask + 31) & ~31)) & (NT - 1);
                 if (rd.barrier_after) __syncthreads();
             }
             __syncthreads();
