@@ -262,18 +262,30 @@ __global__ void __launch_bounds__(P::NT) me_kernel_interp(LaunchArgs a, cx<T>* _
                 cp_async16(bsm + tid + NT, bsrc + tid + NT);
                 cp_async_commit();
             }
+            // software pipeline: the descriptor and the first three operands of the
+            // next amplitude are loaded while the current one is evaluated (a third
+            // operand index of a two-operand kind is 0 with support 0: an external
+            // wavefunction entry, read and not used)
+            IAmp dn;
+            Wf<T> p0, p1, p2;
+            auto fetch = [&](int ai) {
+                dn = P::amp(ai);
+                p0 = tab.ld(dn.op[0] + vsup[dn.sup[0] * NT + tid]);
+                p1 = tab.ld(dn.op[1] + vsup[dn.sup[1] * NT + tid]);
+                p2 = tab.ld(dn.op[2] + vsup[dn.sup[2] * NT + tid]);
+            };
+            if (st.amp_begin < st.amp_end) fetch(st.amp_begin);
             for (int ai = st.amp_begin; ai < st.amp_end; ++ai) {
-                const IAmp d = P::amp(ai);
+                const IAmp d = dn;
+                const Wf<T> w0 = p0, w1 = p1, w2 = p2;
+                if (ai + 1 < st.amp_end) fetch(ai + 1);
                 const int kind = d.kind & 0x3f;
-                const Wf<T> w0 = tab.ld(d.op[0] + vsup[d.sup[0] * NT + tid]);
-                const Wf<T> w1 = tab.ld(d.op[1] + vsup[d.sup[1] * NT + tid]);
                 cx<T> x;
                 if (kind == A_DOTV) {           // amputated: two-operand contractions
                     x = DOTV<T>(w0, w1);
                 } else if (kind == A_DOTF) {
                     x = DOTF<T>(w0, w1);
                 } else {
-                    const Wf<T> w2 = tab.ld(d.op[2] + vsup[d.sup[2] * NT + tid]);
                     switch (kind) {
                     case A_FFV1_0: x = FFV1_0<T>(w0, w1, w2); break;
                     case A_VVV1_0: x = VVV1_0<T>(w0, sln[d.la].p, w1, sln[d.lb].p, w2); break;
