@@ -306,17 +306,17 @@ def rambo_sample(seed, ev0, nevt, sqrt_s, masses, cuts=None, momenta_out=None, w
 
 def workload_handle(name: str, precision="mixed") -> Handle:
     """Handle for one of the named workloads (see workloads.py)."""
-    from .workloads import PARTICLES, WORKLOADS, MT
+    from .workloads import PARTICLES, MT, workload
 
-    w = WORKLOADS[name]
+    w = workload(name)
     masses = [MT if p in ("t", "t~") else 0.0 for p in PARTICLES[w.process]]
     return me_init(w.process, masses, [w.alpha], precision)
 
 
 def cuts_for(name: str):
-    from .workloads import DR_MIN, PT_MIN, WORKLOADS
+    from .workloads import DR_MIN, PT_MIN, workload
 
-    w = WORKLOADS[name]
+    w = workload(name)
     mask = 0
     for j, c in enumerate(w.cut_mask):
         if c:

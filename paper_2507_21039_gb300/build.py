@@ -32,7 +32,8 @@ NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-r
 STATIC_SOURCES = ["me_abi.cu", "rambo.cu", "serve.cu"]
 # processes compiled into the library (build option ME_BUILD_PROCESSES: a
 # comma-separated subset, for quicker builds of kernel variants)
-ALL_PROCESSES = ("ee_mumu", "gg_ttx", "gg_ttxg", "gg_ttxgg", "gg_ttxggg")
+ALL_PROCESSES = ("ee_mumu", "gg_ttx", "gg_ttxg", "gg_ttxgg", "gg_ttxggg", "uux_epem", "uux_epemg", "uux_epemgg",
+                 "uux_epemggg")
 PROCESSES = tuple(p for p in os.environ.get("ME_BUILD_PROCESSES", ",".join(ALL_PROCESSES)).split(",")
                   if p in ALL_PROCESSES) or ALL_PROCESSES
 

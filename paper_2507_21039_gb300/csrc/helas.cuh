@@ -225,6 +225,101 @@ __device__ __forceinline__ void FFV1_1(const Wf<T>& V, const Wf<T>& Fi, const Ln
 }
 
 // ---------------------------------------------------------------------------
+// Chiral vertices of the Drell-Yan quark line (the colourless photon/Z
+// insertion; reading R15).  Upper spinor components are left-handed, so in
+// gamma.V = [[0, V.s], [V.sb, 0]] the V.s block meets right-handed and the
+// V.sb block left-handed components.  The insertion slash(LL) P_L + slash(LR)
+// P_R = [[0, LR.s], [LL.sb, 0]]: the FFV1 routines with the s block taken from
+// LR and the sb block from LL.
+// ---------------------------------------------------------------------------
+// FFVLR_0: Fo (slash(LL) P_L + slash(LR) P_R) Fi
+template <class T>
+__device__ __forceinline__ cx<T> FFVLR_0(const Wf<T>& Fo, const Wf<T>& LL, const Wf<T>& LR, const Wf<T>& Fi)
+{
+    const Blk<T> r = sblk(LR), l = sblk(LL);
+    cx<T> t0 = cfma(r.s01, Fi.c[3], r.s00 * Fi.c[2]);
+    cx<T> t1 = cfma(r.s11, Fi.c[3], r.s10 * Fi.c[2]);
+    cx<T> t2 = l.s11 * Fi.c[0] - l.s01 * Fi.c[1];
+    cx<T> t3 = l.s00 * Fi.c[1] - l.s10 * Fi.c[0];
+    cx<T> a = Fo.c[0] * t0;
+    a = cfma(Fo.c[1], t1, a);
+    a = cfma(Fo.c[2], t2, a);
+    a = cfma(Fo.c[3], t3, a);
+    return a;
+}
+
+// FFVLR_2: Fo' = inv * Fo (slash(LL) P_L + slash(LR) P_R) qslash   (massless quark)
+template <class T>
+__device__ __forceinline__ void FFVLR_2(const Wf<T>& Fo, const Wf<T>& LL, const Wf<T>& LR, const Ln<T>& q, Wf<T>& out)
+{
+    const Blk<T> r = sblk(LR), l = sblk(LL);
+    // X_L = (o2,o3) LL.sb, X_R = (o0,o1) LR.s
+    cx<T> xl0 = Fo.c[2] * l.s11 - Fo.c[3] * l.s10;
+    cx<T> xl1 = Fo.c[3] * l.s00 - Fo.c[2] * l.s01;
+    cx<T> xr0 = cfma(Fo.c[1], r.s10, Fo.c[0] * r.s00);
+    cx<T> xr1 = cfma(Fo.c[1], r.s11, Fo.c[0] * r.s01);
+    // Y_L = X_R (q.sb), Y_R = X_L (q.s)
+    const T q0 = q.p[0], q1 = q.p[1], q2 = q.p[2], q3 = q.p[3], inv = q.inv;
+    cx<T> yl0 = rfma(q0 + q3, xr0, xr1 * cx<T>{q1, q2});
+    cx<T> yl1 = rfma(q0 - q3, xr1, xr0 * cx<T>{q1, -q2});
+    cx<T> yr0 = rfma(q0 - q3, xl0, xl1 * cx<T>{-q1, -q2});
+    cx<T> yr1 = rfma(q0 + q3, xl1, xl0 * cx<T>{-q1, q2});
+    out.c[0] = inv * yl0;
+    out.c[1] = inv * yl1;
+    out.c[2] = inv * yr0;
+    out.c[3] = inv * yr1;
+}
+
+// FFVLR_1: Fi' = inv * qslash (slash(LL) P_L + slash(LR) P_R) Fi   (massless quark)
+template <class T>
+__device__ __forceinline__ void FFVLR_1(const Wf<T>& LL, const Wf<T>& LR, const Wf<T>& Fi, const Ln<T>& q, Wf<T>& out)
+{
+    const Blk<T> r = sblk(LR), l = sblk(LL);
+    // X upper = LR.s (i2,i3), lower = LL.sb (i0,i1)
+    cx<T> xl0 = cfma(r.s01, Fi.c[3], r.s00 * Fi.c[2]);
+    cx<T> xl1 = cfma(r.s11, Fi.c[3], r.s10 * Fi.c[2]);
+    cx<T> xr0 = l.s11 * Fi.c[0] - l.s01 * Fi.c[1];
+    cx<T> xr1 = l.s00 * Fi.c[1] - l.s10 * Fi.c[0];
+    const T q0 = q.p[0], q1 = q.p[1], q2 = q.p[2], q3 = q.p[3], inv = q.inv;
+    cx<T> yl0 = rfma(q0 - q3, xr0, cx<T>{-q1, q2} * xr1);
+    cx<T> yl1 = rfma(q0 + q3, xr1, cx<T>{-q1, -q2} * xr0);
+    cx<T> yr0 = rfma(q0 + q3, xl0, cx<T>{q1, -q2} * xl1);
+    cx<T> yr1 = rfma(q0 - q3, xl1, cx<T>{q1, q2} * xl0);
+    out.c[0] = inv * yl0;
+    out.c[1] = inv * yl1;
+    out.c[2] = inv * yr0;
+    out.c[3] = inv * yr1;
+}
+
+// Lepton-pair objects of the insertion: with S = Fo gamma P_R Fi and
+// Sb = Fo gamma P_L Fi (Fo = ubar(e-), Fi = v(e+), upper index),
+//   LL = c.c[0] Sb + c.c[1] S,   LR = c.c[2] Sb + c.c[3] S,
+// c the event's electroweak coefficients (sums over photon and Z of quark
+// coupling x lepton coupling / propagator denominator; see ew_coefficients).
+template <class T>
+__device__ __forceinline__ void LEPLR(const Wf<T>& Fo, const Wf<T>& Fi, const Wf<T>& c, Wf<T>& LL, Wf<T>& LR)
+{
+    const cx<T>*o = Fo.c, *i = Fi.c;
+    const cx<T> a = o[0] * i[2], b = o[1] * i[3], e = o[0] * i[3], f = o[1] * i[2];   // right-handed
+    const cx<T> cc = o[2] * i[0], d = o[3] * i[1], g = o[2] * i[1], h = o[3] * i[0]; // left-handed
+    const cx<T> fe = f - e, gh = g - h;
+    Wf<T> S, Sb;
+    S.c[0] = a + b;
+    S.c[1] = e + f;
+    S.c[2] = {-fe.im, fe.re};    // i (f - e)
+    S.c[3] = a - b;
+    Sb.c[0] = cc + d;
+    Sb.c[1] = {-(g.re + h.re), -(g.im + h.im)};
+    Sb.c[2] = {-gh.im, gh.re};   // i (g - h)
+    Sb.c[3] = d - cc;
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+        LL.c[m] = cfma(c.c[0], Sb.c[m], c.c[1] * S.c[m]);
+        LR.c[m] = cfma(c.c[2], Sb.c[m], c.c[3] * S.c[m]);
+    }
+}
+
+// ---------------------------------------------------------------------------
 // amputated vertices (no propagator) and two-operand contractions.  A final
 // vertex with one operand's index left open; contracting it with that operand
 // gives the amplitude of the direct vertex routine (same products, grouped

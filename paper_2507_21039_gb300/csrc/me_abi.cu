@@ -287,7 +287,8 @@ int me_init(me_handle** hp, const char* process, const double* masses, int nmass
     const ProcDesc* pd = me::find_process(process);
     if (!pd) return ME_EINVAL;
     if (precision < ME_PREC_FP64 || precision > ME_PREC_MIXED64) return ME_EINVAL;
-    const bool qcd = pd->ngluon > 0;
+    const bool qcd = pd->family == 1;      // g g -> t t~ + n g: massive tops
+    const bool strong = pd->family != 0;   // couplings {alpha_s} (Drell-Yan: electroweak part fixed)
     double mt = qcd ? 173.0 : 0.0;
     if (nmass != 0 || masses) {
         if (!masses || nmass != pd->npar) return ME_EINVAL;
@@ -303,7 +304,7 @@ int me_init(me_handle** hp, const char* process, const double* masses, int nmass
                 if (masses[i] != 0.0) return ME_EINVAL;
         }
     }
-    double alpha = qcd ? 0.118 : 1.0 / 132.5;
+    double alpha = strong ? 0.118 : 1.0 / 132.5;
     if (ncoup != 0 || couplings) {
         if (!couplings || ncoup != 1 || !(couplings[0] > 0.0) || !std::isfinite(couplings[0])) return ME_EINVAL;
         alpha = couplings[0];
@@ -367,7 +368,8 @@ int me_set_option(me_handle* h, int option, int value)
     case ME_OPT_GAUGE_CHECK:
         if (value < -1 || value >= h->proc->npar) return ME_EINVAL;
         if (value >= 0 && h->proc->ngluon == 0) return ME_EINVAL;
-        if (value >= 0 && (value == 2 || value == 3)) return ME_EINVAL;  // not a gluon
+        // not a gluon: t, t~ (2, 3) of g g -> t t~ + n g; u, u~, e+, e- (0..3) of Drell-Yan
+        if (value >= 0 && (value == 2 || value == 3 || (h->proc->family == 2 && value < 4))) return ME_EINVAL;
         h->gauge_ext = value;
         return ME_OK;
     default: return ME_EINVAL;
@@ -543,6 +545,7 @@ int me_sigmakin_sde(me_handle* h, const double* momenta, int64_t nevt, int chann
                     void* cuda_stream)
 {
     if (!h || nevt < 0 || channel < 0 || channel >= h->proc->ndiag) return ME_EINVAL;
+    if (h->proc->family == 2) return ME_EINVAL;  // Drell-Yan: no channel weights (diagrams without line sets)
     if (nevt == 0) return ME_OK;
     if (!momenta || !me2 || !weight || !is_device_ptr(momenta) || !is_device_ptr(me2) || !is_device_ptr(weight))
         return ME_EINVAL;
@@ -609,7 +612,7 @@ int me_hsample_probabilities(const me_handle* h, double* p, int cap, int* n)
 
 int me_diagram_lines(const me_handle* h, int diagram, int* masks, int cap, int* n)
 {
-    if (!h || !n || diagram < 0 || diagram >= h->proc->ndiag) return ME_EINVAL;
+    if (!h || !n || diagram < 0 || diagram >= h->proc->ndiag || h->proc->family == 2) return ME_EINVAL;
     const int nl = h->proc->diag_nlines[diagram];
     *n = nl;
     if (masks) {

@@ -31,7 +31,7 @@ enum LineKind : unsigned char { L_EXT = 0, L_MASSLESS = 1, L_MASSIVE = 2 };
 // shared-memory bytes for E events of process P at precision T (+ J storage)
 template <class P, class T> __host__ __device__ constexpr size_t setup_bytes(int E)
 {
-    return (size_t)E * P::NPAR * 4 * sizeof(double) + (size_t)E * P::NPAR * 2 * sizeof(Wf<T>) +
+    return (size_t)E * P::NPAR * 4 * sizeof(double) + (size_t)E * P::NEXT * sizeof(Wf<T>) +
            (size_t)E * P::NLINES * sizeof(Ln<T>);
 }
 
@@ -261,12 +261,57 @@ __device__ __forceinline__ FSum fsum_warp(FSum v)
     return v;
 }
 
+// Drell-Yan electroweak parameters (reading R15: G_F-scheme values, fixed
+// widths; couplings -i gamma^mu (gL P_L + gR P_R), photon gL = gR = e Q, Z
+// gL = e (T3 - Q sw^2) / (sw cw), gR = -e Q sw^2 / (sw cw))
+constexpr double kDyAlpha = 1.0 / 132.507, kDyMZ = 91.188, kDyWZ = 2.441404, kDyMW = 80.419002;
+
+// The four electroweak coefficients of the Drell-Yan insertion for the event's
+// lepton pair (particles 2 = e+, 3 = e-), in FP64 and rounded to T:
+//   c[0] = sum_V gL^u gL^e / D_V,  c[1] = sum_V gL^u gR^e / D_V,
+//   c[2] = sum_V gR^u gL^e / D_V,  c[3] = sum_V gR^u gR^e / D_V,
+// D_photon = s, D_Z = s - M_Z^2 + i M_Z Gamma_Z, s = (p_e+ + p_e-)^2
+template <class T> __device__ __forceinline__ Wf<T> ew_coefficients(const double* __restrict__ p)
+{
+    double q[4];
+#pragma unroll
+    for (int mu = 0; mu < 4; ++mu) q[mu] = p[8 + mu] + p[12 + mu];
+    const double s = q[0] * q[0] - q[1] * q[1] - q[2] * q[2] - q[3] * q[3];
+    const double e = sqrt(4.0 * M_PI * kDyAlpha);
+    const double cw = kDyMW / kDyMZ, sw = sqrt(1.0 - cw * cw), swcw = sw * cw;
+    // couplings [boson][L/R]: u quark (Q = 2/3, T3 = 1/2) and electron (Q = -1, T3 = -1/2)
+    const double gu[2][2] = {{e * 2.0 / 3.0, e * 2.0 / 3.0},
+                             {e * (0.5 - 2.0 / 3.0 * sw * sw) / swcw, -e * 2.0 / 3.0 * sw * sw / swcw}};
+    const double ge[2][2] = {{-e, -e}, {e * (-0.5 + sw * sw) / swcw, e * sw * sw / swcw}};
+    // 1 / D_V: photon 1/s; Z 1/(a + i b) = (a - i b) / (a^2 + b^2)
+    const double za = s - kDyMZ * kDyMZ, zb = kDyMZ * kDyWZ, zn = 1.0 / (za * za + zb * zb);
+    const double inv_re[2] = {1.0 / s, za * zn}, inv_im[2] = {0.0, -zb * zn};
+    Wf<T> c;
+#pragma unroll
+    for (int x = 0; x < 4; ++x) {
+        const int cu = x >> 1, ce = x & 1;  // quark chirality (L, R), lepton chirality (L, R)
+        double re = 0.0, im = 0.0;
+#pragma unroll
+        for (int v = 0; v < 2; ++v) {
+            const double g = gu[v][cu] * ge[v][ce];
+            re += g * inv_re[v];
+            im += g * inv_im[v];
+        }
+        c.c[x] = {(T)re, (T)im};
+    }
+    return c;
+}
+
+// Setup item of the straight-line kernel: external wavefunctions (2 NPAR),
+// then, for a process with the Drell-Yan insertion, its electroweak
+// coefficients (one table entry), then the lines
 template <class P, class T>
 __device__ __forceinline__ void event_setup(const double* __restrict__ p, int item, double mt, int gauge_ext,
                                             Wf<T>* __restrict__ ext, Ln<T>* __restrict__ ln)
 {
     if (item < 2 * P::NPAR) ext[item] = ext_wavefunction<P, T>(p, item, mt, gauge_ext);
-    else ln[item - 2 * P::NPAR] = line_data<P, T>(p, item - 2 * P::NPAR, mt);
+    else if (item < P::NEXT) ext[item] = ew_coefficients<T>(p);
+    else ln[item - P::NEXT] = line_data<P, T>(p, item - P::NEXT, mt);
 }
 
 // Colour form J^+ N J in precision C of a colour-flow vector J held in
@@ -300,7 +345,7 @@ __global__ void __launch_bounds__(P::THREADS) me_kernel_scalar(LaunchArgs a)
 
     double* smom = reinterpret_cast<double*>(smem);
     Wf<T>* sext = reinterpret_cast<Wf<T>*>(smom + E * NPAR * 4);
-    Ln<T>* sln = reinterpret_cast<Ln<T>*>(sext + E * NPAR * 2);
+    Ln<T>* sln = reinterpret_cast<Ln<T>*>(sext + E * P::NEXT);
 
     // (a1) coalesced load of this CTA's momenta
     const double* g = a.mom + e0 * NPAR * 4;
@@ -314,10 +359,10 @@ __global__ void __launch_bounds__(P::THREADS) me_kernel_scalar(LaunchArgs a)
     __syncthreads();
 
     // (a2, a3 denominators) helicity-independent per-event data, FP64
-    constexpr int PER = 2 * NPAR + NL;
+    constexpr int PER = P::NEXT + NL;
     for (int it = threadIdx.x; it < ne * PER; it += TH) {
         const int ev = it / PER, j = it - ev * PER;
-        event_setup<P, T>(smom + ev * NPAR * 4, j, a.mt, a.gauge_ext, sext + ev * NPAR * 2, sln + ev * NL);
+        event_setup<P, T>(smom + ev * NPAR * 4, j, a.mt, a.gauge_ext, sext + ev * P::NEXT, sln + ev * NL);
     }
     __syncthreads();
 
@@ -325,7 +370,7 @@ __global__ void __launch_bounds__(P::THREADS) me_kernel_scalar(LaunchArgs a)
     const int ev = threadIdx.x / S, slot = threadIdx.x - ev * S;
     double acc = 0.0, snum = 0.0, sden = 0.0;
     if (ev < ne) {
-        const Wf<T>* ext = sext + ev * NPAR * 2;
+        const Wf<T>* ext = sext + ev * P::NEXT;
         const Ln<T>* ln = sln + ev * NL;
         for (int i = slot; i < a.nlist; i += S) {
             // helicity sampling: one helicity per event (external states of

@@ -46,6 +46,7 @@ struct ProcDesc {
     size_t (*jscratch_per_cta)(int precision);
     // resident CTAs of such a launch on the current device (its scratch is this x jscratch_per_cta)
     int (*jscratch_ctas)(int precision);
+    int family;                // 0: e+e- -> mu+mu-, 1: g g -> t t~ + n g, 2: u u~ -> e+ e- + n g
 };
 
 const ProcDesc* find_process(const char* name);

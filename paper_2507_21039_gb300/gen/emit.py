@@ -12,7 +12,7 @@ import math
 import struct
 
 from .colour import colour_matrix
-from .plan import FLOPS, Plan, build_plan, colour_groups
+from .plan import FLOPS, Plan, build_plan, build_plan_dy, colour_groups
 from .interp import AMP_KINDS, ROUTINES, build_interp
 from .tabplan import build_tabplan
 
@@ -57,10 +57,19 @@ def _apply_kernel_overrides():
 _apply_kernel_overrides()
 
 
+# Drell-Yan processes u ubar -> e+ e- + n g (the paper's second standalone
+# workload, Sec. 4; photon and Z exchange, reading R15): name -> gluon count
+DY_PROCESSES = {"uux_epem": 0, "uux_epemg": 1, "uux_epemgg": 2, "uux_epemggg": 3}
+
+
 def _ext_table(process: str):
     if process == "ee_mumu":
         # e-(in) u, e+(in) vbar, mu-(out) ubar, mu+(out) v; massless
         return ["FI_U", "FO_V", "FO_U", "FI_V"], [0, 0, 0, 0]
+    if process in DY_PROCESSES:
+        # u(in) u, ubar(in) vbar, e+(out) v, e-(out) ubar, gluons(out) eps*; massless
+        n = DY_PROCESSES[process]
+        return ["FI_U", "FO_V", "FI_V", "FO_U"] + ["VOUT"] * n, [0] * (4 + n)
     npar = {"gg_ttx": 4, "gg_ttxg": 5, "gg_ttxgg": 6, "gg_ttxggg": 7}[process]
     kinds = ["VIN", "VIN", "FO_U", "FI_V"] + ["VOUT"] * (npar - 4)
     massive = [0, 0, 1, 1] + [0] * (npar - 4)
@@ -82,6 +91,14 @@ def _line_tables(P: Plan):
                 else:
                     pm |= 1 << e
             kind.append(0 if len(ln.gluons) == 1 else 1)
+        elif P.process.startswith("dy_"):  # Drell-Yan quark line ("q", "qe"): -p_ubar + P_S (+ p_e+ + p_e-), massless
+            assert ln.kind in ("q", "qe"), ln.kind
+            mm |= 1 << 1
+            if ln.kind == "qe":
+                pm |= 0b1100
+            for g in ln.gluons:
+                pm |= 1 << P.gluon_ext[g]
+            kind.append(1)
         else:  # top propagator: p_t + P_S
             pm |= 1 << 2
             for g in ln.gluons:
@@ -181,7 +198,8 @@ def _coef_call(col, c, var):
 
 
 def emit_process(process: str) -> tuple[str, dict]:
-    P = build_plan(process)
+    dy = process in DY_PROCESSES
+    P = build_plan_dy(DY_PROCESSES[process]) if dy else build_plan(process)
     npar = P.npar
     ncol = P.ncol
     k = len(P.gluon_ext)
@@ -191,6 +209,10 @@ def emit_process(process: str) -> tuple[str, dict]:
     if process == "ee_mumu":
         num, den = [[1]], 1
         iden, cpow = 4.0, 2
+    elif dy:  # quark line with k gluons: the same string basis (delta_ij for k = 0);
+        # spin x colour average 4 x 9, k! identical gluons; electroweak couplings fixed
+        num, den = colour_matrix(k) if k else ([[3]], 1)
+        iden, cpow = 4.0 * 9.0 * math.factorial(k), k
     else:
         num, den = colour_matrix(k)
         iden, cpow = 4.0 * 64.0 * math.factorial(k - 2), k
@@ -203,7 +225,13 @@ def emit_process(process: str) -> tuple[str, dict]:
     for i, op in enumerate(P.ops):
         a = [f"w{x}" for x in op.args]
         kd = op.kind
-        if kd.startswith("ext_"):
+        if kd == "ext_lepL":  # Drell-Yan: both insertion objects from ubar(e-), v(e+) and the coefficients
+            iR = next(j for j, o in enumerate(P.ops) if o.kind == "ext_lepR")
+            body.append(f"Wf<T> w{i}, w{iR}; LEPLR<T>(ext[6 + ((hel >> {npar - 4}) & 1)], "
+                        f"ext[4 + ((hel >> {npar - 3}) & 1)], ext[{2 * npar}], w{i}, w{iR});")
+        elif kd == "ext_lepR":
+            pass
+        elif kd.startswith("ext_"):
             e = op.ext
             body.append(f"const Wf<T>& w{i} = ext[{2 * e} + ((hel >> {npar - 1 - e}) & 1)];")
         elif kd == "VVV1P0_1":
@@ -213,6 +241,10 @@ def emit_process(process: str) -> tuple[str, dict]:
             body.append(f"Wf<T> w{i}; {kd}<T>({a[0]}, {a[1]}, {a[2]}, ln[{op.line}].inv, w{i});")
         elif kd in ("FFV1_2", "FFV1_1"):
             body.append(f"Wf<T> w{i}; {kd}<T>({a[0]}, {a[1]}, ln[{op.line}], mt, w{i});")
+        elif kd == "FFVLR_2":
+            body.append(f"Wf<T> w{i}; FFVLR_2<T>({a[0]}, {a[1]}, {a[2]}, ln[{op.line}], w{i});")
+        elif kd == "FFVLR_1":
+            body.append(f"Wf<T> w{i}; FFVLR_1<T>({a[0]}, {a[1]}, {a[2]}, ln[{op.line}], w{i});")
         elif kd == "FFV1P0_3":
             body.append(f"Wf<T> w{i}; FFV1P0_3<T>({a[0]}, {a[1]}, ln[{op.line}].inv, w{i});")
         elif kd == "FFV1_0":
@@ -277,6 +309,9 @@ def emit_process(process: str) -> tuple[str, dict]:
         tc_members = (f"\n    static constexpr bool NSPLIT = {'true' if nsplit else 'false'};"
                       f"\n    __device__ static __forceinline__ const uint2* bfrag() {{ return c_bfrag; }}")
     ns = f"p_{process}"
+    family = 0 if process == "ee_mumu" else (2 if dy else 1)
+    # internal-line sets of the diagrams (QCD and e+e-); the Drell-Yan plans carry none
+    diag_lines = P.diag_lines if P.diag_lines else [()] * P.ndiagrams
     if IP:  # FP64 chains (FP64, paper-mixed, FP64 channel weights) keep J in global memory
         jscratch_body = ("    return (precision == PREC_FP64 || precision == PREC_MIXED64)\n"
                          "               ? interp_jscratch_per_cta<ProcInterpD, double>()\n"
@@ -301,17 +336,20 @@ namespace {ns} {{
 
 __constant__ unsigned char c_ext_kind[{npar}] = {{{", ".join(str(EXT_KINDS[x]) for x in kinds)}}};
 __constant__ unsigned char c_ext_massive[{npar}] = {{{", ".join(str(x) for x in massive)}}};
-__constant__ unsigned short c_line_plus[{nlines}] = {{{", ".join(str(x) for x in plus)}}};
-__constant__ unsigned short c_line_minus[{nlines}] = {{{", ".join(str(x) for x in minus)}}};
-__constant__ unsigned char c_line_kind[{nlines}] = {{{", ".join(str(x) for x in lkind)}}};
-__constant__ unsigned int c_line_side[{nlines}] = {{{", ".join(str(x) for x in sides)}}};
+__constant__ unsigned short c_line_plus[{max(nlines, 1)}] = {{{", ".join(str(x) for x in plus) or "0"}}};
+__constant__ unsigned short c_line_minus[{max(nlines, 1)}] = {{{", ".join(str(x) for x in minus) or "0"}}};
+__constant__ unsigned char c_line_kind[{max(nlines, 1)}] = {{{", ".join(str(x) for x in lkind) or "0"}}};
+__constant__ unsigned int c_line_side[{max(nlines, 1)}] = {{{", ".join(str(x) for x in sides) or "0"}}};
 static const int h_cnum[{ncol * ncol}] = {{{cnum_flat}}};
-static const int h_diag_lines[{4 * P.ndiagrams}] = {{{", ".join(str(x) for key in P.diag_lines for x in (list(key) + [0] * (4 - len(key))))}}};
-static const int h_diag_nlines[{P.ndiagrams}] = {{{", ".join(str(len(key)) for key in P.diag_lines)}}};
+static const int h_diag_lines[{4 * P.ndiagrams}] = {{{", ".join(str(x) for key in diag_lines for x in (list(key) + [0] * (4 - len(key))))}}};
+static const int h_diag_nlines[{P.ndiagrams}] = {{{", ".join(str(len(key)) for key in diag_lines)}}};
 {tc_array}
 struct Proc {{
     static constexpr int NPAR = {npar}, NCOL = {ncol}, NLINES = {nlines}, THREADS = {threads};
     static constexpr int CDEN = {den};
+    // Drell-Yan insertion: its electroweak coefficients follow the 2 NPAR external states
+    static constexpr bool EW = {"true" if dy else "false"};
+    static constexpr int NEXT = 2 * NPAR + (EW ? 1 : 0);
     // most terms of a line momentum written over its shorter side (line_side)
     static constexpr int SIDE = {max(side_max, 1)};
     static constexpr bool J_SMEM = {"true" if j_smem else "false"};
@@ -373,7 +411,7 @@ const ProcDesc* procdesc_{process}()
     static const ProcDesc d = {{"{process}", {npar}, {1 << npar}, {ncol}, {P.ndiagrams}, {len(P.amps)}, {k}, {nlines},
                                {threads}, {iden!r}, {den}, {ns}::h_cnum, {flops_hel}LL,
                                {P.colour_flops_per_helicity()}LL, {cpow}, &{ns}::launch, {ns}::h_diag_lines,
-                               {ns}::h_diag_nlines, &{ns}::jscratch_per_cta, &{ns}::jscratch_ctas}};
+                               {ns}::h_diag_nlines, &{ns}::jscratch_per_cta, &{ns}::jscratch_ctas, {family}}};
     return &d;
 }}
 
@@ -812,7 +850,7 @@ struct {name} : Proc {{
     return src, I
 
 
-PROCESSES = ("ee_mumu", "gg_ttx", "gg_ttxg", "gg_ttxgg", "gg_ttxggg")
+PROCESSES = ("ee_mumu", "gg_ttx", "gg_ttxg", "gg_ttxgg", "gg_ttxggg") + tuple(DY_PROCESSES)
 
 
 def emit_registry(processes=PROCESSES) -> str:

@@ -44,6 +44,9 @@ FLOPS = {
     "VVV1A_1": 116, "VVV1A_2": 116, "VVV1A_3": 116,
     "VVVV1A": 78, "VVVV3A": 78, "VVVV4A": 78,
     "DOTV": 30, "DOTF": 30,
+    # Drell-Yan insertion (massless quark line): the FFV1 routines with a second
+    # 2x2 block and no mass terms; the lepton-pair objects of both chiralities
+    "FFVLR_0": 80, "FFVLR_2": 116, "FFVLR_1": 116, "ext_lepL": 176,
 }
 V4NAMES = ("VVVV1", "VVVV3", "VVVV4")
 

@@ -23,6 +23,10 @@ PARTICLES = {
     "gg_ttxg": ("g", "g", "t", "t~", "g"),
     "gg_ttxgg": ("g", "g", "t", "t~", "g", "g"),
     "gg_ttxggg": ("g", "g", "t", "t~", "g", "g", "g"),
+    "uux_epem": ("u", "u~", "e+", "e-"),
+    "uux_epemg": ("u", "u~", "e+", "e-", "g"),
+    "uux_epemgg": ("u", "u~", "e+", "e-", "g", "g"),
+    "uux_epemggg": ("u", "u~", "e+", "e-", "g", "g", "g"),
 }
 
 
@@ -72,6 +76,22 @@ WORKLOADS = {
                    "headline workload"),
     "gg_ttxggg": _w("gg_ttxggg", "gg_ttxggg", 2000.0, 5, 1 << 18, True, ("fp64", "mixed")),
 }
+
+#: the paper's second standalone workload, u u~ -> e+ e- + n g (photon and Z;
+#: electroweak parameters fixed as in the library's reading of the paper): a
+#: synthetic stand-in at sqrt(s) = 500 GeV with the gluon cuts above
+DY_WORKLOADS = {
+    "uux_epem": _w("uux_epem", "uux_epem", 500.0, 11, 1 << 20, False, ("fp64", "fp32", "mixed")),
+    "uux_epemg": _w("uux_epemg", "uux_epemg", 500.0, 12, 1 << 20, True, ("fp64", "fp32", "mixed")),
+    "uux_epemgg": _w("uux_epemgg", "uux_epemgg", 500.0, 13, 1 << 20, True, ("fp64", "fp32", "mixed")),
+    "uux_epemggg": _w("uux_epemggg", "uux_epemggg", 500.0, 14, 1 << 18, True, ("fp64", "fp32", "mixed")),
+}
+
+
+def workload(name: str) -> Workload:
+    """A benchmark workload or a Drell-Yan workload by name."""
+    return WORKLOADS[name] if name in WORKLOADS else DY_WORKLOADS[name]
+
 
 #: serving mix: process weights, log-uniform batch sizes, per-request seeds
 SERVING_MIX = {

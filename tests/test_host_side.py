@@ -268,7 +268,8 @@ def test_stage_sign_matrices_replay_the_flow_updates():
     assert np.abs(J1 - (Jre[:120] + 1j * Jim[:120])).max() < 1e-12 * np.abs(J1).max()
 
 
-@pytest.mark.parametrize("process", ["ee_mumu", "gg_ttx", "gg_ttxg", "gg_ttxgg", "gg_ttxggg"])
+@pytest.mark.parametrize("process", ["ee_mumu", "gg_ttx", "gg_ttxg", "gg_ttxgg", "gg_ttxggg", "uux_epemg",
+                                     "uux_epemgg", "uux_epemggg"])
 def test_line_sides_and_gram_denominators(orc, process):
     """The FP32 kernels' per-event setup: each line's momentum written over its
     shorter side (the generator's packed table) equals the line's defining sum
@@ -278,13 +279,23 @@ def test_line_sides_and_gram_denominators(orc, process):
     momentum sum minus m^2 within FP64 rounding of the largest term."""
     from paper_2507_21039_gb300.gen import emit
 
-    P = build_plan(process)
+    from paper_2507_21039_gb300.gen.plan import build_plan_dy
+    from paper_2507_21039_gb300.workloads import workload
+
+    dy = process in emit.DY_PROCESSES
+    P = build_plan_dy(emit.DY_PROCESSES[process]) if dy else build_plan(process)
     plus, minus, kind = emit._line_tables(P)
     sides, kmax = emit._line_sides(plus, minus, P.npar)
     assert kmax <= 3
-    w = WORKLOADS[process]
+    w = workload(process)
     mom, _, _ = orc.rambo(w.seed, w.sqrt_s, w.masses_final, 0, 64, w.cut_mask, 20.0, 0.4)
-    mt = 0.0 if process == "ee_mumu" else MT
+    mt = 0.0 if process == "ee_mumu" or dy else MT
+    if dy:  # the Drell-Yan quark line: -p_ubar + gluons (+ e+ + e- past the insertion)
+        for ln, pm, mm in zip(P.lines, plus, minus):
+            if ln.kind == "g":
+                continue
+            want_p = sum(1 << P.gluon_ext[g] for g in ln.gluons) | (0b1100 if ln.kind == "qe" else 0)
+            assert (pm, mm) == (want_p, 0b10)
     hi = mom.astype(np.float32)
     lo = (mom - hi.astype(np.float64)).astype(np.float32)
     assert np.all(np.abs(hi.astype(np.float64) + lo - mom) <= 2.0**-48 * np.abs(mom) + 1e-300)
