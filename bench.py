@@ -32,9 +32,24 @@ METRIC = "|M|^2 events/s gg->t tbar gg (mixed vs FP64, 1 GB300); serving p50/p99
 # dominant kernel of the mixed-precision step, per workload
 KERNELS = {"ee_mumu": "me_kernel_scalar<ee_mumu, float>", "gg_ttx": "me_kernel_scalar<gg_ttx, float>",
            "gg_ttxg": "me_kernel_tab<gg_ttxg, float>", "gg_ttxgg": "me_kernel_tab<gg_ttxgg, float>",
-           "gg_ttxggg": "me_kernel_interp<gg_ttxggg, float>"}
+           "gg_ttxggg": "me_kernel_interp<gg_ttxggg, float>",
+           "uux_epem": "me_kernel_scalar<uux_epem, float>", "uux_epemg": "me_kernel_scalar<uux_epemg, float>",
+           "uux_epemgg": "me_kernel_scalar<uux_epemgg, float>", "uux_epemggg": "me_kernel_scalar<uux_epemggg, float>"}
 PROCESS_LABEL = {"ee_mumu": "e+ e- -> mu+ mu-", "gg_ttx": "g g -> t t~", "gg_ttxg": "g g -> t t~ g",
-                 "gg_ttxgg": "g g -> t t~ g g", "gg_ttxggg": "g g -> t t~ g g g"}
+                 "gg_ttxgg": "g g -> t t~ g g", "gg_ttxggg": "g g -> t t~ g g g",
+                 "uux_epem": "u u~ -> e+ e-", "uux_epemg": "u u~ -> e+ e- g", "uux_epemgg": "u u~ -> e+ e- g g",
+                 "uux_epemggg": "u u~ -> e+ e- g g g"}
+DY_NGLUON = {"uux_epem": 0, "uux_epemg": 1, "uux_epemgg": 2, "uux_epemggg": 3}
+
+
+def oracle_me2(name, mom):
+    """The FP64 CPU oracle's |M|^2 for a workload (QCD / e+e- or Drell-Yan)."""
+    import oracle
+    from paper_2507_21039_gb300.workloads import ALPHA_S, MT, workload
+
+    if name in DY_NGLUON:
+        return oracle.dy_me2(DY_NGLUON[name], mom, alpha_s=ALPHA_S)
+    return oracle.me2(name, mom, mt=MT, alpha=workload(name).alpha)
 FP32_LANES_PER_SM = 128     # FP32 FMA lanes per SM (4 SMSPs x 32)
 
 
@@ -57,6 +72,10 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the gg -> t t~ ggg configuration added to the headline line")
+    ap.add_argument("--serving-requests", type=int, default=500,
+                    help="requests per load point of the serving sweep (the definition's 2000 take ~8 minutes)")
     ap.add_argument("--small", action="store_true",
                     help="the small processes (ee -> mu mu, gg -> t t~): HBM GB/s, launch overhead, FP-pipe fraction")
     ap.add_argument("--case", nargs=3, metavar=("WORKLOAD", "PRECISION", "NEVT"),
@@ -160,30 +179,34 @@ def measured_peaks():
 def cpu_baseline(name, seconds, rank):
     """The FP64 CPU oracle as it stands, on the host cores, on a bounded sample."""
     import oracle
-    from paper_2507_21039_gb300.workloads import DR_MIN, MT, PT_MIN, WORKLOADS
+    from paper_2507_21039_gb300.workloads import DR_MIN, PT_MIN, workload
 
-    w = WORKLOADS[name]
+    w = workload(name)
     mom, _, _ = oracle.rambo(w.seed, w.sqrt_s, w.masses_final, 0, 256, w.cut_mask, PT_MIN, DR_MIN)
     t = time.perf_counter()
-    oracle.me2(name, mom, mt=MT, alpha=w.alpha)
+    oracle_me2(name, mom)
     rate = 256 / (time.perf_counter() - t)
     n = int(max(256, min(1 << 17, rate * seconds)))
     mom, _, _ = oracle.rambo(w.seed, w.sqrt_s, w.masses_final, 0, n, w.cut_mask, PT_MIN, DR_MIN)
     t = time.perf_counter()
-    oracle.me2(name, mom, mt=MT, alpha=w.alpha)
+    oracle_me2(name, mom)
     dt = time.perf_counter() - t
     # one core, on a sample of about a sixth of the time
     cores = oracle.max_threads()
     n1 = int(max(64, min(n, (n / dt) / cores * seconds / 6)))
-    t = time.perf_counter()
-    oracle.me2(name, mom[:n1], mt=MT, alpha=w.alpha, nthreads=1)
-    dt1 = time.perf_counter() - t
-    return {"value": n / dt, "unit": "events/s", "cores": cores, "kind": "oracle",
-            "sample": f"first {n} events of the {name} workload (seed {w.seed}), FP64 Berends-Giele "
-                      f"colour-ordered recursion + brute-force colour matrix, all helicities, "
-                      f"OpenMP over events; {dt:.1f} s",
-            "single_core": {"value": n1 / dt1, "unit": "events/s", "cores": 1,
-                            "sample": f"first {n1} events, one thread; {dt1:.1f} s"}}
+    out = {"value": n / dt, "unit": "events/s", "cores": cores, "kind": "oracle",
+           "sample": f"first {n} events of the {name} workload (seed {w.seed}), FP64 Berends-Giele "
+                     f"colour-ordered recursion + brute-force colour matrix, all helicities, "
+                     f"OpenMP over events; {dt:.1f} s"}
+    if name not in DY_NGLUON:  # the oracle's Drell-Yan entry point has no thread limit
+        from paper_2507_21039_gb300.workloads import MT
+
+        t = time.perf_counter()
+        oracle.me2(name, mom[:n1], mt=MT, alpha=w.alpha, nthreads=1)
+        dt1 = time.perf_counter() - t
+        out["single_core"] = {"value": n1 / dt1, "unit": "events/s", "cores": 1,
+                              "sample": f"first {n1} events, one thread; {dt1:.1f} s"}
+    return out
 
 
 # ------------------------------------------------------------------ arms
@@ -191,25 +214,23 @@ def run_reference(args):
     world, rank, _ = dist_setup(want_cuda=False)
     if rank != 0:
         return
-    from paper_2507_21039_gb300.workloads import WORKLOADS
-
     import oracle
-    from paper_2507_21039_gb300.workloads import DR_MIN, MT, PT_MIN
+    from paper_2507_21039_gb300.workloads import DR_MIN, PT_MIN, workload
 
     name = args.workload
-    w = WORKLOADS[name]
+    w = workload(name)
     oracle.build()
     # size each step so that warmup + steps end within a few minutes
     mom, _, _ = oracle.rambo(w.seed, w.sqrt_s, w.masses_final, 0, 128, w.cut_mask, PT_MIN, DR_MIN)
     t = time.perf_counter()
-    oracle.me2(name, mom, mt=MT, alpha=w.alpha)
+    oracle_me2(name, mom)
     rate = 128 / (time.perf_counter() - t)
     per_step = max(64, int(rate * min(20.0, 150.0 / max(1, args.steps + args.warmup))))
     times = []
     for s in range(args.warmup + args.steps):
         mom, _, _ = oracle.rambo(w.seed, w.sqrt_s, w.masses_final, s * per_step, per_step, w.cut_mask, PT_MIN, DR_MIN)
         t = time.perf_counter()
-        oracle.me2(name, mom, mt=MT, alpha=w.alpha)
+        oracle_me2(name, mom)
         dt = time.perf_counter() - t
         if s >= args.warmup:
             times.append(dt)
@@ -236,11 +257,11 @@ def run_ours(args):
 
     __graft_entry__.build()
     import paper_2507_21039_gb300 as me
-    from paper_2507_21039_gb300.workloads import WORKLOADS
+    from paper_2507_21039_gb300.workloads import workload
 
     torch.cuda.set_device(local)
     name = args.workload
-    w = WORKLOADS[name]
+    w = workload(name)
     n = w.nevt
     masses = [0.0, 0.0] + list(w.masses_final)
     cuts = me.cuts_for(name)
@@ -365,13 +386,17 @@ def run_ours(args):
         "roofline": roofline,
         "clocks": clocks,
     }
+    if name == "gg_ttxgg" and world == 1 and not args.no_extra:
+        out["gg_ttxggg"] = extra_workload(me, "gg_ttxggg", steps=3, warmup=2, fp64_steps=1)
     if not args.no_serving and rank == 0:
-        try:
-            from paper_2507_21039_gb300 import serving
+        from paper_2507_21039_gb300 import serving
 
-            out["serving"] = serving.bench_point()
-        except (ImportError, AttributeError):
-            pass
+        sw = serving.sweep(nreq=args.serving_requests)
+        point = next(p for p in sw["points"] if p["load"] == 0.7)
+        out["serving"] = dict(point, requests=sw["requests_per_point"], mean_batch=sw["mean_batch"],
+                              saturation_events_per_s=sw["saturation_events_per_s"], processes=sw["processes"],
+                              precision=sw["precision"], lanes=sw["lanes"])
+        out["serving_sweep"] = sw
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(name, args.cpu_seconds, rank)
     if rank == 0:
@@ -382,6 +407,59 @@ def run_ours(args):
         import torch.distributed as dist
 
         dist.destroy_process_group()
+
+
+def extra_workload(me, name, steps, warmup, fp64_steps):
+    """Another benchmark configuration on this GPU, reported beside the
+    headline: the same step (device RAMBO + |M|^2 on the workload's batch),
+    mixed and FP64, CUDA events on the launching stream, and the mixed
+    kernel's fraction of the derived FP32 peak."""
+    import torch
+
+    from paper_2507_21039_gb300.workloads import workload
+
+    w = workload(name)
+    n = w.nevt
+    masses = [0.0, 0.0] + list(w.masses_final)
+    cuts = me.cuts_for(name)
+    stream = torch.cuda.current_stream()
+    mom = torch.empty((n, w.npar, 4), dtype=torch.float64, device="cuda")
+    me2 = torch.empty(n, dtype=torch.float64, device="cuda")
+    me.rambo_sample(w.seed, 0, n, w.sqrt_s, masses, cuts, momenta_out=mom, check=True)
+    res = {"workload": name, "process": PROCESS_LABEL[name], "events_per_step": n, "sqrt_s": w.sqrt_s,
+           "seed": w.seed, "step": "rambo_sample (device) + me_sigmakin"}
+    for prec, st, wu in (("mixed", steps, warmup), ("fp64", fp64_steps, 0)):
+        h = me.workload_handle(name, prec)
+        me.me_filter_helicities(h, mom)
+        for _ in range(wu):
+            me.rambo_sample(w.seed, 0, n, w.sqrt_s, masses, cuts, momenta_out=mom, stream=stream)
+            me.me_sigmakin(h, mom, me2, stream=stream)
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(st)]
+        s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s0.record(stream)
+        for a, b in ev:
+            me.rambo_sample(w.seed, 0, n, w.sqrt_s, masses, cuts, momenta_out=mom, stream=stream)
+            a.record(stream)
+            me.me_sigmakin(h, mom, me2, stream=stream)
+            b.record(stream)
+        s1.record(stream)
+        torch.cuda.synchronize()
+        dt = s0.elapsed_time(s1) / 1e3
+        kms = statistics.mean(a.elapsed_time(b) for a, b in ev)
+        res[prec] = {"value": n * st / dt, "unit": "events/s", "steps": st, "warmup": wu,
+                     "ms_per_step": 1e3 * dt / st, "me_kernel_ms": kms}
+        if prec == "mixed":
+            chain_f, colour_f = me.me_flops_per_event(h)
+            peaks, peak_src = measured_peaks()
+            fp32_peak = n_sm() * FP32_LANES_PER_SM * 2 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
+            achieved = (chain_f + colour_f) * n / (kms / 1e3) / 1e12
+            res["roofline"] = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+                               "frac": achieved / fp32_peak, "kernel": KERNELS[name],
+                               "flops_per_event": chain_f + colour_f, "peak_source": f"derived ({peak_src})"}
+        h.close()
+    res["mixed_over_fp64"] = res["mixed"]["value"] / res["fp64"]["value"]
+    return res
 
 
 def run_small():
@@ -448,9 +526,9 @@ def run_case(name, prec, nevt):
 
     __graft_entry__.build()
     import paper_2507_21039_gb300 as me
-    from paper_2507_21039_gb300.workloads import WORKLOADS
+    from paper_2507_21039_gb300.workloads import workload
 
-    w = WORKLOADS[name]
+    w = workload(name)
     masses = [0.0, 0.0] + list(w.masses_final)
     mom = me.rambo_sample(w.seed, 0, nevt, w.sqrt_s, masses, me.cuts_for(name), check=True)
     h = me.workload_handle(name, prec)

@@ -11,9 +11,12 @@
  *   - a scheduler thread groups queued requests of the same (process,
  *     precision) into one batch, up to max_batch events;
  *   - batches run on `lanes` CUDA streams at once; a batch is admitted only
- *     while the device bytes of all batches in flight (momenta + |M|^2) stay
- *     within hbm_budget_bytes, so requests that arrive while others run start
- *     as soon as a lane and memory are free;
+ *     while the device bytes of all batches in flight (momenta + |M|^2, plus
+ *     the global scratch of launches that use one: the FP64 colour-flow
+ *     vectors of gg_ttxggg) stay within hbm_budget_bytes, so requests that
+ *     arrive while others run start as soon as a lane and memory are free; a
+ *     later, smaller batch that fits may start before an older one that does
+ *     not (the older one waits for room after being passed over 8 times);
  *   - each lane replays its batch as a CUDA graph (H2D momenta, |M|^2 kernel,
  *     D2H results), captured per batch and updated in place;
  *   - results do not depend on the batch a request lands in (every event is
@@ -67,8 +70,15 @@ int srv_wait(srv_server* s, uint64_t ticket, int timeout_ms, double* latency_us)
  * written after this call returns).  The ticket is released. */
 int srv_cancel(srv_server* s, uint64_t ticket);
 
-/* srv_stats -- JSON object with counters (requests, batches, events, queue
- * depth, bytes in flight, graph updates) written into buf (cap bytes). */
+/* srv_stats -- JSON object with counters written into buf (cap bytes):
+ * requests, batches, events, queue depth, bytes in flight, graph updates, and
+ *   max_lanes_busy          most lanes holding a launched, unfinished batch at once;
+ *   max_device_concurrency  most batches seen running on the device at the same
+ *                           time (from timing events around each batch: the
+ *                           batches of different lanes overlap on the GPU);
+ *   head_bypasses           batches started ahead of an older request that did
+ *                           not fit the budget yet (at most 8 in a row for one);
+ *   lane_buffer_bytes       the lanes' fixed device buffers (outside the budget). */
 int srv_stats(srv_server* s, char* buf, int cap);
 
 /* srv_destroy -- stop the scheduler after finishing the batches in flight;

@@ -1,13 +1,19 @@
 // Continuous-batching server for |M|^2 requests (declared in include/me_serve.h).
 //
-// One scheduler thread owns the queue.  It takes the oldest queued request,
-// groups the queued requests of the same (process, precision) behind it into a
-// batch of at most max_batch events, and starts the batch on a free lane (CUDA
-// stream) as soon as the bytes of all batches in flight stay within the HBM
-// budget.  A lane stages the requests' momenta into its pinned buffer, runs
-// H2D copy -> |M|^2 kernel -> D2H copy (as a CUDA graph when enabled), and a
-// host function queued behind the D2H copy scatters the results to the
-// requests' buffers, stamps their latency and frees the lane.
+// One scheduler thread owns the queue.  It takes the oldest queued request
+// whose batch fits the HBM budget, groups the queued requests of the same
+// (process, precision) behind it into a batch of at most max_batch events, and
+// starts the batch on a free lane (CUDA stream).  A request that does not fit
+// yet is passed over by later, smaller ones at most kMaxBypass times; then the
+// scheduler waits for it.  A batch's device bytes are its momenta and |M|^2
+// plus the global scratch its launch allocates (the FP64 colour-flow vectors of
+// the largest process).  A lane stages the requests' momenta into its pinned
+// buffer, runs H2D copy -> |M|^2 kernel -> D2H copy (as a CUDA graph when
+// enabled) between two timing events, and a host function queued behind the
+// D2H copy scatters the results to the requests' buffers, stamps their
+// latency and frees the lane.  The scheduler thread reads the timing events of
+// finished batches (a host function may not call CUDA) and keeps the largest
+// number of batches seen running at once on the device.
 #include <algorithm>
 #include <atomic>
 #include <chrono>
@@ -26,6 +32,7 @@
 #include <cuda_runtime.h>
 
 #include "me.h"
+#include "me_proc.h"
 #include "me_serve.h"
 
 namespace {
@@ -55,6 +62,8 @@ struct GraphSlot {
 struct Lane {
     int index = 0;
     cudaStream_t stream = nullptr;
+    cudaEvent_t ev_start = nullptr, ev_end = nullptr;  // device time of the lane's current batch
+    bool timing_pending = false;                        // a finished batch whose events are not read yet
     double* d_mom = nullptr;
     double* d_me2 = nullptr;
     double* h_mom = nullptr;
@@ -69,14 +78,13 @@ struct Lane {
 
 constexpr int kMaxPar = 7;
 constexpr int kMaxLanes = 16;
+constexpr int kMaxBypass = 8;        // times the oldest request may be passed over by later ones
+constexpr size_t kMaxIntervals = 4096;  // device intervals of recent batches kept for the overlap count
 
 int npar_of(const char* process)
 {
-    static const std::pair<const char*, int> table[] = {
-        {"ee_mumu", 4}, {"gg_ttx", 4}, {"gg_ttxg", 5}, {"gg_ttxgg", 6}, {"gg_ttxggg", 7}};
-    for (auto& e : table)
-        if (std::strcmp(process, e.first) == 0) return e.second;
-    return 0;
+    const me::ProcDesc* pd = me::find_process(process);
+    return pd && pd->npar <= kMaxPar ? pd->npar : 0;
 }
 
 bool is_pinned(const void* p)
@@ -107,7 +115,14 @@ struct srv_server {
     std::thread sched;
     // counters
     uint64_t n_requests = 0, n_batches = 0, n_events = 0, n_graph_updates = 0, n_graph_instantiations = 0,
-             n_failed = 0, n_cancelled = 0, max_queue = 0, max_bytes_in_flight = 0;
+             n_failed = 0, n_cancelled = 0, max_queue = 0, max_bytes_in_flight = 0, n_bypass = 0;
+    int max_lanes_busy = 0;           // host view: lanes holding a launched, unfinished batch at once
+    int max_device_concurrency = 0;   // device view: batches whose kernels ran at overlapping times
+    int head_bypassed = 0;            // times the current oldest request was passed over
+    uint64_t lane_buffer_bytes = 0;   // fixed device bytes of the lanes' buffers
+    cudaEvent_t ev_ref = nullptr;     // time origin of the device intervals
+    std::deque<std::pair<float, float>> intervals;
+    void read_timings();
 
     me_handle* handle_for(const std::string& proc, int prec, int* status);
     void run();
@@ -124,9 +139,11 @@ me_handle* srv_server::handle_for(const std::string& proc, int prec, int* status
     auto it = handles.find(key);
     if (it != handles.end()) return it->second;
     const int npar = npar_of(proc.c_str());
+    const me::ProcDesc* pd = me::find_process(proc.c_str());
     double masses[kMaxPar] = {0};
-    const bool qcd = proc != "ee_mumu";
+    const bool qcd = pd && pd->family == 1;  // g g -> t t~ + n g: massive tops
     if (qcd) masses[2] = masses[3] = 173.0;
+    const double probe_sqrt_s = qcd ? 2000.0 : (pd && pd->family == 2 ? 500.0 : 100.0);
     me_handle* h = nullptr;
     *status = me_init(&h, proc.c_str(), masses, npar, nullptr, 0, prec);
     if (*status != ME_OK) return nullptr;
@@ -137,8 +154,8 @@ me_handle* srv_server::handle_for(const std::string& proc, int prec, int* status
         *status = ME_ENOMEM;
         return nullptr;
     }
-    *status = rambo_sample(20240607, 0, nprobe, qcd ? 2000.0 : 100.0, masses, npar, nullptr, d_probe, nullptr,
-                           nullptr, nullptr);
+    *status = rambo_sample(20240607, 0, nprobe, probe_sqrt_s, masses, npar, nullptr, d_probe, nullptr, nullptr,
+                           nullptr);
     if (*status == ME_OK && cudaDeviceSynchronize() != cudaSuccess) *status = ME_ECUDA;
     if (*status == ME_OK) *status = me_filter_helicities(h, d_probe, nprobe, nullptr);
     // one direct launch outside any capture (sets kernel attributes once)
@@ -177,6 +194,7 @@ void CUDART_CB srv_server::on_done(void* arg)
         }
         lane->batch.clear();
         lane->busy = false;
+        lane->timing_pending = true;
         s->bytes_in_flight -= lane->bytes;
         lane->bytes = 0;
     }
@@ -220,9 +238,12 @@ void srv_server::launch(Lane& lane, std::vector<std::shared_ptr<Request>> batch,
         cudaGraph_t g = nullptr;
         e = cudaStreamBeginCapture(lane.stream, cudaStreamCaptureModeRelaxed);
         if (e == cudaSuccess) {
+            // external records: the graph records the events each time it runs
+            cudaEventRecordWithFlags(lane.ev_start, lane.stream, cudaEventRecordExternal);
             cudaMemcpyAsync(lane.d_mom, lane.h_mom, mbytes, cudaMemcpyHostToDevice, lane.stream);
             status = me_sigmakin(h, lane.d_mom, n, lane.d_me2, lane.stream);
             cudaMemcpyAsync(lane.h_me2, lane.d_me2, sizeof(double) * n, cudaMemcpyDeviceToHost, lane.stream);
+            cudaEventRecordWithFlags(lane.ev_end, lane.stream, cudaEventRecordExternal);
             e = cudaStreamEndCapture(lane.stream, &g);
         }
         if (e == cudaSuccess && status == ME_OK) {
@@ -247,10 +268,12 @@ void srv_server::launch(Lane& lane, std::vector<std::shared_ptr<Request>> batch,
         }
         if (g) cudaGraphDestroy(g);
     } else {
-        e = cudaMemcpyAsync(lane.d_mom, lane.h_mom, mbytes, cudaMemcpyHostToDevice, lane.stream);
+        e = cudaEventRecord(lane.ev_start, lane.stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(lane.d_mom, lane.h_mom, mbytes, cudaMemcpyHostToDevice, lane.stream);
         if (e == cudaSuccess) status = me_sigmakin(h, lane.d_mom, n, lane.d_me2, lane.stream);
         if (e == cudaSuccess && status == ME_OK)
             e = cudaMemcpyAsync(lane.h_me2, lane.d_me2, sizeof(double) * n, cudaMemcpyDeviceToHost, lane.stream);
+        if (e == cudaSuccess && status == ME_OK) e = cudaEventRecord(lane.ev_end, lane.stream);
     }
     if (e == cudaSuccess && status == ME_OK) e = cudaLaunchHostFunc(lane.stream, &srv_server::on_done, &lane);
     if (e != cudaSuccess || status != ME_OK) {
@@ -260,6 +283,47 @@ void srv_server::launch(Lane& lane, std::vector<std::shared_ptr<Request>> batch,
         lane.bytes = 0;
         batch = std::move(b);
         return fail(status != ME_OK ? status : ME_ECUDA);
+    }
+}
+
+// Device bytes of one batch: momenta and |M|^2 of its events in the lane's
+// buffers, plus the global scratch the launch allocates (the FP64 colour-flow
+// vectors of the largest process: per resident CTA, times the resident CTAs)
+uint64_t batch_bytes(const std::string& process, int precision, int npar, int64_t n)
+{
+    uint64_t b = sizeof(double) * (4 * (uint64_t)npar + 1) * (uint64_t)n;
+    if (const me::ProcDesc* pd = me::find_process(process.c_str())) {
+        const size_t per = pd->jscratch_per_cta(precision);
+        if (per) b += (uint64_t)per * (uint64_t)std::max(1, pd->jscratch_ctas(precision));
+    }
+    return b;
+}
+
+// Device intervals of the batches finished since the last call (scheduler
+// thread, lock held): each new interval is compared with the recent ones to
+// find the largest number of batches that ran at the same time.
+void srv_server::read_timings()
+{
+    for (auto& l : lanes) {
+        if (!l.timing_pending || l.busy) continue;
+        l.timing_pending = false;
+        float t0 = 0.0f, t1 = 0.0f;
+        if (cudaEventElapsedTime(&t0, ev_ref, l.ev_start) != cudaSuccess ||
+            cudaEventElapsedTime(&t1, ev_ref, l.ev_end) != cudaSuccess) {
+            cudaGetLastError();
+            continue;
+        }
+        // largest overlap count at the start of the new interval or of any stored one inside it
+        std::vector<float> points{t0};
+        for (auto& iv : intervals)
+            if (iv.first > t0 && iv.first < t1) points.push_back(iv.first);
+        for (float p : points) {
+            int c = (p >= t0 && p < t1) ? 1 : 0;
+            for (auto& iv : intervals) c += (iv.first <= p && p < iv.second) ? 1 : 0;
+            max_device_concurrency = std::max(max_device_concurrency, c);
+        }
+        intervals.emplace_back(t0, t1);
+        if (intervals.size() > kMaxIntervals) intervals.pop_front();
     }
 }
 
@@ -276,27 +340,53 @@ void srv_server::run()
             return false;
         });
         if (stop) break;
-        // oldest request first; same (process, precision) requests behind it join its batch
-        auto head = queue.front();
-        const uint64_t per_event = sizeof(double) * (4 * head->npar + 1);
+        read_timings();
+        // the oldest request whose batch fits the budget (the oldest one itself once
+        // it has been passed over kMaxBypass times); the queued requests of the
+        // same (process, precision) behind it join its batch
         std::vector<std::shared_ptr<Request>> batch;
-        int64_t n = 0;
-        for (auto it = queue.begin(); it != queue.end();) {
-            auto& r = *it;
-            if (r->process == head->process && r->precision == head->precision && n + r->nevt <= cfg.max_batch) {
-                n += r->nevt;
-                batch.push_back(r);
-                it = queue.erase(it);
-            } else {
-                ++it;
+        uint64_t bytes = 0;
+        bool head = true;
+        for (size_t qi = 0; qi < queue.size(); ++qi) {
+            const auto cand = queue[qi];
+            bool seen = false;  // a group already considered (an earlier request of the same kind)
+            for (size_t j = 0; j < qi && !seen; ++j)
+                seen = queue[j]->process == cand->process && queue[j]->precision == cand->precision;
+            if (seen) continue;
+            int64_t n = 0;
+            for (auto& r : queue)
+                if (r->process == cand->process && r->precision == cand->precision && n + r->nevt <= cfg.max_batch)
+                    n += r->nevt;
+            const uint64_t b = batch_bytes(cand->process, cand->precision, cand->npar, n);
+            if (bytes_in_flight == 0 || bytes_in_flight + b <= cfg.hbm_budget_bytes) {
+                bytes = b;
+                for (auto it = queue.begin(); it != queue.end();) {
+                    auto& r = *it;
+                    if (r->process == cand->process && r->precision == cand->precision &&
+                        (int64_t)(r->nevt) <= n) {
+                        n -= r->nevt;
+                        batch.push_back(r);
+                        it = queue.erase(it);
+                    } else {
+                        ++it;
+                    }
+                }
+                break;
             }
+            if (head && head_bypassed >= kMaxBypass) break;  // the oldest request waits for room
+            head = false;
         }
-        const uint64_t bytes = per_event * (uint64_t)n;
-        if (bytes_in_flight > 0 && bytes_in_flight + bytes > cfg.hbm_budget_bytes) {
-            // not enough device memory budget yet: put the batch back, wait for a completion
-            for (auto rit = batch.rbegin(); rit != batch.rend(); ++rit) queue.push_front(*rit);
-            cv_work.wait(lock, [&] { return stop || bytes_in_flight + bytes <= cfg.hbm_budget_bytes; });
+        if (batch.empty()) {  // nothing fits the budget yet: wait for a completion or a new request
+            const uint64_t before = bytes_in_flight;
+            const size_t queued = queue.size();
+            cv_work.wait(lock, [&] { return stop || bytes_in_flight < before || queue.size() != queued; });
             continue;
+        }
+        if (head) {
+            head_bypassed = 0;
+        } else {
+            ++head_bypassed;
+            ++n_bypass;
         }
         Lane* lane = nullptr;
         for (auto& l : lanes)
@@ -305,9 +395,16 @@ void srv_server::run()
                 break;
             }
         lane->busy = true;
+        int busy = 0;
+        for (auto& l : lanes) busy += l.busy;
+        max_lanes_busy = std::max(max_lanes_busy, busy);
         bytes_in_flight += bytes;
         max_bytes_in_flight = std::max(max_bytes_in_flight, bytes_in_flight);
-        for (auto& r : batch) r->state = RUNNING;
+        int64_t n = 0;
+        for (auto& r : batch) {
+            r->state = RUNNING;
+            n += r->nevt;
+        }
         ++n_batches;
         n_events += n;
         lock.unlock();
@@ -334,7 +431,9 @@ int srv_create(srv_server** out, const srv_config* cfg)
         Lane& l = s->lanes[i];
         l.index = i;
         l.owner = s.get();
-        if (cudaStreamCreateWithFlags(&l.stream, cudaStreamNonBlocking) != cudaSuccess) rc = ME_ECUDA;
+        if (cudaStreamCreateWithFlags(&l.stream, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreate(&l.ev_start) != cudaSuccess || cudaEventCreate(&l.ev_end) != cudaSuccess)
+            rc = ME_ECUDA;
         else if (cudaMalloc(&l.d_mom, mom_bytes) != cudaSuccess || cudaMalloc(&l.d_me2, me2_bytes) != cudaSuccess ||
                  cudaMallocHost(&l.h_mom, mom_bytes) != cudaSuccess ||
                  cudaMallocHost(&l.h_me2, me2_bytes) != cudaSuccess)
@@ -345,6 +444,13 @@ int srv_create(srv_server** out, const srv_config* cfg)
         srv_destroy(s.release());
         return rc;
     }
+    if (cudaEventCreate(&s->ev_ref) != cudaSuccess || cudaEventRecord(s->ev_ref, 0) != cudaSuccess ||
+        cudaEventSynchronize(s->ev_ref) != cudaSuccess) {
+        cudaGetLastError();
+        srv_destroy(s.release());
+        return ME_ECUDA;
+    }
+    s->lane_buffer_bytes = (uint64_t)cfg->lanes * (mom_bytes + me2_bytes);
     srv_server* raw = s.release();
     raw->sched = std::thread([raw] { raw->run(); });
     *out = raw;
@@ -420,18 +526,21 @@ int srv_stats(srv_server* s, char* buf, int cap)
 {
     if (!s || !buf || cap <= 0) return ME_EINVAL;
     std::lock_guard<std::mutex> lock(s->mu);
+    s->read_timings();
     int busy = 0;
     for (auto& l : s->lanes) busy += l.busy;
     snprintf(buf, cap,
              "{\"requests\": %llu, \"batches\": %llu, \"events\": %llu, \"queue_depth\": %zu, \"max_queue_depth\": "
              "%llu, \"lanes_busy\": %d, \"bytes_in_flight\": %llu, \"graph_updates\": %llu, "
              "\"graph_instantiations\": %llu, \"failed\": %llu, \"cancelled\": %llu, \"handles\": %zu, "
-             "\"max_bytes_in_flight\": %llu}",
+             "\"max_bytes_in_flight\": %llu, \"max_lanes_busy\": %d, \"max_device_concurrency\": %d, "
+             "\"head_bypasses\": %llu, \"lane_buffer_bytes\": %llu}",
              (unsigned long long)s->n_requests, (unsigned long long)s->n_batches, (unsigned long long)s->n_events,
              s->queue.size(), (unsigned long long)s->max_queue, busy, (unsigned long long)s->bytes_in_flight,
              (unsigned long long)s->n_graph_updates, (unsigned long long)s->n_graph_instantiations,
              (unsigned long long)s->n_failed, (unsigned long long)s->n_cancelled, s->handles.size(),
-             (unsigned long long)s->max_bytes_in_flight);
+             (unsigned long long)s->max_bytes_in_flight, s->max_lanes_busy, s->max_device_concurrency,
+             (unsigned long long)s->n_bypass, (unsigned long long)s->lane_buffer_bytes);
     return ME_OK;
 }
 
@@ -451,12 +560,15 @@ void srv_destroy(srv_server* s)
         for (auto& kv : l.graphs)
             if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
         if (l.stream) cudaStreamDestroy(l.stream);
+        if (l.ev_start) cudaEventDestroy(l.ev_start);
+        if (l.ev_end) cudaEventDestroy(l.ev_end);
         cudaFree(l.d_mom);
         cudaFree(l.d_me2);
         cudaFreeHost(l.h_mom);
         cudaFreeHost(l.h_me2);
     }
     for (auto& kv : s->handles) me_free(kv.second);
+    if (s->ev_ref) cudaEventDestroy(s->ev_ref);
     delete s;
 }
 

@@ -38,15 +38,21 @@ def test_same_alone_and_in_the_mix(orc, srvmod, graphs):
     import paper_2507_21039_gb300 as me
 
     srv = srvmod.Server(lanes=3, max_batch=1 << 14, use_graphs=graphs)
+    burst = [("gg_ttxgg", 8192, "fp64"), ("gg_ttx", 3000, "mixed"), ("gg_ttxgg", 1234, "mixed"),
+             ("ee_mumu", 999, "fp64"), ("gg_ttxg", 4096, "mixed"), ("gg_ttxgg", 2048, "mixed"),
+             ("gg_ttx", 517, "fp64"), ("gg_ttxgg", 300, "fp64")]
+    # resident handles first (creating one filters its helicities, which waits for the device)
+    for name, prec in sorted({(b[0], b[2]) for b in burst}):
+        m, _ = pinned_events(orc, name, 64)
+        srv.wait(srv.submit(name, m, out_like(64), prec))
+    warm = srv.stats()["requests"]
     probe, probe_np = pinned_events(orc, "gg_ttxgg", 777, ev0=5000)
     alone = out_like(777)
     srv.wait(srv.submit("gg_ttxgg", probe, alone, "mixed"))
-    # the same request amid a burst of other processes, precisions and sizes
+    # the same request amid a burst of other processes, precisions and sizes (the
+    # long FP64 batch first: the others start while it runs)
     others = []
-    for i, (name, n, prec) in enumerate([("gg_ttx", 3000, "mixed"), ("gg_ttxgg", 1234, "mixed"),
-                                         ("ee_mumu", 999, "fp64"), ("gg_ttxg", 4096, "mixed"),
-                                         ("gg_ttxgg", 2048, "mixed"), ("gg_ttx", 517, "fp64"),
-                                         ("gg_ttxgg", 300, "fp64")]):
+    for i, (name, n, prec) in enumerate(burst):
         m, _ = pinned_events(orc, name, n, ev0=100 * i)
         o = out_like(n)
         others.append((name, prec, m, o, srv.submit(name, m, o, prec)))
@@ -69,9 +75,12 @@ def test_same_alone_and_in_the_mix(orc, srvmod, graphs):
         rel = np.abs(o.numpy()[:64] / ref - 1)
         assert rel.max() < (1e-12 if prec == "fp64" else 1e-3)
     st = srv.stats()
-    assert st["requests"] == 10 and st["failed"] == 0
+    assert st["requests"] == warm + 11 and st["failed"] == 0
     if graphs:
         assert st["graph_instantiations"] + st["graph_updates"] >= st["batches"]
+    # the burst's batches ran at the same time on the device (timing events
+    # around each batch on its lane's stream), not one after another
+    assert st["max_lanes_busy"] >= 2 and st["max_device_concurrency"] >= 2, st
     srv.close()
 
 
@@ -136,4 +145,54 @@ def test_nonfinite_event_does_not_leak_into_neighbours(orc, srvmod):
     keep[17] = False
     assert torch.equal(res[keep], good[keep])
     assert not torch.isfinite(res[17])
+    srv.close()
+
+
+def test_smaller_request_passes_one_that_does_not_fit(orc, srvmod):
+    """Admission without head-of-line blocking: while a large batch holds most
+    of the budget, an older large request that does not fit waits and a later
+    small one that fits starts (and finishes) first; every result is right."""
+    npar = 6
+    per_event = 8 * (4 * npar + 1)
+    srv = srvmod.Server(lanes=4, max_batch=1 << 14, hbm_budget_bytes=per_event * 12000)
+    big, big_np = pinned_events(orc, "gg_ttxgg", 8000)
+    small, small_np = pinned_events(orc, "gg_ttx", 500)
+    o_a, o_b, o_c = out_like(8000), out_like(8000), out_like(500)
+    ta = srv.submit("gg_ttxgg", big, o_a, "fp64")    # holds 8000 events' bytes for a while
+    tb = srv.submit("gg_ttxgg", big, o_b, "mixed")   # does not fit beside it: waits
+    tc = srv.submit("gg_ttx", small, o_c, "mixed")   # fits: starts before tb
+    lat_c = srv.wait(tc)
+    lat_b = srv.wait(tb)
+    srv.wait(ta)
+    st = srv.stats()
+    assert st["head_bypasses"] >= 1 and lat_c < lat_b, (st, lat_c, lat_b)
+    assert st["max_bytes_in_flight"] <= per_event * 12000
+    ref = orc.me2("gg_ttx", small_np[:64], mt=MT, alpha=WORKLOADS["gg_ttx"].alpha)
+    assert np.abs(o_c.numpy()[:64] / ref - 1).max() < 1e-3
+    ref = orc.me2("gg_ttxgg", big_np[:16], mt=MT, alpha=WORKLOADS["gg_ttxgg"].alpha)
+    assert np.abs(o_a.numpy()[:16] / ref - 1).max() < 1e-12
+    assert np.abs(o_b.numpy()[:16] / ref - 1).max() < 1e-3
+    srv.close()
+
+
+def test_budget_counts_launch_scratch_and_serves_drell_yan(orc, srvmod):
+    """An FP64 gg -> t t~ ggg batch is charged its launch's colour-flow scratch
+    (240 KB per resident CTA) beside its momenta and |M|^2; a Drell-Yan request
+    is served like the others."""
+    from paper_2507_21039_gb300.workloads import ALPHA_S, DY_WORKLOADS
+
+    srv = srvmod.Server(lanes=2, max_batch=1 << 12)
+    m, _ = pinned_events(orc, "gg_ttxggg", 64)
+    o = out_like(64)
+    srv.wait(srv.submit("gg_ttxggg", m, o, "fp64"))
+    st = srv.stats()
+    assert st["max_bytes_in_flight"] >= 64 * 8 * (4 * 7 + 1) + 240 * 1024, st
+    w = DY_WORKLOADS["uux_epemgg"]
+    dmom, _, _ = orc.rambo(w.seed, w.sqrt_s, w.masses_final, 0, 300, w.cut_mask, PT_MIN, DR_MIN)
+    d = torch.empty(dmom.shape, dtype=torch.float64, pin_memory=True)
+    d.copy_(torch.from_numpy(dmom))
+    od = out_like(300)
+    srv.wait(srv.submit("uux_epemgg", d, od, "fp64"))
+    ref = orc.dy_me2(2, dmom, alpha_s=ALPHA_S)
+    assert np.abs(od.numpy() / ref - 1).max() < 1e-12
     srv.close()
