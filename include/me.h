@@ -61,8 +61,9 @@ extern "C" {
 #define ME_PREC_FP64 0   /* chain, colour sum and helicity sum in FP64 */
 #define ME_PREC_FP32 1   /* chain and colour sum in FP32; momenta, p^2-m^2 and helicity sum in FP64 */
 #define ME_PREC_MIXED 2  /* FP32 chain (FP64 momenta, p^2-m^2), colour sum on BF16 tensor cores
-                            with hi/lo split operands and FP32 accumulation (24 and 120 flows;
-                            FP32 scalar below), FP64 helicity sum */
+                            with hi/lo split operands and FP32 accumulation where that is
+                            faster on GB300 (120 flows; below, FP32 scalar, which measured
+                            faster at 24 flows), FP64 helicity sum */
 #define ME_PREC_MIXED64 3 /* the paper's mixed mode (Sec. 4.1, Table 1): FP64 chain, the colour-flow
                              amplitudes cast to FP32 for the colour sum, FP64 helicity sum */
 

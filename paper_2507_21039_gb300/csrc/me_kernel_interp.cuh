@@ -39,13 +39,6 @@
 #define ME_INTERP_J_MMA 1
 #endif
 
-// Bound on each wait for the tensor cores (clock cycles, about a second):
-// a wait that runs out marks the thread's events as failed (|M|^2 = NaN) and
-// the kernel stops waiting instead of hanging the GPU
-#ifndef ME_WAIT_LIMIT_CYCLES
-#define ME_WAIT_LIMIT_CYCLES (1LL << 31)
-#endif
-
 namespace me {
 
 struct __align__(8) IRound {
@@ -500,24 +493,8 @@ template <class P, class T, bool TC, class C, bool SDE> cudaError_t interp_resid
         cudaGetLastError();
         per_sm = 1;
     }
-    if constexpr (L::J_MMA) {
-        // The occupancy query counts one CTA per SM for a kernel that allocates
-        // tensor memory; the SM takes another CTA once the resident one has
-        // given up its allocation permit (right after its allocation here), so
-        // the residency is what shared memory, registers and TMEM columns allow
-        int smem_sm = 0, reserved = 0;
-        cudaFuncAttributes fa{};
-        if (cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) == cudaSuccess &&
-            cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev) == cudaSuccess &&
-            cudaFuncGetAttributes(&fa, me_kernel_interp<P, T, TC, C, SDE>) == cudaSuccess && fa.numRegs > 0) {
-            const int by_smem = (int)((size_t)smem_sm / (L::launch_bytes + fa.sharedSizeBytes + (size_t)reserved));
-            const int regs = (fa.numRegs + 7) / 8 * 8;
-            const int by_regs = 65536 / (regs * P::NT);
-            per_sm = std::max(1, std::min({by_smem, by_regs, (int)(512 / L::TMEM_COLS)}));
-        } else {
-            cudaGetLastError();
-        }
-    }
+    if constexpr (L::J_MMA) per_sm = tmem_kernel_ctas_per_sm(me_kernel_interp<P, T, TC, C, SDE>, L::launch_bytes, P::NT,
+                                                             L::TMEM_COLS);
     return cudaSuccess;
 }
 

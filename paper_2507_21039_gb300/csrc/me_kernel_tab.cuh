@@ -21,6 +21,7 @@
 
 #include "me_colour_tc.cuh"
 #include "me_kernel.cuh"
+#include "me_tmem.cuh"
 
 // Ordering point between amplitudes (a warp barrier, which ptxas does not move
 // shared-memory loads across): keeps the operand loads of many amplitudes from
@@ -131,6 +132,95 @@ template <class P, class T> __host__ __device__ constexpr size_t tab_smem_bytes(
 
 template <class P, class T> __host__ __device__ constexpr int tab_epc() { return is_fp64<T>() ? P::EPC_D : P::EPC_F; }
 
+// Build option ME_TAB_TC_UMMA: the tensor-core colour sum of a CTA of 128
+// helicity rows as tcgen05.mma with the result in TMEM (1, default where the
+// colour numerators are exact in BF16 and at most 32 flows), or as per-warp
+// mma.sync (0)
+#ifndef ME_TAB_TC_UMMA
+#define ME_TAB_TC_UMMA 1
+#endif
+template <class P, class T, bool TC> __host__ __device__ constexpr bool tab_umma()
+{
+    if constexpr (!TC) {
+        return false;
+    } else {
+        return ME_TAB_TC_UMMA && P::NCOL <= 32 && !P::NSPLIT && P::NT * tab_epc<P, T>() == 128 &&
+               tab_epc<P, T>() == 2 && (size_t)P::TAB * sizeof(Wf<T>) >= 4 * 4096;
+    }
+}
+constexpr uint32_t kTabUmmaCols = 64;  // TMEM columns: Re rows' results 0-31, Im rows' 32-63
+
+// Colour form J^+ N J of the CTA's 128 helicity rows (thread = row = TMEM
+// lane) on the tensor cores with tcgen05.mma (Sec. 4.1 colour algebra):
+//   * each thread writes its row of A: Re J and Im J split exactly into BF16
+//     hi + lo (16 significant bits of each FP32 value), flows 0..31 (zero past
+//     NCOL) as two K = 16 operand images per matrix -- eight 4096-byte images,
+//     four in each event slot's table region, which is dead at this point;
+//   * one thread issues Y_re = (Re J)_hi N + (Re J)_lo N and the same for Im
+//     (M = 128, N = 32, K = 16, eight MMAs; N exact in BF16, FP32 accumulation
+//     in TMEM columns 0-31 and 32-63) and commits them to the mbarrier;
+//   * every thread waits (bounded), reads its row of Y from TMEM and returns
+//     Re J . Y_re + Im J . Y_im with its own FP32 J.
+// The caller has passed a CTA barrier after the last table read.  Returns NaN
+// for the thread if a wait ran out (`failed` then stays set).
+template <class P, class T, class JT>
+__device__ __forceinline__ float colour_umma(const JT& J, unsigned char* smem_all, const unsigned char* cn_smem,
+                                             uint32_t tmem_base, uint64_t* bar, uint32_t& ncommit, bool& failed)
+{
+    constexpr int NCOL = P::NCOL;
+    // image j = 2 m + ks (m: 0 Re hi, 1 Re lo, 2 Im hi, 3 Im lo; ks: K step) of event slot j / 4
+    auto img = [&](int m, int ks) -> unsigned char* {
+        const int j = 2 * m + ks;
+        return smem_all + (size_t)(j >> 2) * tab_smem_bytes<P, T>() + tab_table_offset<P, T>() + (size_t)(j & 3) * 4096;
+    };
+    auto jre = [&](int f) { return f < NCOL ? (float)J[f < NCOL ? f : 0].re : 0.0f; };
+    auto jim = [&](int f) { return f < NCOL ? (float)J[f < NCOL ? f : 0].im : 0.0f; };
+    const int row = threadIdx.x;
+#pragma unroll
+    for (int ks = 0; ks < 2; ++ks)
+#pragma unroll
+        for (int kc = 0; kc < 2; ++kc) {  // 8 flows = one 16-byte chunk of the row per matrix
+            uint32_t w[4][4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int f = 16 * ks + 8 * kc + 2 * q;
+                split2(jre(f), jre(f + 1), w[0][q], w[1][q]);
+                split2(jim(f), jim(f + 1), w[2][q], w[3][q]);
+            }
+            const uint32_t off = umma_k16_offset(row, 8 * kc);
+#pragma unroll
+            for (int m = 0; m < 4; ++m)
+                *reinterpret_cast<uint4*>(img(m, ks) + off) = make_uint4(w[m][0], w[m][1], w[m][2], w[m][3]);
+        }
+    fence_proxy_async_smem();
+    __syncthreads();
+    if (row == 0 && !failed) {
+        tmem_fence_after_sync();
+        constexpr uint32_t ID = umma_idesc_bf16_f32(128, 32, false);
+#pragma unroll
+        for (int ks = 0; ks < 2; ++ks) {
+            const uint64_t bdesc = umma_smem_desc(cn_smem + 1024 * ks, 128, 256);
+#pragma unroll
+            for (int m = 0; m < 4; ++m)  // the first MMA into each result overwrites it
+                umma_bf16(tmem_base + (m < 2 ? 0u : 32u), umma_smem_desc(img(m, ks), 128, 256), bdesc, ID,
+                          ks > 0 || (m & 1));
+        }
+        umma_commit(bar);
+    }
+    if (!failed && !mbar_wait_bounded(bar, ncommit & 1u, ME_WAIT_LIMIT_CYCLES)) failed = true;
+    ++ncommit;
+    tmem_fence_after_sync();
+    const uint32_t tl = tmem_base + ((uint32_t)(32 * (row >> 5)) << 16);
+    uint32_t y[4][16];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) tmem_ld_16(tl + 16u * (uint32_t)c, y[c]);
+    float v = 0.0f;
+#pragma unroll
+    for (int c = 0; c < NCOL; ++c)
+        v = fmaf(jre(c), __uint_as_float(y[c >> 4][c & 15]), fmaf(jim(c), __uint_as_float(y[2 + (c >> 4)][c & 15]), v));
+    return failed ? __int_as_float(0x7fc00000) : v;
+}
+
 template <class P, class T, bool TC, class C = T, bool SDE = false>
 __global__ void __launch_bounds__(P::NT * tab_epc<P, T>(), is_fp64<T>() ? P::MIN_CTAS_D : P::MIN_CTAS_F)
     me_kernel_tab(LaunchArgs a)
@@ -151,6 +241,29 @@ __global__ void __launch_bounds__(P::NT * tab_epc<P, T>(), is_fp64<T>() ? P::MIN
     double* sgram = reinterpret_cast<double*>(smem + tab_gram_offset<P, T>());
     const double m2 = a.mt * a.mt;
     const float mtf = (float)a.mt;
+    // tcgen05 colour sum: the numerators (B operand) in shared memory once per
+    // CTA, 64 TMEM columns, one mbarrier for the MMAs' completion
+    constexpr bool UMMA = tab_umma<P, T, TC>();
+    __shared__ __align__(16) unsigned char cn_smem[UMMA ? 2048 : 16];
+    __shared__ uint32_t tmem_base;
+    __shared__ __align__(8) uint64_t mma_bar;
+    uint32_t ncommit = 0;  // MMA commits so far (the same in every thread)
+    bool failed = false;   // a wait for the tensor cores ran out
+    if constexpr (UMMA) {
+        if (threadIdx.x < 32) {
+            tmem_alloc(&tmem_base, kTabUmmaCols);
+            tmem_relinquish();
+        }
+        if (threadIdx.x == 0) {
+            mbar_init(&mma_bar, 1);
+            mbar_init_fence();
+        }
+        for (int i = threadIdx.x; i < 128; i += blockDim.x) reinterpret_cast<uint4*>(cn_smem)[i] = __ldg(P::umma_cn() + i);
+        fence_proxy_async_smem();
+        tmem_fence_before_sync();
+        __syncthreads();
+        tmem_fence_after_sync();
+    }
 
     for (long long e0 = (long long)blockIdx.x * EPC; e0 < a.nevt; e0 += (long long)gridDim.x * EPC) {
         const long long e = e0 + grp;
@@ -218,7 +331,10 @@ __global__ void __launch_bounds__(P::NT * tab_epc<P, T>(), is_fp64<T>() ? P::MIN
             if constexpr (P::STAGED) P::template staged<T, SDE>(tab, sln, (T)a.mt, tid, h, J, sde);
             else P::template amps<T, SDE>(tab, h, sln, J, sde);
             T v;
-            if constexpr (TC) {
+            if constexpr (UMMA) {
+                __syncthreads();  // single pass (nlist <= NT): the tables are dead, reuse them as staging
+                v = colour_umma<P, T>(J, smem_all, cn_smem, tmem_base, &mma_bar, ncommit, failed);
+            } else if constexpr (TC) {
                 __syncthreads();  // single pass (nlist <= NT): the tables are dead, reuse them as staging
 #if ME_TAB_TC_FROM_SMEM
                 // J leaves the registers first ([flow][lane] FP32 per warp), so the
@@ -292,7 +408,17 @@ __global__ void __launch_bounds__(P::NT * tab_epc<P, T>(), is_fp64<T>() ? P::MIN
                 if constexpr (SDE) a.sde_w[e] = sden > 0.0 ? snum / sden : 0.0;
             }
         }
+        if constexpr (UMMA) tmem_fence_before_sync();  // TMEM reads done before the next events' MMAs
         __syncthreads();  // shared memory is reused by the next events
+    }
+    if constexpr (UMMA) {
+        if (ncommit > 0 && failed) mbar_wait_bounded(&mma_bar, (ncommit - 1) & 1u, ME_WAIT_LIMIT_CYCLES);
+        tmem_fence_before_sync();
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            tmem_fence_after_sync();
+            tmem_dealloc(tmem_base, kTabUmmaCols);
+        }
     }
 }
 
@@ -310,7 +436,19 @@ template <class P, class T, bool TC = false, class C = T, bool SDE = false> cuda
         cudaError_t e = ensure_smem(me_kernel_tab<P, T, TC, C, SDE>, smem, granted);
         if (e != cudaSuccess) return e;
         const long long ctas = (a.nevt + EPC - 1) / EPC;
-        const long long grid = ctas < 0x7fffffffLL ? ctas : 0x7fffffffLL;
+        long long grid = ctas < 0x7fffffffLL ? ctas : 0x7fffffffLL;
+        if constexpr (tab_umma<P, T, TC>()) {
+            // persistent: TMEM is allocated once per CTA, which then loops over event pairs
+            static int resident = 0;
+            if (!resident) {
+                int dev = 0, nsm = 0;
+                cudaGetDevice(&dev);
+                cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+                resident = std::max(1, nsm) *
+                           tmem_kernel_ctas_per_sm(me_kernel_tab<P, T, TC, C, SDE>, smem, P::NT * EPC, (int)kTabUmmaCols);
+            }
+            if (grid > resident) grid = resident;
+        }
         me_kernel_tab<P, T, TC, C, SDE><<<(unsigned)grid, P::NT * EPC, smem, a.stream>>>(a);
         return cudaGetLastError();
     }
@@ -321,9 +459,13 @@ template <class P, class T, bool TC = false, class C = T, bool SDE = false> cuda
 template <class P, class T, bool TC, class C, bool SDE> cudaError_t launch_interp(const LaunchArgs& a);
 
 // Build option ME_MIXED_TC_MIN_NCOL: smallest colour basis whose mixed-precision
-// colour sum runs on the tensor cores (default 24).
+// colour sum runs on the tensor cores.  Default 120, the crossover measured on
+// GB300: at 24 flows (gg -> t t~ g g, J in registers, 0.65 k FMA per helicity)
+// the FP32 scalar form is faster than either tensor-core form (20.2 ms per 2^20
+// events against 21.5 ms with mma.sync and 22.8 ms with tcgen05.mma); at 120
+// flows the tensor cores pay (gg -> t t~ ggg: 674 ms against 847 ms per 2^18).
 #ifndef ME_MIXED_TC_MIN_NCOL
-#define ME_MIXED_TC_MIN_NCOL 24
+#define ME_MIXED_TC_MIN_NCOL 120
 #endif
 template <class P> cudaError_t launch_mixed(const LaunchArgs& a)
 {

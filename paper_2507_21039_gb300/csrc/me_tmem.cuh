@@ -11,7 +11,17 @@
 // tcgen05.wait::st.  Every access here is warp-collective (.sync.aligned): the
 // whole warp executes it with the same address.
 #pragma once
+#include <algorithm>
 #include <cstdint>
+
+#include <cuda_runtime.h>
+
+// Bound on each wait for the tensor cores (clock cycles, about a second):
+// a wait that runs out marks the thread's events as failed (|M|^2 = NaN) and
+// the kernel stops waiting instead of hanging the GPU
+#ifndef ME_WAIT_LIMIT_CYCLES
+#define ME_WAIT_LIMIT_CYCLES (1LL << 31)
+#endif
 
 namespace me {
 
@@ -184,6 +194,28 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
     while (!mbar_try_wait(bar, parity))
         if (clock64() - t0 > limit) return false;
     return true;
+}
+
+// Resident CTAs per SM of a kernel that allocates `tmem_cols` TMEM columns
+// per CTA.  The occupancy query counts one CTA per SM for such a kernel; the
+// SM takes another CTA once the resident one has given up its allocation
+// permit (our kernels do right after allocating), so the residency is what
+// shared memory, registers and the 512 TMEM columns allow.  (1 on failure.)
+template <class K> int tmem_kernel_ctas_per_sm(K kernel, size_t dyn_smem, int threads, int tmem_cols)
+{
+    int dev = 0, smem_sm = 0, reserved = 0;
+    cudaFuncAttributes fa{};
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev) != cudaSuccess ||
+        cudaFuncGetAttributes(&fa, kernel) != cudaSuccess || fa.numRegs <= 0) {
+        cudaGetLastError();
+        return 1;
+    }
+    const int by_smem = (int)((size_t)smem_sm / (dyn_smem + fa.sharedSizeBytes + (size_t)reserved));
+    const int regs = (fa.numRegs + 7) / 8 * 8;
+    const int by_regs = 65536 / (regs * threads);
+    return std::max(1, std::min({by_smem, by_regs, 512 / tmem_cols}));
 }
 
 }  // namespace me

@@ -308,6 +308,23 @@ def emit_process(process: str) -> tuple[str, dict]:
                     + "\n};\n")
         tc_members = (f"\n    static constexpr bool NSPLIT = {'true' if nsplit else 'false'};"
                       f"\n    __device__ static __forceinline__ const uint2* bfrag() {{ return c_bfrag; }}")
+        if ncol <= 32 and not nsplit:
+            # colour numerators as the B operand of tcgen05.mma (K-major, N = K = 32,
+            # padded with zeros): two K = 16 images, B[n][k] = N[k][n], BF16 exact
+            img = [0] * 1024
+            for ks in range(2):
+                for n_ in range(32):
+                    for kk in range(16):
+                        k_ = 16 * ks + kk
+                        if n_ < ncol and k_ < ncol:
+                            img[512 * ks + umma_k16_offset(n_, kk) // 2] = _bf16_bits(num[k_][n_])
+            words = [img[i] | (img[i + 1] << 16) for i in range(0, 1024, 2)]
+            tc_array += (f"__device__ __align__(16) const unsigned int c_umma_cn[512] = {{\n    "
+                         + ",\n    ".join(", ".join("%du" % x for x in words[i:i + 12]) for i in range(0, 512, 12))
+                         + "\n};\n")
+            tc_members += ("\n    // colour numerators as a tcgen05.mma operand (two K = 16 images of 32 x 16)"
+                           "\n    __device__ static __forceinline__ const uint4* umma_cn() "
+                           "{ return reinterpret_cast<const uint4*>(c_umma_cn); }")
     ns = f"p_{process}"
     family = 0 if process == "ee_mumu" else (2 if dy else 1)
     # internal-line sets of the diagrams (QCD and e+e-); the Drell-Yan plans carry none

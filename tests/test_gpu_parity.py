@@ -270,13 +270,15 @@ def test_host_buffer_pipeline_matches_device(name, prec):
 
 
 def test_mixed_uses_tensor_core_colour_sum(orc):
-    """gg -> t t~ g g mixed: the colour sum runs on BF16 tensor cores (hi/lo
-    split, FP32 accumulation).  Its results differ bitwise from the FP32 scalar
-    colour sum but both agree with the FP64 oracle within the FP32 tolerances;
-    per-helicity contributions add up to the event total."""
-    name = "gg_ttxgg"
+    """gg -> t t~ ggg mixed: the 120-flow colour sum runs on BF16 tensor cores
+    (hi/lo split, FP32 accumulation).  Its results differ bitwise from the FP32
+    scalar colour sum but both agree with the FP64 oracle within the FP32
+    tolerances; per-helicity contributions add up to the event total.  At 24
+    flows (gg -> t t~ g g) the mixed mode's colour sum is the FP32 scalar one
+    (measured faster there), so mixed and FP32 agree bitwise."""
+    name = "gg_ttxggg"
     w = WORKLOADS[name]
-    mom = oracle_events(orc, name, 300)
+    mom = oracle_events(orc, name, 64)
     ref = orc.me2(name, mom, mt=MT, alpha=w.alpha)
     d = torch.from_numpy(mom).cuda()
     out = {}
@@ -290,10 +292,12 @@ def test_mixed_uses_tensor_core_colour_sum(orc):
         plain = me.me_sigmakin(h, d)
         torch.cuda.synchronize()
         assert torch.equal(plain, me2)
-        assert np.allclose(hel.sum(1).cpu().numpy(), me2.cpu().numpy(), rtol=1e-12, atol=0)
+        assert np.allclose(hel.sum(1).cpu().numpy(), me2.cpu().numpy(), rtol=1e-6, atol=0)
         out[prec] = me2.cpu().numpy()
         h.close()
     assert not np.array_equal(out["fp32"], out["mixed"])
     for prec in ("fp32", "mixed"):
         rel = np.abs(out[prec] / ref - 1)
         assert np.median(rel) <= LOW_MEDIAN and rel.max() <= LOW_MAX, (prec, np.median(rel), rel.max())
+    mom2 = oracle_events(orc, "gg_ttxgg", 300)
+    assert np.array_equal(gpu_me2("gg_ttxgg", "fp32", mom2), gpu_me2("gg_ttxgg", "mixed", mom2))

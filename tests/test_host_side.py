@@ -268,6 +268,28 @@ def test_stage_sign_matrices_replay_the_flow_updates():
     assert np.abs(J1 - (Jre[:120] + 1j * Jim[:120])).max() < 1e-12 * np.abs(J1).max()
 
 
+def test_colour_numerators_as_tensor_core_operand():
+    """gg -> t t~ g g's colour numerators as the B operand of the table
+    kernel's tcgen05.mma colour sum: the two BF16 K = 16 images decoded through
+    the operand layout give N[k][n] for k, n < 24 and zero in the padding."""
+    from paper_2507_21039_gb300.gen.emit import emit_process, umma_k16_offset
+
+    src, _ = emit_process("gg_ttxgg")
+    body = re.search(r"c_umma_cn\[512\] = \{(.*?)\};", src, re.S).group(1)
+    words = [int(x) for x in re.findall(r"\d+", body)]
+    halves = np.array([(w >> sh) & 0xFFFF for w in words for sh in (0, 16)], dtype=np.uint32)
+    vals = (halves << 16).astype(np.uint32).view(np.float32).astype(float)
+    num, _ = colour_matrix(4)
+    B = np.zeros((32, 32))
+    for ks in range(2):
+        for n in range(32):
+            for kk in range(16):
+                B[n, 16 * ks + kk] = vals[512 * ks + umma_k16_offset(n, kk) // 2]
+    ref = np.zeros((32, 32))
+    ref[:24, :24] = np.array(num, dtype=float).T
+    assert np.array_equal(B, ref)
+
+
 @pytest.mark.parametrize("process", ["ee_mumu", "gg_ttx", "gg_ttxg", "gg_ttxgg", "gg_ttxggg", "uux_epemg",
                                      "uux_epemgg", "uux_epemggg"])
 def test_line_sides_and_gram_denominators(orc, process):
