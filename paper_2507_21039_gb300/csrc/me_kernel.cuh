@@ -29,10 +29,26 @@ enum ExtKind : unsigned char { VIN = 0, VOUT = 1, FO_U = 2, FO_V = 3, FI_U = 4, 
 enum LineKind : unsigned char { L_EXT = 0, L_MASSLESS = 1, L_MASSIVE = 2 };
 
 // shared-memory bytes for E events of process P at precision T (+ J storage)
+// Straight-line kernel, per CTA of E events: FP64 momenta, external states
+// (and the Drell-Yan coefficients), lines; for T = float also the momenta split
+// into FP32 hi + lo and the FP64 Gram matrix of the FP32 setup (see below)
+template <class P, class T> __host__ __device__ constexpr size_t scalar_line_offset(int E)
+{
+    return (size_t)E * P::NPAR * 4 * sizeof(double) + (size_t)E * P::NEXT * sizeof(Wf<T>);
+}
+template <class P, class T> __host__ __device__ constexpr size_t scalar_pf_offset(int E)
+{
+    return (scalar_line_offset<P, T>(E) + (size_t)E * P::NLINES * sizeof(Ln<T>) + 15) / 16 * 16;
+}
+template <class P, class T> __host__ __device__ constexpr size_t scalar_gram_offset(int E)
+{
+    return scalar_pf_offset<P, T>(E) + (std::is_same<T, float>::value ? (size_t)E * P::NPAR * 4 * sizeof(float2) : 0);
+}
 template <class P, class T> __host__ __device__ constexpr size_t setup_bytes(int E)
 {
-    return (size_t)E * P::NPAR * 4 * sizeof(double) + (size_t)E * P::NEXT * sizeof(Wf<T>) +
-           (size_t)E * P::NLINES * sizeof(Ln<T>);
+    return (scalar_gram_offset<P, T>(E) +
+            (std::is_same<T, float>::value ? (size_t)E * (P::NPAR * (P::NPAR + 1) / 2) * sizeof(double) : 0) + 15) /
+           16 * 16;
 }
 
 // Single-diagram enhancement (the multi-channel weight of the paper's event
@@ -345,7 +361,11 @@ __global__ void __launch_bounds__(P::THREADS) me_kernel_scalar(LaunchArgs a)
 
     double* smom = reinterpret_cast<double*>(smem);
     Wf<T>* sext = reinterpret_cast<Wf<T>*>(smom + E * NPAR * 4);
-    Ln<T>* sln = reinterpret_cast<Ln<T>*>(sext + E * P::NEXT);
+    Ln<T>* sln = reinterpret_cast<Ln<T>*>(smem + scalar_line_offset<P, T>(E));
+    constexpr bool F32 = std::is_same<T, float>::value;
+    constexpr int NG = NPAR * (NPAR + 1) / 2;
+    float2* spf = reinterpret_cast<float2*>(smem + scalar_pf_offset<P, T>(E));
+    double* sgram = reinterpret_cast<double*>(smem + scalar_gram_offset<P, T>(E));
 
     // (a1) coalesced load of this CTA's momenta
     const double* g = a.mom + e0 * NPAR * 4;
@@ -358,17 +378,37 @@ __global__ void __launch_bounds__(P::THREADS) me_kernel_scalar(LaunchArgs a)
     }
     __syncthreads();
 
-    // (a2, a3 denominators) helicity-independent per-event data, FP64
+    // (a2, a3 denominators) helicity-independent per-event data: FP64 in FP64
+    // kernels; in FP32 kernels with lines, from the split momenta with FP64 only
+    // for the Gram matrix and the denominators (the FP32 setup of the table kernels)
     constexpr int PER = P::NEXT + NL;
-    for (int it = threadIdx.x; it < ne * PER; it += TH) {
-        const int ev = it / PER, j = it - ev * PER;
-        event_setup<P, T>(smom + ev * NPAR * 4, j, a.mt, a.gauge_ext, sext + ev * P::NEXT, sln + ev * NL);
+    if constexpr (F32 && NL > 0) {  // (without lines there is no denominator to protect)
+        constexpr int NA = 4 * NPAR + NG;
+        for (int it = threadIdx.x; it < ne * NA; it += TH) {
+            const int ev = it / NA, j = it - ev * NA;
+            split_or_gram<NPAR>(smom + ev * NPAR * 4, j, spf + ev * NPAR * 4, sgram + ev * NG);
+        }
+        __syncthreads();
+        const double m2 = a.mt * a.mt;
+        const float mtf = (float)a.mt;
+        for (int it = threadIdx.x; it < ne * PER; it += TH) {
+            const int ev = it / PER, j = it - ev * PER;
+            if (j < 2 * NPAR) sext[ev * P::NEXT + j] = ext_wavefunction_split<P>(spf + ev * NPAR * 4, j, mtf, a.gauge_ext);
+            else if (j < P::NEXT) sext[ev * P::NEXT + j] = ew_coefficients<T>(smom + ev * NPAR * 4);
+            else sln[ev * NL + j - P::NEXT] = line_data_split<P>(spf + ev * NPAR * 4, sgram + ev * NG, j - P::NEXT, m2);
+        }
+    } else {
+        for (int it = threadIdx.x; it < ne * PER; it += TH) {
+            const int ev = it / PER, j = it - ev * PER;
+            event_setup<P, T>(smom + ev * NPAR * 4, j, a.mt, a.gauge_ext, sext + ev * P::NEXT, sln + ev * NL);
+        }
     }
     __syncthreads();
 
     // (a3-a6) chain, colour sum, helicity accumulation
     const int ev = threadIdx.x / S, slot = threadIdx.x - ev * S;
     double acc = 0.0, snum = 0.0, sden = 0.0;
+    FSum facc{0.0f, 0.0f};  // FP32 kernels: compensated helicity sum, one conversion per event
     if (ev < ne) {
         const Wf<T>* ext = sext + ev * P::NEXT;
         const Ln<T>* ln = sln + ev * NL;
@@ -392,7 +432,8 @@ __global__ void __launch_bounds__(P::THREADS) me_kernel_scalar(LaunchArgs a)
                 P::template chain<T, SDE>(ext, hel, ln, (T)a.mt, J, sde);
                 v = colour_as<P, T, C>(J);
             }
-            acc += (double)v;
+            if constexpr (F32) facc = fsum_add(facc, FSum{(float)v, 0.0f});
+            else acc += (double)v;
             if constexpr (SDE) {
                 snum += (double)sde.num;
                 sden += (double)sde.den;
@@ -402,7 +443,12 @@ __global__ void __launch_bounds__(P::THREADS) me_kernel_scalar(LaunchArgs a)
     }
     // (a6) helicity sum: reduce over the S lanes of each event
     for (int off = S >> 1; off > 0; off >>= 1) {
-        acc += __shfl_xor_sync(0xffffffffu, acc, off);
+        if constexpr (F32) {
+            const FSum o{__shfl_xor_sync(0xffffffffu, facc.s, off), __shfl_xor_sync(0xffffffffu, facc.c, off)};
+            facc = fsum_add(facc, o);
+        } else {
+            acc += __shfl_xor_sync(0xffffffffu, acc, off);
+        }
         if constexpr (SDE) {
             snum += __shfl_xor_sync(0xffffffffu, snum, off);
             sden += __shfl_xor_sync(0xffffffffu, sden, off);
@@ -410,6 +456,7 @@ __global__ void __launch_bounds__(P::THREADS) me_kernel_scalar(LaunchArgs a)
     }
     // (a7) normalisation g^{2k} / (IDEN * colour denominator)
     if (ev < ne && slot == 0) {
+        if constexpr (F32) acc = (double)facc.s + (double)facc.c;
         a.me2[e0 + ev] = acc * a.norm * (a.w_ev ? a.w_ev[e0 + ev] : 1.0);
         if constexpr (SDE) a.sde_w[e0 + ev] = sden > 0.0 ? snum / sden : 0.0;
     }
