@@ -379,14 +379,22 @@ __global__ void __launch_bounds__(P::THREADS) me_kernel_scalar(LaunchArgs a)
     __syncthreads();
 
     // (a2, a3 denominators) helicity-independent per-event data: FP64 in FP64
-    // kernels; in FP32 kernels with lines, from the split momenta with FP64 only
-    // for the Gram matrix and the denominators (the FP32 setup of the table kernels)
+    // kernels; in FP32 kernels from the split momenta, with FP64 only for the Gram
+    // matrix and the line denominators (the FP32 setup of the table kernels)
     constexpr int PER = P::NEXT + NL;
-    if constexpr (F32 && NL > 0) {  // (without lines there is no denominator to protect)
-        constexpr int NA = 4 * NPAR + NG;
+    if constexpr (F32) {
+        // without lines there is no denominator to protect: the first phase then
+        // only rounds each momentum component to FP32, once per event rather than
+        // once per external state that reads it (conversions from FP64 issue on
+        // the FP64 pipe)
+        constexpr int NA = NL > 0 ? 4 * NPAR + NG : 4 * NPAR;
         for (int it = threadIdx.x; it < ne * NA; it += TH) {
-            const int ev = it / NA, j = it - ev * NA;
-            split_or_gram<NPAR>(smom + ev * NPAR * 4, j, spf + ev * NPAR * 4, sgram + ev * NG);
+            if constexpr (NL > 0) {
+                const int ev = it / NA, j = it - ev * NA;
+                split_or_gram<NPAR>(smom + ev * NPAR * 4, j, spf + ev * NPAR * 4, sgram + ev * NG);
+            } else {
+                spf[it] = make_float2(__double2float_rn(smom[it]), 0.0f);
+            }
         }
         __syncthreads();
         const double m2 = a.mt * a.mt;
