@@ -1,7 +1,8 @@
 // Staged, descriptor-driven |M|^2 kernel for the largest process
 // (arXiv:2507.21039 Sec. 3.1 chain, Sec. 4.1 colour sum, helicity sum).
 //
-// One CTA of NT threads per event, one helicity per thread.  The helicity-
+// One CTA per event, NT helicity slots (one thread each, or two threads each
+// when J lives in tensor memory: see below).  The helicity-
 // recycled table of off-shell objects (see me_kernel_tab.cuh) does not fit in
 // shared memory for seven external particles, so the generator cuts the
 // amplitudes into stages: each stage first computes, cooperatively and level by
@@ -22,7 +23,13 @@
 //     cores accumulate in FP32 in TMEM (columns 0-127 Re J, 128-255 Im J of the
 //     thread's lane): six tcgen05.mma (M = 128, N = 128, K = 16) per stage,
 //     issued by one thread after the CTA barrier that ends the stage.  J then
-//     needs no shared memory, so two CTAs share an SM.
+//     needs no shared memory, so two CTAs share an SM.  Each helicity has two
+//     threads (CTA of 2 NT): the generator splits every stage's amplitudes at
+//     a colour-group boundary into two halves of about equal cost; the second
+//     thread evaluates the later half and writes its group sums into the later
+//     columns of A.  The tensor memory (two CTAs x 256 columns) caps the events
+//     in flight per SM at two; the pairs double the warps that hide the
+//     latency of the amplitude chain.
 //   * FP32, build option ME_INTERP_J_MMA=0: in shared memory, updated flow by
 //     flow by each group's last member (one CTA per SM).
 //   * FP64: in a global scratch (L2-resident), updated flow by flow; its tables
@@ -38,6 +45,13 @@
 #ifndef ME_INTERP_J_MMA
 #define ME_INTERP_J_MMA 1
 #endif
+// Build option ME_INTERP_HPAIR: with J in tensor memory, two threads per
+// helicity share out each stage's amplitudes at a colour-group boundary (1,
+// default: twice the warps per SM for the same tensor memory) or one thread
+// evaluates them all (0)
+#ifndef ME_INTERP_HPAIR
+#define ME_INTERP_HPAIR 1
+#endif
 
 namespace me {
 
@@ -46,8 +60,11 @@ struct __align__(8) IRound {
     unsigned short ntask;
     unsigned char kind, barrier_after;
 };
-struct __align__(8) IStage {
+struct __align__(16) IStage {
     unsigned short round_begin, round_end, amp_begin, amp_end;
+    // two threads per helicity: the first evaluates [amp_begin, amp_mid), the
+    // second [amp_mid, amp_end) from group update slot_mid on (a group boundary)
+    unsigned short amp_mid, slot_mid, pad0, pad1;
 };
 struct __align__(16) IAmp {
     unsigned short op[4];
@@ -78,6 +95,11 @@ template <class P, class T> struct InterpLayout {
     static constexpr bool J_MMA = sizeof(T) == 4 && ME_INTERP_J_MMA;
     static constexpr bool J_IN_SMEM = sizeof(T) == 4 && !J_MMA;
     static constexpr uint32_t TMEM_COLS = 256;
+    // threads per CTA: one per helicity, or two with J in tensor memory (the
+    // second takes the later colour groups of each stage); register budget for
+    // two resident CTAs when J is in tensor memory
+    static constexpr int NTH = (J_MMA && ME_INTERP_HPAIR) ? 2 * P::NT : P::NT;
+    static constexpr int MIN_CTAS = J_MMA ? 2 : 1;
     // J_MMA operands: six A matrices (BF16 hi / mid / lo of Im G and Re G, 128 x 16
     // each) and the stage's sign matrix B (128 flows x 16), 4096 bytes each
     static constexpr size_t amat = (jsm + 1023) / 1024 * 1024;
@@ -128,9 +150,11 @@ __device__ __forceinline__ void bf16_split3(float x, __nv_bfloat16& hi, __nv_bfl
 
 // TC: colour sum on BF16 tensor cores (T = float); otherwise scalar in C
 template <class P, class T, bool TC, class C = T, bool SDE = false>
-__global__ void __launch_bounds__(P::NT) me_kernel_interp(LaunchArgs a, cx<T>* __restrict__ jglobal)
+__global__ void __launch_bounds__(InterpLayout<P, T>::NTH, InterpLayout<P, T>::MIN_CTAS)
+    me_kernel_interp(LaunchArgs a, cx<T>* __restrict__ jglobal)
 {
     using L = InterpLayout<P, T>;
+    constexpr int NTH = L::NTH;
     extern __shared__ __align__(1024) unsigned char smem[];
     constexpr int NPAR = P::NPAR, NL = P::NLINES, NT = P::NT, NCOL = P::NCOL;
     double* smom = reinterpret_cast<double*>(smem + L::mom);
@@ -142,9 +166,10 @@ __global__ void __launch_bounds__(P::NT) me_kernel_interp(LaunchArgs a, cx<T>* _
     cx<T>* jp = nullptr;
     if constexpr (L::J_IN_SMEM) jp = reinterpret_cast<cx<T>*>(smem + L::jsm) + threadIdx.x;
     else if constexpr (!L::J_MMA) jp = jglobal + (size_t)blockIdx.x * NCOL * NT + threadIdx.x;
-    __shared__ double red[NT / 32];
-    __shared__ FSum fred[NT / 32];
-    __shared__ double red_sde[SDE ? 2 : 1][NT / 32];
+    __shared__ double red[NTH / 32];
+    __shared__ FSum fred[NTH / 32];
+    __shared__ double red_sde[SDE ? 2 : 1][NTH / 32];
+    __shared__ unsigned char pair_nonfinite[NTH > NT ? NT : 1];  // second thread of a helicity: a group sum was not finite
     constexpr bool F32 = sizeof(T) == 4;
     float2* spf = reinterpret_cast<float2*>(smem + L::pf);
     double* sgram = reinterpret_cast<double*>(smem + L::gram);
@@ -154,7 +179,9 @@ __global__ void __launch_bounds__(P::NT) me_kernel_interp(LaunchArgs a, cx<T>* _
     __shared__ uint32_t tmem_base;
     __shared__ __align__(8) uint64_t mma_bar;
     const int tid = threadIdx.x;
-    const bool act = tid < a.nlist;
+    const int h = tid & (NT - 1);  // helicity slot (lane of J in tensor memory)
+    const int half = tid / NT;     // 1: the second thread of helicity h
+    const bool act = h < a.nlist;
     uint32_t tj = 0;
     uint32_t ncommit = 0;  // tensor-core commits so far (the same count in every thread)
     bool failed = false;   // a wait for the tensor cores ran out: this thread stops waiting
@@ -173,52 +200,53 @@ __global__ void __launch_bounds__(P::NT) me_kernel_interp(LaunchArgs a, cx<T>* _
         // operands start at zero: a slot no group of a stage uses is multiplied by
         // a zero column of B and must hold a finite value
         uint4* z = reinterpret_cast<uint4*>(smem + L::amat);
-        for (int i = tid; i < 7 * 4096 / 16; i += NT) z[i] = make_uint4(0u, 0u, 0u, 0u);
+        for (int i = tid; i < 7 * 4096 / 16; i += NTH) z[i] = make_uint4(0u, 0u, 0u, 0u);
         fence_proxy_async_smem();
         tmem_fence_before_sync();
         __syncthreads();
         tmem_fence_after_sync();
         tj = tmem_base + ((uint32_t)(32 * ((tid >> 5) & 3)) << 16);
     }
-    // compressed variant index of every operand support for helicity h
-    // (support particles in descending order = helicity bits from low to high)
-    auto variants = [&](int h) {
+    // compressed variant index of every operand support for helicity `hel`,
+    // stored at this thread's helicity slot h (support particles in descending
+    // order = helicity bits from low to high)
+    auto variants = [&](int hel) {
         for (int s = 0; s < P::NSUP; ++s) {
             const unsigned m = P::support_mask(s);
             unsigned v = 0, j = 0;
             for (int b = 0; b < NPAR; ++b)
-                if ((m >> b) & 1) v |= ((h >> b) & 1) << j++;
-            vsup[s * NT + tid] = (unsigned char)v;
+                if ((m >> b) & 1) v |= ((hel >> b) & 1) << j++;
+            vsup[s * NT + h] = (unsigned char)v;
         }
     };
-    if (!a.hel_ev) variants(a.hel_list[act ? tid : 0]);
+    if (!a.hel_ev && half == 0) variants(a.hel_list[act ? h : 0]);
     // wait for the tensor cores' commit number c (its mbarrier phase parity is c & 1)
     auto wait_commit = [&](uint32_t c) {
         if (!failed && !mbar_wait_bounded(&mma_bar, c & 1u, ME_WAIT_LIMIT_CYCLES)) failed = true;
     };
 
     for (long long e = blockIdx.x; e < a.nevt; e += gridDim.x) {
-        if (a.hel_ev) variants(a.hel_ev[e]);  // helicity sampling: one helicity per event (nlist = 1)
+        if (a.hel_ev && half == 0) variants(a.hel_ev[e]);  // helicity sampling: one helicity per event (nlist = 1)
         const double* g = a.mom + e * NPAR * 4;
-        for (int i = tid; i < NPAR * 4; i += NT) smom[i] = __ldg(g + i);
+        for (int i = tid; i < NPAR * 4; i += NTH) smom[i] = __ldg(g + i);
         if constexpr (!L::J_MMA) {
             for (int c = 0; c < NCOL; ++c) jp[c * NT] = {T(0), T(0)};
         }
         __syncthreads();
         if constexpr (F32) {  // split momenta and FP64 Gram matrix, then lines and external states in FP32
-            if constexpr (split_items_one_pass<NPAR, NT>()) {
+            if constexpr (split_items_one_pass<NPAR, NTH>()) {
                 const int it = split_item_of<NPAR>(tid);
                 if (it >= 0) split_or_gram<NPAR>(smom, it, spf, sgram);
             } else {
-                for (int it = tid; it < 4 * NPAR + Gram<NPAR>::N; it += NT) split_or_gram<NPAR>(smom, it, spf, sgram);
+                for (int it = tid; it < 4 * NPAR + Gram<NPAR>::N; it += NTH) split_or_gram<NPAR>(smom, it, spf, sgram);
             }
             __syncthreads();
-            for (int it = tid; it < NL + 2 * NPAR; it += NT) {
+            for (int it = tid; it < NL + 2 * NPAR; it += NTH) {
                 if (it < NL) sln[it] = line_data_split<P>(spf, sgram, it, m2);
                 else tab.st(it - NL, ext_wavefunction_split<P>(spf, it - NL, mtf, a.gauge_ext));
             }
         } else {
-            for (int it = tid; it < 2 * NPAR + NL; it += NT) {
+            for (int it = tid; it < 2 * NPAR + NL; it += NTH) {
                 if (it < 2 * NPAR) tab.st(it, ext_wavefunction<P, T>(smom, it, a.mt, a.gauge_ext));
                 else sln[it - 2 * NPAR] = line_data<P, T>(smom, it - 2 * NPAR, a.mt);
             }
@@ -231,28 +259,38 @@ __global__ void __launch_bounds__(P::NT) me_kernel_interp(LaunchArgs a, cx<T>* _
         // table rounds start at the warp after the previous round's last task, so
         // that the many small rounds spread over all warps instead of piling onto the
         // first ones (a warp still runs the tasks of one round only)
-        static_assert((NT & (NT - 1)) == 0 && NT % 32 == 0, "round rotation assumes a power-of-two CTA of whole warps");
+        static_assert((NTH & (NTH - 1)) == 0 && NT % 32 == 0, "round rotation assumes a power-of-two CTA of whole warps");
         int rot = 0;
         for (int s = 0; s < P::NSTAGE; ++s) {
             const IStage st = P::stage(s);
             for (int r = st.round_begin; r < st.round_end; ++r) {
                 const IRound rd = P::round(r);
-                for (int t = (tid - rot) & (NT - 1); t < rd.ntask; t += NT)
+                for (int t = (tid - rot) & (NTH - 1); t < rd.ntask; t += NTH)
                     run_task<T, P::TAB>(tab, sln, mt, rd.kind, ld_task(P::tasks() + rd.task_begin + t));
-                rot = (rot + ((rd.ntask + 31) & ~31)) & (NT - 1);
+                rot = (rot + ((rd.ntask + 31) & ~31)) & (NTH - 1);
                 if (rd.barrier_after) __syncthreads();
             }
             __syncthreads();
             int term = P::stage_term_begin(s);
             int slot = 0;  // J_MMA: the stage's next group update (column of A)
+            // this thread's amplitudes of the stage: all of them, or one side of the
+            // stage's split between the two threads of a helicity
+            int amp_lo = st.amp_begin, amp_hi = st.amp_end;
+            if constexpr (NTH > NT) {
+                if (half == 0) {
+                    amp_hi = st.amp_mid;
+                } else {
+                    amp_lo = st.amp_mid;
+                    slot = st.slot_mid;
+                }
+            }
             if constexpr (L::J_MMA) {
                 // the previous stage's tensor-core work has read A and B: they may be rewritten;
                 // this stage's sign matrix is copied in while the amplitudes are evaluated
                 if (ncommit > 0) wait_commit(ncommit - 1);
                 const uint4* bsrc = P::bmat(s);
                 uint4* bsm = reinterpret_cast<uint4*>(smem + L::bmat);
-                cp_async16(bsm + tid, bsrc + tid);
-                cp_async16(bsm + tid + NT, bsrc + tid + NT);
+                for (int i = tid; i < 256; i += NTH) cp_async16(bsm + i, bsrc + i);
                 cp_async_commit();
             }
             // software pipeline: the descriptor and the first three operands of the
@@ -263,15 +301,15 @@ __global__ void __launch_bounds__(P::NT) me_kernel_interp(LaunchArgs a, cx<T>* _
             Wf<T> p0, p1, p2;
             auto fetch = [&](int ai) {
                 dn = P::amp(ai);
-                p0 = tab.ld(dn.op[0] + vsup[dn.sup[0] * NT + tid]);
-                p1 = tab.ld(dn.op[1] + vsup[dn.sup[1] * NT + tid]);
-                p2 = tab.ld(dn.op[2] + vsup[dn.sup[2] * NT + tid]);
+                p0 = tab.ld(dn.op[0] + vsup[dn.sup[0] * NT + h]);
+                p1 = tab.ld(dn.op[1] + vsup[dn.sup[1] * NT + h]);
+                p2 = tab.ld(dn.op[2] + vsup[dn.sup[2] * NT + h]);
             };
-            if (st.amp_begin < st.amp_end) fetch(st.amp_begin);
-            for (int ai = st.amp_begin; ai < st.amp_end; ++ai) {
+            if (amp_lo < amp_hi) fetch(amp_lo);
+            for (int ai = amp_lo; ai < amp_hi; ++ai) {
                 const IAmp d = dn;
                 const Wf<T> w0 = p0, w1 = p1, w2 = p2;
-                if (ai + 1 < st.amp_end) fetch(ai + 1);
+                if (ai + 1 < amp_hi) fetch(ai + 1);
                 const int kind = d.kind & 0x3f;
                 cx<T> x;
                 if (kind == A_DOTV) {           // amputated: two-operand contractions
@@ -283,7 +321,7 @@ __global__ void __launch_bounds__(P::NT) me_kernel_interp(LaunchArgs a, cx<T>* _
                     case A_FFV1_0: x = FFV1_0<T>(w0, w1, w2); break;
                     case A_VVV1_0: x = VVV1_0<T>(w0, sln[d.la].p, w1, sln[d.lb].p, w2); break;
                     default: {
-                        const Wf<T> w3 = tab.ld(d.op[3] + vsup[d.sup[3] * NT + tid]);
+                        const Wf<T> w3 = tab.ld(d.op[3] + vsup[d.sup[3] * NT + h]);
                         x = kind == A_VVVV1_0 ? VVVV1_0<T>(w0, w1, w2, w3)
                           : kind == A_VVVV3_0 ? VVVV3_0<T>(w0, w1, w2, w3) : VVVV4_0<T>(w0, w1, w2, w3);
                     }
@@ -308,7 +346,7 @@ __global__ void __launch_bounds__(P::NT) me_kernel_interp(LaunchArgs a, cx<T>* _
                         __nv_bfloat16 q[6];
                         bf16_split3(gi, q[0], q[1], q[2]);
                         bf16_split3(gr, q[3], q[4], q[5]);
-                        const uint32_t off = umma_k16_offset(tid, slot);
+                        const uint32_t off = umma_k16_offset(h, slot);
 #pragma unroll
                         for (int m = 0; m < 6; ++m)
                             *reinterpret_cast<__nv_bfloat16*>(smem + L::amat + (size_t)m * 4096 + off) = q[m];
@@ -368,6 +406,10 @@ __global__ void __launch_bounds__(P::NT) me_kernel_interp(LaunchArgs a, cx<T>* _
         if constexpr (L::J_MMA) {
             wait_commit(ncommit - 1);  // this event's last tensor-core update is in J
             tmem_fence_after_sync();
+            if constexpr (NTH > NT) {
+                if (half) pair_nonfinite[h] = nonfinite ? 1 : 0;  // read after the barriers below
+            }
+            // warps 0-3 (lanes 0-127 of tensor memory) form the colour sum
             const int w = tid >> 5, lane = tid & 31;
             unsigned char* stage = smem + L::table + (size_t)(w & 1) * L::WJ;
             cx<float>* js = reinterpret_cast<cx<float>*>(stage);
@@ -390,6 +432,9 @@ __global__ void __launch_bounds__(P::NT) me_kernel_interp(LaunchArgs a, cx<T>* _
                 }
                 __syncthreads();
             }
+            if constexpr (NTH > NT) {
+                if (!half && pair_nonfinite[h]) nonfinite = true;
+            }
             if (nonfinite || failed) v = T(NAN);
         } else if constexpr (TC) {
             v = colour_tc_smem<NCOL, NT, P::NSPLIT>(reinterpret_cast<const cx<float>*>(smem + L::jsm), P::bfrag(),
@@ -400,13 +445,15 @@ __global__ void __launch_bounds__(P::NT) me_kernel_interp(LaunchArgs a, cx<T>* _
         double acc = 0.0, dn = 0.0, dd = 0.0;
         FSum facc{0.0f, 0.0f};
         if (act) {
-            if constexpr (F32) facc.s = (float)v;
-            else acc = (double)v;
-            if constexpr (SDE) {
+            if (half == 0) {  // (the second thread of a helicity holds no colour sum)
+                if constexpr (F32) facc.s = (float)v;
+                else acc = (double)v;
+                if (a.hel_out) a.hel_out[e * a.nlist + h] = (double)v * a.norm;
+            }
+            if constexpr (SDE) {  // both threads of a helicity: their own amplitudes
                 dn = (double)snum;
                 dd = (double)sden;
             }
-            if (a.hel_out) a.hel_out[e * a.nlist + tid] = (double)v * a.norm;
         }
         if constexpr (F32) facc = fsum_warp(facc);
         for (int off = 16; off > 0; off >>= 1) {
@@ -429,10 +476,10 @@ __global__ void __launch_bounds__(P::NT) me_kernel_interp(LaunchArgs a, cx<T>* _
             double s = 0.0, sn = 0.0, sd = 0.0;
             if constexpr (F32) {  // one conversion per event
                 FSum f = fred[0];
-                for (int w = 1; w < NT / 32; ++w) f = fsum_add(f, fred[w]);
+                for (int w = 1; w < NTH / 32; ++w) f = fsum_add(f, fred[w]);
                 s = (double)f.s + (double)f.c;
             }
-            for (int w = 0; w < NT / 32; ++w) {
+            for (int w = 0; w < NTH / 32; ++w) {
                 if constexpr (!F32) s += red[w];
                 if constexpr (SDE) {
                     sn += red_sde[0][w];
@@ -487,13 +534,13 @@ template <class P, class T, bool TC, class C, bool SDE> cudaError_t interp_resid
     per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, me_kernel_interp<P, T, TC, C, SDE>, P::NT,
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, me_kernel_interp<P, T, TC, C, SDE>, L::NTH,
                                                       L::launch_bytes) != cudaSuccess ||
         per_sm < 1) {
         cudaGetLastError();
         per_sm = 1;
     }
-    if constexpr (L::J_MMA) per_sm = tmem_kernel_ctas_per_sm(me_kernel_interp<P, T, TC, C, SDE>, L::launch_bytes, P::NT,
+    if constexpr (L::J_MMA) per_sm = tmem_kernel_ctas_per_sm(me_kernel_interp<P, T, TC, C, SDE>, L::launch_bytes, L::NTH,
                                                              L::TMEM_COLS);
     return cudaSuccess;
 }
@@ -532,7 +579,7 @@ template <class P, class T, bool TC = false, class C = T, bool SDE = false> cuda
             own = true;
         }
     }
-    me_kernel_interp<P, T, TC, C, SDE><<<(unsigned)grid, P::NT, L::launch_bytes, a.stream>>>(a, jg);
+    me_kernel_interp<P, T, TC, C, SDE><<<(unsigned)grid, L::NTH, L::launch_bytes, a.stream>>>(a, jg);
     e = cudaGetLastError();
     if (own) cudaFreeAsync(jg, a.stream);
     return e;

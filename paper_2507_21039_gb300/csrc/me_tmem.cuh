@@ -215,7 +215,7 @@ template <class K> int tmem_kernel_ctas_per_sm(K kernel, size_t dyn_smem, int th
     const int by_smem = (int)((size_t)smem_sm / (dyn_smem + fa.sharedSizeBytes + (size_t)reserved));
     const int regs = (fa.numRegs + 7) / 8 * 8;
     const int by_regs = 65536 / (regs * threads);
-    return std::max(1, std::min({by_smem, by_regs, 512 / tmem_cols}));
+    return std::max(1, std::min({by_smem, by_regs, 2048 / threads, 512 / tmem_cols}));
 }
 
 }  // namespace me

@@ -803,7 +803,7 @@ def emit_interp_struct(process: str, nt: int, stage_amps: int, num, mode: int = 
                 assert col < 128
                 img[umma_k16_offset(col, k) // 2] = 0x3F80 if c == (0, -1) else 0xBF80
         bmat += [img[i] | (img[i + 1] << 16) for i in range(0, 2048, 2)]
-        stages.append((r0, len(rounds), a0, len(amps)))
+        stages.append((r0, len(rounds), a0, len(amps), a0 + st.mid, st.slot_mid))
     masks = []
     for S in I.supports:
         m = 0
@@ -818,7 +818,7 @@ def emit_interp_struct(process: str, nt: int, stage_amps: int, num, mode: int = 
     # fit its 64 KB (uniform reads through the constant cache), for the first
     # struct of the unit only; per-thread data (table tasks) stays in global memory
     uniform = ("c_rounds", "c_stages", "c_amps", "c_terms", "c_stage_term", "c_diag")
-    cbytes = 8 * len(rounds) + 8 * len(stages) + 16 * len(amps) + 2 * len(terms) + 4 * len(stage_term) + 2 * len(diags)
+    cbytes = 8 * len(rounds) + 16 * len(stages) + 16 * len(amps) + 2 * len(terms) + 4 * len(stage_term) + 2 * len(diags)
     use_const = CONST_DESCRIPTORS and not prefix and cbytes <= 60 * 1024
 
     def arr(aname, ctype, rows, fmt, per_line=6):
@@ -832,7 +832,7 @@ def emit_interp_struct(process: str, nt: int, stage_amps: int, num, mode: int = 
     src = ""
     src += arr("c_itasks", "TabTask", tasks, lambda t: "{%d, %d, %d, %d, %d, %d, %d, 0, 0}" % t, 4)
     src += arr("c_rounds", "IRound", rounds, lambda r: "{%du, %d, %d, %d}" % r, 8)
-    src += arr("c_stages", "IStage", stages, lambda r: "{%d, %d, %d, %d}" % r, 8)
+    src += arr("c_stages", "IStage", stages, lambda r: "{%d, %d, %d, %d, %d, %d, 0, 0}" % r, 4)
     src += arr("c_amps", "IAmp", amps, lambda a: "{{%d, %d, %d, %d}, {%d, %d, %d, %d}, %d, %d, %d, %d}" % (
         *a[0], *a[1], a[2], a[3], a[4], a[5]), 3)
     src += arr("c_terms", "unsigned short", terms, lambda x: "%d" % x, 16)

@@ -32,6 +32,11 @@ class Stage:
     rounds: list = field(default_factory=list)     # (kind, [task tuples]) with a barrier between levels
     barriers: list = field(default_factory=list)   # round indices after which a barrier is needed
     amps: list = field(default_factory=list)       # amplitude indices (into plan.amps)
+    # split of the amplitudes between the two threads of a helicity (kernels that
+    # run two threads per helicity): the first takes amps[:mid], the second
+    # amps[mid:]; mid falls on a colour-group boundary, slot_mid = groups before it
+    mid: int = 0
+    slot_mid: int = 0
 
 
 @dataclass
@@ -77,6 +82,28 @@ class _Arena:
         self.free = merged
 
 
+# issue cost of closing a colour group (the BF16 split of G and its operand
+# stores), in the units of FLOPS, for balancing the halves of a stage
+FLUSH_COST = 24
+
+
+def _split_amplitudes(ops, amps, stage_amps, flush):
+    """Split point of a stage's amplitude list at a colour-group boundary that
+    balances the two halves' cost (amplitude flops + group closings); returns
+    (mid, groups before mid)."""
+    cost = [FLOPS[ops[amps[a][0]].kind] + (FLUSH_COST if a in flush else 0) for a in stage_amps]
+    total = sum(cost)
+    best, acc, groups = (total, 0, 0), 0, 0
+    for i, a in enumerate(stage_amps):
+        acc += cost[i]
+        if a in flush:
+            groups += 1
+            key = max(acc, total - acc)
+            if key < best[0]:
+                best = (key, i + 1, groups)
+    return best[1], best[2]
+
+
 def build_interp(process: str, stage_amps: int = 48, amputated: bool = False, group: bool = True) -> InterpPlan:
     T = build_tabplan(process, amputated)
     P = T.plan
@@ -107,22 +134,27 @@ def build_interp(process: str, stage_amps: int = 48, amputated: bool = False, gr
         group_terms = [tuple(P.amps[a][1]) for a in range(len(P.amps))]
         members = [[a] for a in range(len(P.amps))]
     unit_deps = [set().union(*(amp_deps[a] for a in m)) for m in members]
-    live, order, remaining = set(), [], set(range(len(members)))
+    live, order, units, remaining = set(), [], [], set(range(len(members)))
     while remaining:
         best = min(remaining, key=lambda g: (sum(size[o] for o in unit_deps[g] - live), members[g][0]))
         order += members[best]
+        units.append(members[best])
         remaining.remove(best)
         live |= unit_deps[best]
     # the last member of each group carries the group's colour terms
     flush = {members[g][-1]: group_terms[g] for g in range(len(members))}
 
-    # stages and lifetimes
-    stage_of_amp = {}
+    # stages of at most stage_amps amplitudes, cut between colour groups (a group
+    # sum never stays open across a stage, so the amplitudes of a stage can be
+    # shared out between threads at any group boundary)
     stages = []
-    for k in range(0, len(order), stage_amps):
-        stages.append(Stage(amps=order[k:k + stage_amps]))
-        for a in order[k:k + stage_amps]:
-            stage_of_amp[a] = len(stages) - 1
+    for u in units:
+        assert len(u) <= stage_amps, "a colour group larger than a stage"
+        if not stages or len(stages[-1].amps) + len(u) > stage_amps:
+            stages.append(Stage())
+        stages[-1].amps += u
+    for st in stages:
+        st.mid, st.slot_mid = _split_amplitudes(ops, P.amps, st.amps, flush)
     first, last = {}, {}
     computed = set()
     for si, st in enumerate(stages):

@@ -187,7 +187,7 @@ def test_descriptor_kernel_reads_its_descriptors_from_constant_memory():
     src, _ = emit_interp_struct("gg_ttxggg", nt, sf, colour_matrix(5)[0], mf)
     for name in ("c_amps", "c_terms", "c_rounds", "c_stages", "c_stage_term", "c_diag"):
         assert re.search(r"__constant__ \w+( \w+)? " + name + r"\[", src), name
-    sizes = {"IAmp": 16, "IRound": 8, "IStage": 8, "unsigned short": 2, "int": 4}
+    sizes = {"IAmp": 16, "IRound": 8, "IStage": 16, "unsigned short": 2, "int": 4}
     total = 0
     for ctype, name, n in re.findall(r"__constant__ ([\w ]+?) (c_\w+)\[(\d+)\]", src):
         total += sizes[ctype] * int(n)
@@ -219,6 +219,37 @@ def test_interpreter_descriptors_encode_the_colour_groups():
             assert terms[t] == col | (0x8000 if c == (0, -1) else 0)
             t += 1
     assert t == len(terms)
+
+
+def test_stage_split_between_the_threads_of_a_helicity():
+    """The FP32 descriptor kernel runs two threads per helicity; each stage's
+    amplitudes are shared out at a colour-group boundary.  Every stage closes
+    all its groups (no group sum stays open across a stage), the split point
+    lies on a group boundary, the second thread's first update slot counts the
+    groups before it, the halves are balanced to within the largest group, and
+    the emitted stage descriptors carry the split."""
+    from paper_2507_21039_gb300.gen.emit import INTERP_PROCESSES, emit_interp_struct
+    from paper_2507_21039_gb300.gen.interp import FLOPS, FLUSH_COST
+
+    nt, sf, mf, _, _ = INTERP_PROCESSES["gg_ttxggg"]
+    src, I = emit_interp_struct("gg_ttxggg", nt, sf, colour_matrix(5)[0], mf)
+    P = I.tab.plan
+    body = re.search(r"c_stages\[\d+\] = \{(.*?)\n\};", src, re.S).group(1)
+    rows = [tuple(int(x) for x in r) for r in re.findall(r"\{(\d+), (\d+), (\d+), (\d+), (\d+), (\d+), 0, 0\}", body)]
+    assert len(rows) == len(I.stages)
+    a0 = 0
+    for st, row in zip(I.stages, rows):
+        amps = st.amps
+        assert 0 < len(amps) <= sf and amps[-1] in I.flush
+        assert st.mid == 0 or amps[st.mid - 1] in I.flush
+        assert st.slot_mid == sum(1 for a in amps[:st.mid] if a in I.flush)
+        assert row[2:] == (a0, a0 + len(amps), a0 + st.mid, st.slot_mid)
+        cost = [FLOPS[P.ops[P.amps[a][0]].kind] + (FLUSH_COST if a in I.flush else 0) for a in amps]
+        ends = [i + 1 for i, a in enumerate(amps) if a in I.flush]
+        best = min(max(sum(cost[:m]), sum(cost[m:])) for m in ends)
+        assert max(sum(cost[:st.mid]), sum(cost[st.mid:])) == min(best, sum(cost))
+        a0 += len(amps)
+    assert a0 == len(P.amps)
 
 
 def test_stage_sign_matrices_replay_the_flow_updates():
