@@ -110,7 +110,7 @@ def build(force: bool = False, verbose: bool = False, jobs: int | None = None) -
     os.makedirs(OBJ, exist_ok=True)
     stamp = os.path.join(BUILD, "stamp")
     dig = (_digest(_inputs()) + ",".join(PROCESSES) + os.environ.get("ME_GEN_KERNEL", "") + " ".join(_extra_flags())
-           + os.environ.get("ME_INTERP_CONST", ""))
+           + os.environ.get("ME_INTERP_CONST", "") + os.environ.get("ME_SCALAR_MIN_CTAS", ""))
     if not force and os.path.exists(LIB) and os.path.exists(stamp) and open(stamp).read() == dig:
         return LIB
     gen_srcs = generate()

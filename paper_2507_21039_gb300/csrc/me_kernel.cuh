@@ -350,7 +350,8 @@ template <class P, class T, class C, class JT> __device__ __forceinline__ T colo
 
 // Scalar colour contraction and helicity sum.  T: chain precision, C: colour.
 template <class P, class T, class C = T, bool SDE = false>
-__global__ void __launch_bounds__(P::THREADS) me_kernel_scalar(LaunchArgs a)
+__global__ void __launch_bounds__(P::THREADS, std::is_same<T, float>::value ? P::MIN_CTAS_F : 1)
+    me_kernel_scalar(LaunchArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     constexpr int NPAR = P::NPAR, NL = P::NLINES, TH = P::THREADS;

@@ -52,6 +52,12 @@
 #ifndef ME_INTERP_HPAIR
 #define ME_INTERP_HPAIR 1
 #endif
+// Build option ME_INTERP_A_MMAJOR: the group-sum operands A in the M-major
+// layout (1, default: a warp's 32 rows of one column on distinct banks) or
+// K-major (0: the four row groups of a warp on the same banks, 4-way conflicts)
+#ifndef ME_INTERP_A_MMAJOR
+#define ME_INTERP_A_MMAJOR 1
+#endif
 
 namespace me {
 
@@ -101,9 +107,12 @@ template <class P, class T> struct InterpLayout {
     static constexpr int NTH = (J_MMA && ME_INTERP_HPAIR) ? 2 * P::NT : P::NT;
     static constexpr int MIN_CTAS = J_MMA ? 2 : 1;
     // J_MMA operands: six A matrices (BF16 hi / mid / lo of Im G and Re G, 128 x 16
-    // each) and the stage's sign matrix B (128 flows x 16), 4096 bytes each
+    // each, ABYTES apart) and the stage's sign matrix B (128 flows x 16, 4096 bytes)
+    static constexpr bool A_MMAJOR = ME_INTERP_A_MMAJOR != 0;
+    static constexpr size_t ABYTES = A_MMAJOR ? kUmmaMn16Bytes : 4096;
+    static constexpr uint32_t A_LBO = 128, A_SBO = A_MMAJOR ? kUmmaMn16Sbo : 256;
     static constexpr size_t amat = (jsm + 1023) / 1024 * 1024;
-    static constexpr size_t bmat = amat + 6 * 4096;
+    static constexpr size_t bmat = amat + 6 * ABYTES;
     static constexpr size_t bytes = J_MMA ? bmat + 4096
                                           : jsm + (J_IN_SMEM ? (size_t)P::NCOL * P::NT * sizeof(cx<T>) : 0);
     // colour sum from TMEM: per warp, J as [flow][lane] FP32 and 32 floats of row
@@ -200,7 +209,7 @@ __global__ void __launch_bounds__(InterpLayout<P, T>::NTH, InterpLayout<P, T>::M
         // operands start at zero: a slot no group of a stage uses is multiplied by
         // a zero column of B and must hold a finite value
         uint4* z = reinterpret_cast<uint4*>(smem + L::amat);
-        for (int i = tid; i < 7 * 4096 / 16; i += NTH) z[i] = make_uint4(0u, 0u, 0u, 0u);
+        for (int i = tid; i < (int)((6 * L::ABYTES + 4096) / 16); i += NTH) z[i] = make_uint4(0u, 0u, 0u, 0u);
         fence_proxy_async_smem();
         tmem_fence_before_sync();
         __syncthreads();
@@ -346,10 +355,10 @@ __global__ void __launch_bounds__(InterpLayout<P, T>::NTH, InterpLayout<P, T>::M
                         __nv_bfloat16 q[6];
                         bf16_split3(gi, q[0], q[1], q[2]);
                         bf16_split3(gr, q[3], q[4], q[5]);
-                        const uint32_t off = umma_k16_offset(h, slot);
+                        const uint32_t off = L::A_MMAJOR ? umma_mn16_offset(h, slot) : umma_k16_offset(h, slot);
 #pragma unroll
                         for (int m = 0; m < 6; ++m)
-                            *reinterpret_cast<__nv_bfloat16*>(smem + L::amat + (size_t)m * 4096 + off) = q[m];
+                            *reinterpret_cast<__nv_bfloat16*>(smem + L::amat + (size_t)m * L::ABYTES + off) = q[m];
                         ++slot;
                         term += d.nterm;
                     } else {
@@ -372,14 +381,16 @@ __global__ void __launch_bounds__(InterpLayout<P, T>::NTH, InterpLayout<P, T>::M
                 if (tid == 0 && !failed) {
                     tmem_fence_after_sync();
                     const uint64_t bdesc = umma_smem_desc(smem + L::bmat, 128, 256);
-                    constexpr uint32_t ID_POS = umma_idesc_bf16_f32(128, 128, false);
-                    constexpr uint32_t ID_NEG = umma_idesc_bf16_f32(128, 128, true);
+                    constexpr uint32_t ID_POS = umma_idesc_bf16_f32(128, 128, false, L::A_MMAJOR);
+                    constexpr uint32_t ID_NEG = umma_idesc_bf16_f32(128, 128, true, L::A_MMAJOR);
 #pragma unroll
                     for (int m = 0; m < 3; ++m) {  // the first update of an event overwrites J
                         const bool acc = s > 0 || m > 0;
-                        umma_bf16(tmem_base, umma_smem_desc(smem + L::amat + (size_t)m * 4096, 128, 256), bdesc, ID_POS, acc);
-                        umma_bf16(tmem_base + 128, umma_smem_desc(smem + L::amat + (size_t)(3 + m) * 4096, 128, 256),
-                                  bdesc, ID_NEG, acc);
+                        umma_bf16(tmem_base, umma_smem_desc(smem + L::amat + (size_t)m * L::ABYTES, L::A_LBO, L::A_SBO),
+                                  bdesc, ID_POS, acc);
+                        umma_bf16(tmem_base + 128,
+                                  umma_smem_desc(smem + L::amat + (size_t)(3 + m) * L::ABYTES, L::A_LBO, L::A_SBO), bdesc,
+                                  ID_NEG, acc);
                     }
                     umma_commit(&mma_bar);
                 }

@@ -114,6 +114,25 @@ __host__ __device__ constexpr uint32_t umma_k16_offset(int row, int k)
     return (uint32_t)((row >> 3) * 256 + (k >> 3) * 128 + (row & 7) * 16 + (k & 7) * 2);
 }
 
+// M-major (MN-major) K = 16 operand for an M = 128 A written one element per
+// thread and column: the 8 consecutive rows of a K row form 16 contiguous bytes,
+// the 8 K rows of a core matrix follow at 16-byte pitch (128 bytes), the two K
+// groups at LBO = 128 and the 16 row groups at SBO = 272.  The 16 bytes of
+// padding per row group put the four row groups a warp writes for one column on
+// different banks (with SBO = 256 they would share the same four).  Element
+// (row, k) is at byte (row / 8) * 272 + (k / 8) * 128 + (k % 8) * 16 + (row % 8) * 2,
+// inside 16 * 272 = 4352 bytes; read with strides 128 and 272 in either role
+// every access stays inside them.
+constexpr uint32_t kUmmaMn16Sbo = 272, kUmmaMn16Bytes = 16 * kUmmaMn16Sbo;
+__host__ __device__ constexpr uint32_t umma_mn16_offset(int row, int k)
+{
+    return (uint32_t)((row >> 3) * kUmmaMn16Sbo + (k >> 3) * 128 + (k & 7) * 16 + (row & 7) * 2);
+}
+static_assert(umma_mn16_offset(1, 0) == 2 && umma_mn16_offset(0, 1) == 16 && umma_mn16_offset(0, 8) == 128 &&
+                  umma_mn16_offset(8, 0) == 272 && umma_mn16_offset(127, 15) + 2 <= kUmmaMn16Bytes,
+              "M-major operand layout");
+static_assert(15 * 128 + 272 + 128 <= kUmmaMn16Bytes, "strides read in swapped roles stay inside the operand");
+
 // shared-memory matrix descriptor: start address, leading-dimension (K)
 // byte offset, stride-dimension (M/N) byte offset, each in 16-byte units;
 // bit 46 set (descriptor version of the sm_100 family); no swizzle, base offset 0
@@ -125,12 +144,13 @@ __device__ __forceinline__ uint64_t umma_smem_desc(const void* smem_ptr, uint32_
 }
 
 // instruction descriptor of kind::f16: FP32 accumulator (bits 4-5 = 1), BF16 A
-// and B (bits 7-9, 10-12 = 1), B optionally negated (bit 14), both K-major
-// (bits 15, 16 = 0), N / 8 at bits 17-22, M / 16 at bits 24-28
-__host__ __device__ constexpr uint32_t umma_idesc_bf16_f32(int m, int n, bool neg_b)
+// and B (bits 7-9, 10-12 = 1), B optionally negated (bit 14), A K-major or
+// M-major (bit 15 = 0 / 1), B K-major (bit 16 = 0), N / 8 at bits 17-22,
+// M / 16 at bits 24-28
+__host__ __device__ constexpr uint32_t umma_idesc_bf16_f32(int m, int n, bool neg_b, bool a_m_major = false)
 {
-    return (1u << 4) | (1u << 7) | (1u << 10) | (neg_b ? (1u << 14) : 0u) | ((uint32_t)(n >> 3) << 17) |
-           ((uint32_t)(m >> 4) << 24);
+    return (1u << 4) | (1u << 7) | (1u << 10) | (neg_b ? (1u << 14) : 0u) | (a_m_major ? (1u << 15) : 0u) |
+           ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
 }
 
 // D[tmem] (+)= A * B for one M x N x 16 step, issued by a single thread;

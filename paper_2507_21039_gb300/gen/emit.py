@@ -35,6 +35,27 @@ TAB_PROCESSES = {"gg_ttxg": (32, 1, 1, 1, 0, 1, 4), "gg_ttxgg": (64, 2, 2, 5, 60
 INTERP_PROCESSES = {"gg_ttxggg": (128, 16, 0, 16, 0)}
 
 
+# FP32 straight-line kernels whose chain would otherwise hold more registers
+# than leave room for latency hiding: minimum resident CTAs of 128 threads per
+# SM (the register cap is 65536 / (128 x n)); build option
+# ME_SCALAR_MIN_CTAS="proc=n,..." overrides.  Measured on GB300, |M|^2 kernel
+# per 2^20 events: u u~ -> e+ e- g g uncapped 221 registers (2 CTAs) 6.21 ms,
+# 3 CTAs 4.70, 4 CTAs 4.11, 5 CTAs 3.95, 6 CTAs (80 registers, 624 bytes
+# spilled) 3.92; u u~ -> e+ e- g (146 registers) 1.91 ms uncapped, 2.01 at 4
+# CTAs; u u~ -> e+ e- g g g (255 registers) 5.05 ms per 2^18 uncapped, 8.69 at
+# 3 CTAs.
+SCALAR_MIN_CTAS_F = {"uux_epemgg": 6}
+
+
+def _scalar_min_ctas(process: str) -> int:
+    env = __import__("os").environ.get("ME_SCALAR_MIN_CTAS", "")
+    for item in filter(None, env.split(",")):
+        name, _, n = item.partition("=")
+        if name == process:
+            return int(n)
+    return SCALAR_MIN_CTAS_F.get(process, 1)
+
+
 def _apply_kernel_overrides():
     """Build option ME_GEN_KERNEL="proc=interp:NT:STAGE,proc=tab:NT,..." selects
     the kernel family of a process (used to compare kernel designs)."""
@@ -370,6 +391,8 @@ struct Proc {{
     // most terms of a line momentum written over its shorter side (line_side)
     static constexpr int SIDE = {max(side_max, 1)};
     static constexpr bool J_SMEM = {"true" if j_smem else "false"};
+    // FP32 straight-line kernel: at least this many resident CTAs per SM (register cap)
+    static constexpr int MIN_CTAS_F = {_scalar_min_ctas(process)};
     static constexpr bool IS_TAB = false, IS_INTERP = false;{tc_members}
     __device__ static __forceinline__ unsigned ext_kind(int e) {{ return c_ext_kind[e]; }}
     __device__ static __forceinline__ unsigned ext_massive(int e) {{ return c_ext_massive[e]; }}
