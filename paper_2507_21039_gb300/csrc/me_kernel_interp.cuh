@@ -70,7 +70,10 @@ struct __align__(16) IStage {
     unsigned short round_begin, round_end, amp_begin, amp_end;
     // two threads per helicity: the first evaluates [amp_begin, amp_mid), the
     // second [amp_mid, amp_end) from group update slot_mid on (a group boundary)
-    unsigned short amp_mid, slot_mid, pad0, pad1;
+    unsigned short amp_mid, slot_mid;
+    // 1: the stage's table rounds run beside the previous stage's amplitudes
+    // (their slots are not read there); 0: in a phase of their own
+    unsigned short ahead, pad;
 };
 struct __align__(16) IAmp {
     unsigned short op[4];
@@ -270,16 +273,22 @@ __global__ void __launch_bounds__(InterpLayout<P, T>::NTH, InterpLayout<P, T>::M
         // first ones (a warp still runs the tasks of one round only)
         static_assert((NTH & (NTH - 1)) == 0 && NT % 32 == 0, "round rotation assumes a power-of-two CTA of whole warps");
         int rot = 0;
-        for (int s = 0; s < P::NSTAGE; ++s) {
-            const IStage st = P::stage(s);
-            for (int r = st.round_begin; r < st.round_end; ++r) {
+        auto table_rounds = [&](int ts) {  // the table objects that become live in stage ts
+            const IStage tst = P::stage(ts);
+            for (int r = tst.round_begin; r < tst.round_end; ++r) {
                 const IRound rd = P::round(r);
                 for (int t = (tid - rot) & (NTH - 1); t < rd.ntask; t += NTH)
                     run_task<T, P::TAB>(tab, sln, mt, rd.kind, ld_task(P::tasks() + rd.task_begin + t));
                 rot = (rot + ((rd.ntask + 31) & ~31)) & (NTH - 1);
                 if (rd.barrier_after) __syncthreads();
             }
-            __syncthreads();
+        };
+        for (int s = 0; s < P::NSTAGE; ++s) {
+            const IStage st = P::stage(s);
+            if (!(P::TABLE_AHEAD && st.ahead)) {  // a phase of their own (always for the first stage)
+                table_rounds(s);
+                __syncthreads();
+            }
             int term = P::stage_term_begin(s);
             int slot = 0;  // J_MMA: the stage's next group update (column of A)
             // this thread's amplitudes of the stage: all of them, or one side of the
@@ -301,6 +310,11 @@ __global__ void __launch_bounds__(InterpLayout<P, T>::NTH, InterpLayout<P, T>::M
                 uint4* bsm = reinterpret_cast<uint4*>(smem + L::bmat);
                 for (int i = tid; i < 256; i += NTH) cp_async16(bsm + i, bsrc + i);
                 cp_async_commit();
+            }
+            // the next stage's table objects, where they may be computed beside
+            // these amplitudes (the stage barrier below publishes them)
+            if constexpr (P::TABLE_AHEAD) {
+                if (s + 1 < P::NSTAGE && P::stage(s + 1).ahead) table_rounds(s + 1);
             }
             // software pipeline: the descriptor and the first three operands of the
             // next amplitude are loaded while the current one is evaluated (a third
@@ -569,6 +583,9 @@ template <class P, class T, bool TC = false, class C = T, bool SDE = false> cuda
     using L = InterpLayout<P, T>;
     static_assert(!TC || sizeof(T) == 4, "tensor-core colour sum is the mixed-precision path");
     static_assert(L::launch_bytes <= 232448, "interpreter shared memory exceeds 227 KB");
+    // with J in tensor memory two CTAs share an SM (228 KB; per CTA 1 KB reserved
+    // and at most 1.5 KB of static arrays): the generator caps the table for it
+    static_assert(!L::J_MMA || 2 * (L::launch_bytes + 1024 + 1536) <= 233472, "two CTAs per SM do not fit");
     if (a.nlist > P::NT) return cudaErrorInvalidValue;
     int nsm = 0, per_sm = 0;
     cudaError_t e = interp_residency<P, T, TC, C, SDE>(nsm, per_sm);

@@ -23,8 +23,10 @@ EXT_KINDS = {"VIN": 0, "VOUT": 1, "FO_U": 2, "FO_V": 3, "FI_U": 4, "FI_V": 5}
 #             warp fence every n amplitudes in FP32, in FP64)
 # schedule mode: bit 0 = amplitudes as contractions of amputated vertex
 # objects, bit 1 = no colour groups (J updated after every amplitude), bit 2 =
-# no merged contractions (a group's members sharing an operand each contract)
-# (measured on GB300 over stage sizes, events per CTA and fence intervals)
+# no merged contractions (a group's members sharing an operand each contract),
+# bit 3 = (descriptor kernel) each stage's table work runs beside the previous
+# stage's amplitudes (measured on GB300 over stage sizes, events per CTA and
+# fence intervals)
 TAB_PROCESSES = {"gg_ttxg": (32, 1, 1, 1, 0, 1, 4), "gg_ttxgg": (64, 2, 2, 5, 60, 7, 4)}
 # processes evaluated with the staged descriptor kernel (me_kernel_interp.cuh)
 # process -> (threads per event, amplitudes per stage and schedule mode (as
@@ -32,6 +34,9 @@ TAB_PROCESSES = {"gg_ttxg": (32, 1, 1, 1, 0, 1, 4), "gg_ttxgg": (64, 2, 2, 5, 60
 #             memory, so the table peak of its stages must fit beside J; FP64
 #             keeps J in a global scratch.  One schedule for both precisions lets
 #             them share one descriptor set (in constant memory).
+# (mode bit 3, the table work one stage ahead, measured on GB300 for
+# gg -> t t~ g g g: mixed 598 ms per 2^18 events against 592 without, FP32 768
+# against 773 -- no gain, so it stays off)
 INTERP_PROCESSES = {"gg_ttxggg": (128, 16, 0, 16, 0)}
 
 
@@ -769,12 +774,35 @@ CONST_DESCRIPTORS = __import__("os").environ.get("ME_INTERP_CONST", "1") != "0"
 # accumulator slots per thread for the colour windows of the staged descriptor
 
 
+# shared memory of the FP32 descriptor kernel with J in tensor memory, two CTAs
+# per SM (me_kernel_interp.cuh InterpLayout): 228 KB per SM, per CTA 1 KB
+# reserved and up to 1.5 KB of static arrays; after the table the six A
+# operands (4352 bytes each, 1 KB-aligned start) and B (4096 bytes)
+SMEM_PER_SM, SMEM_CTA_RESERVED, INTERP_STATIC_SMEM = 233472, 1024, 1536
+INTERP_OPERAND_BYTES = 6 * 4352 + 4096
+
+
+def _interp_table_cap(process: str, nt: int) -> int:
+    """most table entries (FP32 wavefunctions, 32 bytes) that keep two CTAs of
+    the descriptor kernel resident per SM"""
+    P = build_plan(process)
+    npar, nl = P.npar, len(P.lines)
+    from .interp import build_interp as _bi  # supports of the default schedule bound NSUP
+    nsup = len(_bi(process, INTERP_PROCESSES.get(process, (0, 16))[1]).supports)
+    a16 = lambda x: (x + 15) // 16 * 16
+    table_off = a16(a16(npar * 4 * 8 * 2 + npar * (npar + 1) // 2 * 8 + nl * 20) + nsup * nt)
+    dyn = SMEM_PER_SM // 2 - SMEM_CTA_RESERVED - INTERP_STATIC_SMEM
+    jsm_max = (dyn - INTERP_OPERAND_BYTES) // 1024 * 1024
+    return (jsm_max - table_off) // 32 // 8 * 8
+
+
 def emit_interp_struct(process: str, nt: int, stage_amps: int, num, mode: int = 0,
                        name: str = "ProcInterp", prefix: str = ""):
     """ProcInterp: staged table tasks, amplitude descriptors, colour terms
     (arrays named with `prefix`, struct `name`)."""
     amputated = bool(mode & 1)
-    I = build_interp(process, stage_amps, amputated, not mode & 2)
+    I = build_interp(process, stage_amps, amputated, not mode & 2, bool(mode & 8),
+                     _interp_table_cap(process, nt) if mode & 8 else None)
     T = I.tab
     P = T.plan
     npar = P.npar
@@ -826,7 +854,7 @@ def emit_interp_struct(process: str, nt: int, stage_amps: int, num, mode: int = 
                 assert col < 128
                 img[umma_k16_offset(col, k) // 2] = 0x3F80 if c == (0, -1) else 0xBF80
         bmat += [img[i] | (img[i + 1] << 16) for i in range(0, 2048, 2)]
-        stages.append((r0, len(rounds), a0, len(amps), a0 + st.mid, st.slot_mid))
+        stages.append((r0, len(rounds), a0, len(amps), a0 + st.mid, st.slot_mid, int(st.ahead)))
     masks = []
     for S in I.supports:
         m = 0
@@ -855,7 +883,7 @@ def emit_interp_struct(process: str, nt: int, stage_amps: int, num, mode: int = 
     src = ""
     src += arr("c_itasks", "TabTask", tasks, lambda t: "{%d, %d, %d, %d, %d, %d, %d, 0, 0}" % t, 4)
     src += arr("c_rounds", "IRound", rounds, lambda r: "{%du, %d, %d, %d}" % r, 8)
-    src += arr("c_stages", "IStage", stages, lambda r: "{%d, %d, %d, %d, %d, %d, 0, 0}" % r, 4)
+    src += arr("c_stages", "IStage", stages, lambda r: "{%d, %d, %d, %d, %d, %d, %d, 0}" % r, 4)
     src += arr("c_amps", "IAmp", amps, lambda a: "{{%d, %d, %d, %d}, {%d, %d, %d, %d}, %d, %d, %d, %d}" % (
         *a[0], *a[1], a[2], a[3], a[4], a[5]), 3)
     src += arr("c_terms", "unsigned short", terms, lambda x: "%d" % x, 16)
@@ -871,6 +899,9 @@ def emit_interp_struct(process: str, nt: int, stage_amps: int, num, mode: int = 
 struct {name} : Proc {{
     static constexpr int NT = {nt}, TAB = {(I.table_size + 7) // 8 * 8}, NSUP = {len(I.supports)}, NSTAGE = {len(I.stages)};
     static constexpr bool IS_TAB = false, IS_INTERP = true;
+    // table objects of stage s + 1 computed beside the amplitudes of stage s
+    // (slots reused two stages after their last reader)
+    static constexpr bool TABLE_AHEAD = {"true" if I.ahead else "false"};
     static constexpr long long TABLE_FLOPS = {I.table_flops}LL, AMP_FLOPS = {T.amplitude_flops_per_helicity(not mode & 2)}LL;
     __device__ static __forceinline__ const TabTask* tasks() {{ return {prefix}c_itasks; }}
     __device__ static __forceinline__ IRound round(int r) {{ return {prefix}c_rounds[r]; }}

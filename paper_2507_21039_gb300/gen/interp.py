@@ -37,6 +37,8 @@ class Stage:
     # amps[mid:]; mid falls on a colour-group boundary, slot_mid = groups before it
     mid: int = 0
     slot_mid: int = 0
+    # the stage's table work runs beside the previous stage's amplitudes
+    ahead: bool = False
 
 
 @dataclass
@@ -50,6 +52,7 @@ class InterpPlan:
     table_flops: int
     sign: list = field(default_factory=list)    # +-1 of each amplitude in its colour group's sum
     flush: dict = field(default_factory=dict)   # last member of a group -> the group's colour terms
+    ahead: bool = False                         # table work one stage ahead of the amplitudes
 
 
 class _Arena:
@@ -104,7 +107,13 @@ def _split_amplitudes(ops, amps, stage_amps, flush):
     return best[1], best[2]
 
 
-def build_interp(process: str, stage_amps: int = 48, amputated: bool = False, group: bool = True) -> InterpPlan:
+def build_interp(process: str, stage_amps: int = 48, amputated: bool = False, group: bool = True,
+                 ahead: bool = False, table_cap: int | None = None) -> InterpPlan:
+    """ahead: a stage's table objects may be computed while the previous
+    stage's amplitudes are evaluated (one barrier per stage instead of two);
+    they then must not reuse the slots that those amplitudes read.  A stage
+    runs ahead where its objects fit below table_cap entries that way
+    (Stage.ahead); otherwise its table work keeps a phase of its own."""
     T = build_tabplan(process, amputated)
     P = T.plan
     ops = P.ops
@@ -177,10 +186,25 @@ def build_interp(process: str, stage_amps: int = 48, amputated: bool = False, gr
 
     arena = _Arena(2 * P.npar)
     slot = {}
+    pending = []  # objects last read by the previous stage, not yet released
     for si, st in enumerate(stages):
-        # allocate this stage's new objects (in dependency order), release dead ones after
-        for o in sorted(st.new):
-            slot[o] = arena.alloc(size[o])
+        # allocate this stage's new objects (in dependency order).  Ahead: before
+        # the previous stage's dead objects are released, so that none of their
+        # slots (read by that stage's amplitudes meanwhile) is reused
+        if ahead and si > 0:
+            snap = (list(arena.free), arena.peak)
+            trial = {o: arena.alloc(size[o]) for o in sorted(st.new)}
+            if table_cap is None or arena.peak <= table_cap:
+                slot.update(trial)
+                st.ahead = True
+            else:
+                arena.free, arena.peak = snap
+        for o in pending:
+            arena.release(slot[o], size[o])
+        pending = []
+        if not st.ahead:
+            for o in sorted(st.new):
+                slot[o] = arena.alloc(size[o])
         level = {}
         for o in sorted(st.new):  # op indices are topologically ordered
             level[o] = 1 + max([level.get(a, 0) for a in ops[o].args if a in st.new] or [0])
@@ -206,10 +230,8 @@ def build_interp(process: str, stage_amps: int = 48, amputated: bool = False, gr
                     ln = (op.mom[0], op.mom[1], max(op.line, 0)) if vvv else (0, 0, max(op.line, 0))
                     tasks.append((slot[o] + v, tuple(ins), ln))
             st.rounds.append((kind, tasks))
-        for o in list(slot):
-            if o in last and last[o] == si:
-                arena.release(slot[o], size[o])
-                last[o] = -99  # released
+        # objects last read in this stage are released when the next is placed
+        pending = [o for o in slot if last.get(o) == si]
     supports = sorted({T.support[a] for ai, _ in P.amps for a in ops[ai].args}, key=lambda s: (len(s), s))
     tflops = sum(FLOPS[k] * len(t) for st in stages for k, t in st.rounds)
-    return InterpPlan(T, stages, slot, arena.peak, order, supports, tflops, sign_of, flush)
+    return InterpPlan(T, stages, slot, arena.peak, order, supports, tflops, sign_of, flush, ahead)

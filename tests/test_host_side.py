@@ -235,7 +235,7 @@ def test_stage_split_between_the_threads_of_a_helicity():
     src, I = emit_interp_struct("gg_ttxggg", nt, sf, colour_matrix(5)[0], mf)
     P = I.tab.plan
     body = re.search(r"c_stages\[\d+\] = \{(.*?)\n\};", src, re.S).group(1)
-    rows = [tuple(int(x) for x in r) for r in re.findall(r"\{(\d+), (\d+), (\d+), (\d+), (\d+), (\d+), 0, 0\}", body)]
+    rows = [tuple(int(x) for x in r) for r in re.findall(r"\{(\d+), (\d+), (\d+), (\d+), (\d+), (\d+), \d+, 0\}", body)]
     assert len(rows) == len(I.stages)
     a0 = 0
     for st, row in zip(I.stages, rows):
@@ -250,6 +250,64 @@ def test_stage_split_between_the_threads_of_a_helicity():
         assert max(sum(cost[:st.mid]), sum(cost[st.mid:])) == min(best, sum(cost))
         a0 += len(amps)
     assert a0 == len(P.amps)
+
+
+def test_table_work_ahead_never_overwrites_live_entries():
+    """Schedule mode bit 3 (a build option): where a stage's table rounds run beside the previous stage's amplitudes
+    (Stage.ahead), every entry written in that phase is disjoint from every
+    entry read in it (the amplitudes' operands and the rounds' inputs) and
+    from the other writes; the same holds for the table phases of their own.
+    The table stays within the cap that keeps two CTAs per SM, and the
+    emitted stage descriptors carry the flags."""
+    from paper_2507_21039_gb300.gen.emit import INTERP_PROCESSES, _interp_table_cap, emit_interp_struct
+
+    nt, sf, mf, _, _ = INTERP_PROCESSES["gg_ttxggg"]
+    src, I = emit_interp_struct("gg_ttxggg", nt, sf, colour_matrix(5)[0], mf | 8)
+    P = I.tab.plan
+    ops = P.ops
+    assert I.table_size <= _interp_table_cap("gg_ttxggg", nt)
+    assert sum(st.ahead for st in I.stages) > 0.9 * len(I.stages) and not I.stages[0].ahead
+    body = re.search(r"c_stages\[\d+\] = \{(.*?)\n\};", src, re.S).group(1)
+    flags = [int(f) for f in re.findall(r"\{\d+, \d+, \d+, \d+, \d+, \d+, (\d+), 0\}", body)]
+    assert flags == [int(st.ahead) for st in I.stages]
+
+    def obj_range(x):
+        if ops[x].kind.startswith("ext_"):
+            return set(range(2 * ops[x].ext, 2 * ops[x].ext + 2))
+        return set(range(I.slot[x], I.slot[x] + (1 << len(I.tab.support[x]))))
+
+    def table_levels(st):  # (reads, writes) of each level, the levels split by CTA barriers
+        levels, reads, writes = [], set(), []
+        for ri, (_, tl) in enumerate(st.rounds):
+            for out, ins, _ in tl:
+                reads |= set(ins)
+                writes.append(out)
+            if ri in st.barriers or ri == len(st.rounds) - 1:
+                levels.append((reads, writes))
+                reads, writes = set(), []
+        return levels
+
+    def amp_reads(st):
+        r = set()
+        for ai in st.amps:
+            for x in ops[P.amps[ai][0]].args:
+                r |= obj_range(x)
+        return r
+
+    def check(levels, later_reads):
+        # writes of a phase are disjoint; a level's reads meet no write of its
+        # own or a later level; reads after the phase's last level (amplitudes) no write
+        allw = [w for _, ws in levels for w in ws]
+        assert len(allw) == len(set(allw))
+        for k, (r, _) in enumerate(levels):
+            assert not (r & {w for _, ws in levels[k:] for w in ws})
+        assert not (later_reads & set(allw))
+
+    for si, st in enumerate(I.stages):
+        if not st.ahead:
+            check(table_levels(st), set())
+        nxt = table_levels(I.stages[si + 1]) if si + 1 < len(I.stages) and I.stages[si + 1].ahead else []
+        check(nxt, amp_reads(st))
 
 
 def test_stage_sign_matrices_replay_the_flow_updates():
