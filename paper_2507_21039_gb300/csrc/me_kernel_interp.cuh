@@ -58,8 +58,16 @@
 #ifndef ME_INTERP_A_MMAJOR
 #define ME_INTERP_A_MMAJOR 1
 #endif
+// Build option ME_INTERP_PAIRS: amplitudes evaluated two at a time where the
+// generator pairs them (1, default) or one at a time with the next one's
+// operands loaded ahead (0)
+#ifndef ME_INTERP_PAIRS
+#define ME_INTERP_PAIRS 1
+#endif
 
 namespace me {
+
+constexpr bool kInterpPairs = ME_INTERP_PAIRS != 0;
 
 struct __align__(8) IRound {
     unsigned int task_begin;
@@ -87,9 +95,10 @@ enum IRoutine : unsigned char {
     R_FFV1A_3, R_FFV1A_2, R_FFV1A_1, R_VVV1A_1, R_VVV1A_2, R_VVV1A_3, R_VVVV1A, R_VVVV3A, R_VVVV4A
 };
 enum IAmpKind : unsigned char { A_FFV1_0 = 0, A_VVV1_0, A_VVVV1_0, A_VVVV3_0, A_VVVV4_0, A_DOTV, A_DOTF };
-// IAmp.kind flag above the kind: the amplitude enters its colour group's sum
-// with a minus sign
-constexpr unsigned char AMP_NEG = 0x80;
+// IAmp.kind flags above the kind: the amplitude enters its colour group's sum
+// with a minus sign (AMP_NEG); the amplitude and the next one have the same
+// kind and lie in the same half of the stage (AMP_PAIR)
+constexpr unsigned char AMP_NEG = 0x80, AMP_PAIR = 0x40, AMP_KIND_MASK = 0x3f;
 
 template <class P, class T> struct InterpLayout {
     static constexpr size_t mom = 0;
@@ -316,24 +325,12 @@ __global__ void __launch_bounds__(InterpLayout<P, T>::NTH, InterpLayout<P, T>::M
             if constexpr (P::TABLE_AHEAD) {
                 if (s + 1 < P::NSTAGE && P::stage(s + 1).ahead) table_rounds(s + 1);
             }
-            // software pipeline: the descriptor and the first three operands of the
-            // next amplitude are loaded while the current one is evaluated (a third
-            // operand index of a two-operand kind is 0 with support 0: an external
-            // wavefunction entry, read and not used)
-            IAmp dn;
-            Wf<T> p0, p1, p2;
-            auto fetch = [&](int ai) {
-                dn = P::amp(ai);
-                p0 = tab.ld(dn.op[0] + vsup[dn.sup[0] * NT + h]);
-                p1 = tab.ld(dn.op[1] + vsup[dn.sup[1] * NT + h]);
-                p2 = tab.ld(dn.op[2] + vsup[dn.sup[2] * NT + h]);
-            };
-            if (amp_lo < amp_hi) fetch(amp_lo);
-            for (int ai = amp_lo; ai < amp_hi; ++ai) {
-                const IAmp d = dn;
-                const Wf<T> w0 = p0, w1 = p1, w2 = p2;
-                if (ai + 1 < amp_hi) fetch(ai + 1);
-                const int kind = d.kind & 0x3f;
+            // amplitude x of descriptor d with operands w0..w2 (a third operand index of a
+            // two-operand kind is 0 with support 0: an external wavefunction entry, read
+            // and not used)
+            auto opnd = [&](const IAmp& d, int k) { return tab.ld(d.op[k] + vsup[d.sup[k] * NT + h]); };
+            auto eval = [&](const IAmp& d, const Wf<T>& w0, const Wf<T>& w1, const Wf<T>& w2) {
+                const int kind = d.kind & AMP_KIND_MASK;
                 cx<T> x;
                 if (kind == A_DOTV) {           // amputated: two-operand contractions
                     x = DOTV<T>(w0, w1);
@@ -344,12 +341,16 @@ __global__ void __launch_bounds__(InterpLayout<P, T>::NTH, InterpLayout<P, T>::M
                     case A_FFV1_0: x = FFV1_0<T>(w0, w1, w2); break;
                     case A_VVV1_0: x = VVV1_0<T>(w0, sln[d.la].p, w1, sln[d.lb].p, w2); break;
                     default: {
-                        const Wf<T> w3 = tab.ld(d.op[3] + vsup[d.sup[3] * NT + h]);
+                        const Wf<T> w3 = opnd(d, 3);
                         x = kind == A_VVVV1_0 ? VVVV1_0<T>(w0, w1, w2, w3)
                           : kind == A_VVVV3_0 ? VVVV3_0<T>(w0, w1, w2, w3) : VVVV4_0<T>(w0, w1, w2, w3);
                     }
                     }
                 }
+                return x;
+            };
+            // x into its colour group's sum; the group's last member adds the group to J
+            auto accumulate = [&](const IAmp& d, const cx<T>& x, int ai) {
                 if constexpr (SDE) {  // single-diagram enhancement
                     const T w2 = fma(x.re, x.re, x.im * x.im);
                     sden += w2;
@@ -360,7 +361,7 @@ __global__ void __launch_bounds__(InterpLayout<P, T>::NTH, InterpLayout<P, T>::M
                 // the group's last member: every colour coefficient is +-i, J_c += +-i G
                 if (d.nterm) {
                     if constexpr (L::J_MMA) {
-                        // row tid, column `slot` of the six A matrices: BF16 parts of Im G, Re G
+                        // row h, column `slot` of the six A matrices: BF16 parts of Im G, Re G
                         float gr = (float)G.re, gi = (float)G.im;
                         if (!(isfinite(gr) && isfinite(gi))) {
                             nonfinite = true;
@@ -384,6 +385,77 @@ __global__ void __launch_bounds__(InterpLayout<P, T>::NTH, InterpLayout<P, T>::M
                         }
                     }
                     G = {T(0), T(0)};
+                }
+            };
+            if constexpr (kInterpPairs) {
+                // amplitudes flagged AMP_PAIR and their successor (same kind, same half
+                // of the stage) are evaluated together: two independent dependency
+                // chains for the scheduler; their operands are loaded at once
+                int ai = amp_lo;
+                while (ai < amp_hi) {
+                    const IAmp d0 = P::amp(ai);
+                    const Wf<T> a0 = opnd(d0, 0), a1 = opnd(d0, 1), a2 = opnd(d0, 2);
+                    if ((d0.kind & AMP_PAIR) && ai + 1 < amp_hi) {
+                        const IAmp d1 = P::amp(ai + 1);
+                        const Wf<T> b0 = opnd(d1, 0), b1 = opnd(d1, 1), b2 = opnd(d1, 2);
+                        const int kind = d0.kind & AMP_KIND_MASK;
+                        cx<T> x0, x1;
+                        switch (kind) {
+                        case A_FFV1_0:
+                            x0 = FFV1_0<T>(a0, a1, a2);
+                            x1 = FFV1_0<T>(b0, b1, b2);
+                            break;
+                        case A_VVV1_0:
+                            x0 = VVV1_0<T>(a0, sln[d0.la].p, a1, sln[d0.lb].p, a2);
+                            x1 = VVV1_0<T>(b0, sln[d1.la].p, b1, sln[d1.lb].p, b2);
+                            break;
+                        case A_DOTV:
+                            x0 = DOTV<T>(a0, a1);
+                            x1 = DOTV<T>(b0, b1);
+                            break;
+                        case A_DOTF:
+                            x0 = DOTF<T>(a0, a1);
+                            x1 = DOTF<T>(b0, b1);
+                            break;
+                        default: {
+                            const Wf<T> a3 = opnd(d0, 3), b3 = opnd(d1, 3);
+                            if (kind == A_VVVV1_0) {
+                                x0 = VVVV1_0<T>(a0, a1, a2, a3);
+                                x1 = VVVV1_0<T>(b0, b1, b2, b3);
+                            } else if (kind == A_VVVV3_0) {
+                                x0 = VVVV3_0<T>(a0, a1, a2, a3);
+                                x1 = VVVV3_0<T>(b0, b1, b2, b3);
+                            } else {
+                                x0 = VVVV4_0<T>(a0, a1, a2, a3);
+                                x1 = VVVV4_0<T>(b0, b1, b2, b3);
+                            }
+                        }
+                        }
+                        accumulate(d0, x0, ai);
+                        accumulate(d1, x1, ai + 1);
+                        ai += 2;
+                    } else {
+                        accumulate(d0, eval(d0, a0, a1, a2), ai);
+                        ai += 1;
+                    }
+                }
+            } else {
+                // software pipeline: the descriptor and the first three operands of the
+                // next amplitude are loaded while the current one is evaluated
+                IAmp dn;
+                Wf<T> p0, p1, p2;
+                auto fetch = [&](int ai) {
+                    dn = P::amp(ai);
+                    p0 = opnd(dn, 0);
+                    p1 = opnd(dn, 1);
+                    p2 = opnd(dn, 2);
+                };
+                if (amp_lo < amp_hi) fetch(amp_lo);
+                for (int ai = amp_lo; ai < amp_hi; ++ai) {
+                    const IAmp d = dn;
+                    const Wf<T> w0 = p0, w1 = p1, w2 = p2;
+                    if (ai + 1 < amp_hi) fetch(ai + 1);
+                    accumulate(d, eval(d, w0, w1, w2), ai);
                 }
             }
             if constexpr (L::J_MMA) {

@@ -796,6 +796,20 @@ def _interp_table_cap(process: str, nt: int) -> int:
     return (jsm_max - table_off) // 32 // 8 * 8
 
 
+def _pair_heads(kinds, mid):
+    """positions i of a stage's amplitude list whose amplitude is evaluated
+    together with amplitude i + 1 (descriptor flag AMP_PAIR): greedily, where
+    both have the same kind and lie on the same side of the split at `mid`"""
+    heads, i = set(), 0
+    while i + 1 < len(kinds):
+        if kinds[i] == kinds[i + 1] and (i + 1 < mid or i >= mid):
+            heads.add(i)
+            i += 2
+        else:
+            i += 1
+    return heads
+
+
 def emit_interp_struct(process: str, nt: int, stage_amps: int, num, mode: int = 0,
                        name: str = "ProcInterp", prefix: str = ""):
     """ProcInterp: staged table tasks, amplitude descriptors, colour terms
@@ -825,7 +839,8 @@ def emit_interp_struct(process: str, nt: int, stage_amps: int, num, mode: int = 
         a0 = len(amps)
         stage_term.append(len(terms))
         sup_index = {S: i for i, S in enumerate(I.supports)}
-        for ai in st.amps:
+        heads = _pair_heads([ops[P.amps[ai][0]].kind for ai in st.amps], st.mid)
+        for pos, ai in enumerate(st.amps):
             aop, coefs = P.amps[ai]
             op = ops[aop]
             bases, sups = [], []
@@ -842,7 +857,7 @@ def emit_interp_struct(process: str, nt: int, stage_amps: int, num, mode: int = 
             # (kind bit 7 = minus); the group's last member carries the terms
             gterms = I.flush.get(ai, ())
             assert len(op.args) <= 4 and len(gterms) < 256 and all(c in ((0, 1), (0, -1)) for _, c in coefs + gterms)
-            kind = AMP_KINDS.index(op.kind) | (0x80 if I.sign[ai] < 0 else 0)
+            kind = AMP_KINDS.index(op.kind) | (0x80 if I.sign[ai] < 0 else 0) | (0x40 if pos in heads else 0)
             amps.append((bases, sups, kind, la, lb, len(gterms)))
             for col, c in gterms:
                 terms.append(col | (0x8000 if c == (0, -1) else 0))

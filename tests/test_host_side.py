@@ -310,6 +310,30 @@ def test_table_work_ahead_never_overwrites_live_entries():
         check(nxt, amp_reads(st))
 
 
+def test_amplitude_pairs_share_kind_and_half():
+    """Descriptor flag AMP_PAIR (0x40): the flagged amplitude and the next one
+    are evaluated together, so they have the same kind, lie in the same half
+    of the same stage, and the successor of a pair head is not itself a head."""
+    from paper_2507_21039_gb300.gen.emit import INTERP_PROCESSES, emit_interp_struct
+
+    nt, sf, mf, _, _ = INTERP_PROCESSES["gg_ttxggg"]
+    src, I = emit_interp_struct("gg_ttxggg", nt, sf, colour_matrix(5)[0], mf)
+    amps = re.search(r"c_amps\[\d+\] = \{(.*?)\n\};", src, re.S).group(1)
+    kinds = [int(k) for k in re.findall(r"\}, (\d+), \d+, \d+, \d+\}", amps)]
+    a0, npair = 0, 0
+    for st in I.stages:
+        n = len(st.amps)
+        for i in range(n):
+            k = kinds[a0 + i]
+            if k & 0x40:
+                npair += 1
+                assert i + 1 < n and (kinds[a0 + i + 1] & 0x3F) == (k & 0x3F)
+                assert (i + 1 < st.mid) or (i >= st.mid)
+                assert not kinds[a0 + i + 1] & 0x40
+        a0 += n
+    assert a0 == len(kinds) and 2 * npair > 0.8 * len(kinds)
+
+
 def test_stage_sign_matrices_replay_the_flow_updates():
     """The FP32 descriptor kernel accumulates J on the tensor cores: per stage,
     Re J += Im G . B and Im J += Re G . (-B), G the stage's group sums in update
