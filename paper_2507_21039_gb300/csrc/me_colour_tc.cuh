@@ -126,24 +126,24 @@ __device__ __forceinline__ float colour_tc_warp(const cx<float> (&J)[NCOL], unsi
 
 namespace me {
 
-// Tensor-core colour quadratic form for J held in shared memory as
-// jsm[c * NT + thread] (FP32 complex).  Per warp: rows = its 32 threads' Re J
-// (half 0) or Im J (half 1); A fragments are built straight from jsm (BF16 hi/lo
+// Tensor-core colour quadratic form, one warp, J read from shared memory
+// through el(c, thread, half) (flow c of that thread's Re J for half 0, Im J
+// for half 1; halves H0 <= half < H1).  Per warp: rows = its 32 threads' Re J
+// or Im J; A fragments are built straight from shared memory (BF16 hi/lo
 // split), Y = A N accumulates in FP32 over the K steps of each n-tile, and each
-// fragment entry Y[row][n] is immediately multiplied by J_row[n] from jsm.
-// Returns this thread's own J^+ N J (rows are summed within quads, then handed
-// to their owners through `rowv`, NT floats of shared memory).
-template <int NCOL, int NT, bool NSPLIT>
-__device__ __forceinline__ float colour_tc_smem(const cx<float>* __restrict__ jsm, const uint2* __restrict__ bfrag,
-                                                float* __restrict__ rowv, int tid)
+// fragment entry Y[row][n] is immediately multiplied by J_row[n].  Returns this
+// thread's own share of J^+ N J (rows are summed within quads, then handed to
+// their owners through `rowv`, one float per thread of the CTA).
+template <int NCOL, bool NSPLIT, int H0, int H1, class F>
+__device__ __forceinline__ float colour_tc_rows(F el, const uint2* __restrict__ bfrag, float* __restrict__ rowv,
+                                                int tid)
 {
     using S = TcShape<NCOL>;
     const int lane = tid & 31, wbase = tid & ~31;
     const int g = lane >> 2, t = lane & 3;
-    const float* jf = reinterpret_cast<const float*>(jsm);
     float own = 0.0f;
 #pragma unroll 1
-    for (int half = 0; half < 2; ++half) {
+    for (int half = H0; half < H1; ++half) {
         float rsum[2][2] = {{0.0f, 0.0f}, {0.0f, 0.0f}};  // [mt][row g / g+8]
 #pragma unroll 1
         for (int mt = 0; mt < 2; ++mt) {
@@ -156,8 +156,8 @@ __device__ __forceinline__ float colour_tc_smem(const cx<float>* __restrict__ js
                 const int cols[4] = {c0, c0 + 1, c0 + 8, c0 + 9};
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
-                    v[q] = cols[q] < NCOL ? jf[2 * (cols[q] * NT + l0) + half] : 0.0f;
-                    v[4 + q] = cols[q] < NCOL ? jf[2 * (cols[q] * NT + l1) + half] : 0.0f;
+                    v[q] = cols[q] < NCOL ? el(cols[q], l0, half) : 0.0f;
+                    v[4 + q] = cols[q] < NCOL ? el(cols[q], l1, half) : 0.0f;
                 }
                 split2(v[0], v[1], ahi[ks][0], alo[ks][0]);  // row g,   k = c0, c0+1
                 split2(v[4], v[5], ahi[ks][1], alo[ks][1]);  // row g+8, k = c0, c0+1
@@ -179,12 +179,12 @@ __device__ __forceinline__ float colour_tc_smem(const cx<float>* __restrict__ js
                 }
                 const int n0 = 8 * nt + 2 * t;
                 if (n0 < NCOL) {
-                    rsum[mt][0] = fmaf(acc[0], jf[2 * (n0 * NT + l0) + half], rsum[mt][0]);
-                    rsum[mt][1] = fmaf(acc[2], jf[2 * (n0 * NT + l1) + half], rsum[mt][1]);
+                    rsum[mt][0] = fmaf(acc[0], el(n0, l0, half), rsum[mt][0]);
+                    rsum[mt][1] = fmaf(acc[2], el(n0, l1, half), rsum[mt][1]);
                 }
                 if (n0 + 1 < NCOL) {
-                    rsum[mt][0] = fmaf(acc[1], jf[2 * ((n0 + 1) * NT + l0) + half], rsum[mt][0]);
-                    rsum[mt][1] = fmaf(acc[3], jf[2 * ((n0 + 1) * NT + l1) + half], rsum[mt][1]);
+                    rsum[mt][0] = fmaf(acc[1], el(n0 + 1, l0, half), rsum[mt][0]);
+                    rsum[mt][1] = fmaf(acc[3], el(n0 + 1, l1, half), rsum[mt][1]);
                 }
             }
         }
@@ -209,6 +209,27 @@ __device__ __forceinline__ float colour_tc_smem(const cx<float>* __restrict__ js
         __syncwarp();
     }
     return own;
+}
+
+
+// J held in shared memory as jsm[c * NT + thread] (FP32 complex), both halves
+template <int NCOL, int NT, bool NSPLIT>
+__device__ __forceinline__ float colour_tc_smem(const cx<float>* __restrict__ jsm, const uint2* __restrict__ bfrag,
+                                                float* __restrict__ rowv, int tid)
+{
+    const float* jf = reinterpret_cast<const float*>(jsm);
+    return colour_tc_rows<NCOL, NSPLIT, 0, 2>([jf](int c, int l, int half) { return jf[2 * (c * NT + l) + half]; },
+                                              bfrag, rowv, tid);
+}
+
+// one half of J (Re or Im: its share of the form) held per warp as
+// plane[c * 32 + lane] (FP32); rowv: 32 floats of the warp
+template <int NCOL, bool NSPLIT>
+__device__ __forceinline__ float colour_tc_plane(const float* __restrict__ plane, const uint2* __restrict__ bfrag,
+                                                 float* __restrict__ rowv, int lane)
+{
+    return colour_tc_rows<NCOL, NSPLIT, 0, 1>([plane](int c, int l, int) { return plane[c * 32 + (l & 31)]; }, bfrag,
+                                              rowv, lane);
 }
 
 }  // namespace me

@@ -127,9 +127,13 @@ template <class P, class T> struct InterpLayout {
     static constexpr size_t bmat = amat + 6 * ABYTES;
     static constexpr size_t bytes = J_MMA ? bmat + 4096
                                           : jsm + (J_IN_SMEM ? (size_t)P::NCOL * P::NT * sizeof(cx<T>) : 0);
-    // colour sum from TMEM: per warp, J as [flow][lane] FP32 and 32 floats of row
-    // totals, two warps at a time over the (then dead) table
-    static constexpr size_t WJ = (size_t)P::NCOL * 32 * sizeof(cx<float>) + 32 * sizeof(float);
+    // colour sum from TMEM: per warp, one half of J (Re, then Im) as [flow][lane]
+    // FP32 and 32 floats of row totals, the four warps at once over the (then
+    // dead) table
+    static constexpr size_t WJ = ((size_t)P::NCOL * 32 * sizeof(float) + 32 * sizeof(float) + 15) / 16 * 16;
+    // scalar colour form (FP32 precision): J of a warp as [flow][lane] complex,
+    // two warps at a time (the form reads each numerator once for both halves)
+    static constexpr size_t WJC = (size_t)P::NCOL * 32 * sizeof(cx<float>);
     static constexpr size_t launch_bytes = bytes;
 };
 
@@ -209,7 +213,8 @@ __global__ void __launch_bounds__(InterpLayout<P, T>::NTH, InterpLayout<P, T>::M
     if constexpr (L::J_MMA) {
         static_assert(NT == 128 && NCOL <= 128, "one TMEM lane per helicity, one column per flow");
         static_assert(P::MAXFLUSH <= 16, "at most 16 colour-group updates per stage (one K = 16 step)");
-        static_assert(2 * L::WJ <= (size_t)P::TAB * sizeof(Wf<T>), "colour staging exceeds the table");
+        static_assert(4 * L::WJ <= (size_t)P::TAB * sizeof(Wf<T>) && 2 * L::WJC <= (size_t)P::TAB * sizeof(Wf<T>),
+                      "colour staging exceeds the table");
         if (tid < 32) {
             tmem_alloc(&tmem_base, L::TMEM_COLS);
             tmem_relinquish();
@@ -506,28 +511,51 @@ __global__ void __launch_bounds__(InterpLayout<P, T>::NTH, InterpLayout<P, T>::M
             if constexpr (NTH > NT) {
                 if (half) pair_nonfinite[h] = nonfinite ? 1 : 0;  // read after the barriers below
             }
-            // warps 0-3 (lanes 0-127 of tensor memory) form the colour sum
+            // warps 0-3 (lanes 0-127 of tensor memory) form the colour sum over the dead
+            // table.  Tensor-core form: all four warps at once, one half of J (Re, then
+            // Im) at a time (the form is the sum of the two halves' forms).  Scalar
+            // form: two warps at a time, J complex
             const int w = tid >> 5, lane = tid & 31;
-            unsigned char* stage = smem + L::table + (size_t)(w & 1) * L::WJ;
-            cx<float>* js = reinterpret_cast<cx<float>*>(stage);
-            for (int r = 0; r < 2; ++r) {   // warps 0, 1 then warps 2, 3 over the dead table
-                if ((w >> 1) == r) {
-                    for (int c = 0; c < NCOL; c += 16) {
-                        uint32_t qr[16], qi[16];
-                        tmem_ld_16(tj + (uint32_t)c, qr);
-                        tmem_ld_16(tj + 128u + (uint32_t)c, qi);
+            if constexpr (TC) {
+                if (w < 4) {
+                    unsigned char* stage = smem + L::table + (size_t)w * L::WJ;
+                    float* plane = reinterpret_cast<float*>(stage);
+                    float* rowt = reinterpret_cast<float*>(stage + (size_t)NCOL * 32 * sizeof(float));
+                    T vs = T(0);
+#pragma unroll 1
+                    for (int hh = 0; hh < 2; ++hh) {
+                        for (int c = 0; c < NCOL; c += 16) {
+                            uint32_t q[16];
+                            tmem_ld_16(tj + 128u * (uint32_t)hh + (uint32_t)c, q);
 #pragma unroll
-                        for (int q = 0; q < 16; ++q)
-                            if (c + q < NCOL) js[(c + q) * 32 + lane] = {__uint_as_float(qr[q]), __uint_as_float(qi[q])};
+                            for (int k = 0; k < 16; ++k)
+                                if (c + k < NCOL) plane[(c + k) * 32 + lane] = __uint_as_float(q[k]);
+                        }
+                        __syncwarp();
+                        vs += colour_tc_plane<NCOL, P::NSPLIT>(plane, P::bfrag(), rowt, lane);
+                        __syncwarp();  // the plane is rewritten by the next half
                     }
-                    __syncwarp();
-                    if constexpr (TC)
-                        v = colour_tc_smem<NCOL, 32, P::NSPLIT>(
-                            js, P::bfrag(), reinterpret_cast<float*>(stage + (size_t)NCOL * 32 * sizeof(cx<float>)), lane);
-                    else
-                        v = colour_scalar(reinterpret_cast<const cx<T>*>(js) + lane, 32);
+                    v = vs;
                 }
                 __syncthreads();
+            } else {
+                cx<float>* js = reinterpret_cast<cx<float>*>(smem + L::table + (size_t)(w & 1) * L::WJC);
+                for (int r = 0; r < 2; ++r) {  // warps 0, 1 then warps 2, 3
+                    if ((w >> 1) == r) {
+                        for (int c = 0; c < NCOL; c += 16) {
+                            uint32_t qr[16], qi[16];
+                            tmem_ld_16(tj + (uint32_t)c, qr);
+                            tmem_ld_16(tj + 128u + (uint32_t)c, qi);
+#pragma unroll
+                            for (int k = 0; k < 16; ++k)
+                                if (c + k < NCOL)
+                                    js[(c + k) * 32 + lane] = {__uint_as_float(qr[k]), __uint_as_float(qi[k])};
+                        }
+                        __syncwarp();
+                        v = colour_scalar(reinterpret_cast<const cx<T>*>(js) + lane, 32);
+                    }
+                    __syncthreads();
+                }
             }
             if constexpr (NTH > NT) {
                 if (!half && pair_nonfinite[h]) nonfinite = true;
