@@ -22,6 +22,7 @@
 
 #include "helas.cuh"
 #include "me_proc.h"
+#include "me_split.h"
 
 namespace me {
 
@@ -141,9 +142,10 @@ template <class P, class T> __device__ __forceinline__ Ln<T> line_data(const dou
 // GB300 runs FP64 at 1/64 of the FP32 rate.  In the FP32 and mixed kernels the
 // per-event setup therefore keeps FP64 for the propagator denominators p^2 - m^2
 // alone, and forms them from few FP64 instructions:
-//   * every momentum component is split once into FP32 hi + lo (hi the FP32
-//     rounding of p, lo the rounding of the remainder: p = hi + lo to 2^-48
-//     relative).  hi feeds the external wavefunctions; each line momentum is a
+//   * every momentum component is split once into FP32 hi + lo (p = hi + lo to
+//     2^-47 relative: by conversions in the table kernels, by integer operations
+//     on the bit pattern in the straight-line kernels, see split_or_gram).  hi
+//     feeds the external wavefunctions; each line momentum is a
 //     compensated FP32 sum of the hi and lo parts (the rounding of every hi
 //     addition is recovered exactly and added back), i.e. the FP32 rounding of
 //     its FP64 value up to the last bit;
@@ -160,15 +162,27 @@ template <int NPAR> struct Gram {
 };
 
 // setup item `it` of the first phase: it < 4 NPAR splits momentum component it
-// into pf[it] = {hi, lo}; otherwise the Gram entry it - 4 NPAR (row order)
-template <int NPAR>
+// into pf[it] = {hi, lo}; otherwise the Gram entry it - 4 NPAR (row order).
+// INT_SPLIT: by integer operations on the bit pattern (me_split.h: no FP64-pipe
+// work, about twenty integer instructions), for kernels bound by the FP64 pipe;
+// otherwise by conversions (hi the FP32 rounding of p, lo that of the
+// remainder: three conversions and one FP64 add, fewer issue slots), for the
+// issue-bound table kernels (measured: the integer split cost gg -> t t~ g g
+// 2.6%, and gained e+ e- -> mu+ mu- 22%, u u~ -> e+ e- g 12%)
+template <int NPAR, bool INT_SPLIT = false>
 __device__ __forceinline__ void split_or_gram(const double* __restrict__ p, int it, float2* __restrict__ pf,
                                               double* __restrict__ gram)
 {
     if (it < 4 * NPAR) {
         const double x = p[it];
-        const float hi = __double2float_rn(x);
-        pf[it] = make_float2(hi, __double2float_rn(x - (double)hi));
+        float hi, lo;
+        if constexpr (INT_SPLIT) {
+            split_f32(x, hi, lo);
+        } else {
+            hi = __double2float_rn(x);
+            lo = __double2float_rn(x - (double)hi);
+        }
+        pf[it] = make_float2(hi, lo);
     } else {
         int k = it - 4 * NPAR, i = 0;
         while (k >= NPAR - i) {
@@ -350,7 +364,9 @@ template <class P, class T, class C, class JT> __device__ __forceinline__ T colo
 
 // Scalar colour contraction and helicity sum.  T: chain precision, C: colour.
 template <class P, class T, class C = T, bool SDE = false>
-__global__ void __launch_bounds__(P::THREADS, std::is_same<T, float>::value ? P::MIN_CTAS_F : 1)
+// (a minimum of 0 CTAs per SM leaves the register allocation unconstrained: an
+// explicit 1 made ptxas give gg -> t t~ 125 registers instead of 96)
+__global__ void __launch_bounds__(P::THREADS, (std::is_same<T, float>::value && P::MIN_CTAS_F > 1) ? P::MIN_CTAS_F : 0)
     me_kernel_scalar(LaunchArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -385,16 +401,17 @@ __global__ void __launch_bounds__(P::THREADS, std::is_same<T, float>::value ? P:
     constexpr int PER = P::NEXT + NL;
     if constexpr (F32) {
         // without lines there is no denominator to protect: the first phase then
-        // only rounds each momentum component to FP32, once per event rather than
-        // once per external state that reads it (conversions from FP64 issue on
-        // the FP64 pipe)
+        // only takes each momentum component's leading 24 bits (the hi part of the
+        // split), once per event rather than once per external state that reads it
         constexpr int NA = NL > 0 ? 4 * NPAR + NG : 4 * NPAR;
         for (int it = threadIdx.x; it < ne * NA; it += TH) {
             if constexpr (NL > 0) {
                 const int ev = it / NA, j = it - ev * NA;
-                split_or_gram<NPAR>(smom + ev * NPAR * 4, j, spf + ev * NPAR * 4, sgram + ev * NG);
+                split_or_gram<NPAR, true>(smom + ev * NPAR * 4, j, spf + ev * NPAR * 4, sgram + ev * NG);
             } else {
-                spf[it] = make_float2(__double2float_rn(smom[it]), 0.0f);
+                float hi, lo;
+                split_f32(smom[it], hi, lo);
+                spf[it] = make_float2(hi, 0.0f);
             }
         }
         __syncthreads();

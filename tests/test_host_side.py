@@ -334,6 +334,72 @@ def test_amplitude_pairs_share_kind_and_half():
     assert a0 == len(kinds) and 2 * npair > 0.8 * len(kinds)
 
 
+def test_fp64_split_into_fp32_parts(tmp_path):
+    """me_split.h (the FP32 kernels' per-event split of the FP64 momenta, by
+    integer operations) compiled for the host: hi is x truncated to 24
+    significant bits, lo the next 24 bits truncated (both exact, checked with
+    integer arithmetic on the binary expansion), so |x - hi - lo| < 2^-47 |x|
+    wherever the remainder stays in FP32's normal range (|x| >= 2^-73);
+    zero keeps its sign, values below FP32's normal range give 0, above it inf,
+    NaN stays NaN."""
+    import math
+    import shutil
+    import subprocess
+
+    gxx = shutil.which("g++")
+    if gxx is None:
+        pytest.skip("no host C++ compiler")
+    src = tmp_path / "split.cpp"
+    src.write_text("""
+#include "me_split.h"
+#include <cstdio>
+int main(int argc, char** argv) {
+    FILE* f = fopen(argv[1], "rb"); FILE* o = fopen(argv[2], "wb");
+    double x;
+    while (fread(&x, sizeof x, 1, f) == 1) { float h, l; me::split_f32(x, h, l); fwrite(&h, 4, 1, o); fwrite(&l, 4, 1, o); }
+    fclose(f); fclose(o); return 0;
+}
+""")
+    exe = tmp_path / "split"
+    csrc = os.path.join(ROOT, "paper_2507_21039_gb300", "csrc")
+    subprocess.run([gxx, "-O2", "-std=c++17", "-I", csrc, str(src), "-o", str(exe)], check=True)
+    rng = np.random.default_rng(5)
+    mags = np.exp(rng.uniform(np.log(1e-30), np.log(1e30), 20000))
+    xs = np.concatenate([mags * rng.choice([-1.0, 1.0], len(mags)), rng.normal(0, 500, 5000),
+                         [0.0, -0.0, 1.0, -1.0, 2.0 ** -126, 2.0 ** -127, 1e-300, 3e38, 1e39, -1e300,
+                          np.inf, -np.inf, np.nan, 1.0 + 2.0 ** -30, 1.0 - 2.0 ** -53]])
+    (tmp_path / "in.bin").write_bytes(xs.astype("<f8").tobytes())
+    subprocess.run([str(exe), str(tmp_path / "in.bin"), str(tmp_path / "out.bin")], check=True)
+    out = np.frombuffer((tmp_path / "out.bin").read_bytes(), dtype="<f4").reshape(-1, 2)
+    assert len(out) == len(xs)
+
+    def trunc_bits(v, nbits):  # v > 0: v truncated to nbits significant bits, exactly
+        mant, ex = math.frexp(v)  # v = mant * 2^ex, 0.5 <= mant < 1
+        q = int(mant * (1 << 53))  # exact: 53-bit integer
+        keep = q >> (53 - nbits) << (53 - nbits)
+        return math.ldexp(keep, ex - 53)
+
+    for x, (h, l) in zip(xs, out):
+        h, l = float(h), float(l)
+        if math.isnan(x):
+            assert math.isnan(h)
+            continue
+        if math.isinf(x) or abs(x) >= 2.0 ** 128:
+            assert h == math.copysign(math.inf, x) and l == 0.0
+            continue
+        if abs(x) < 2.0 ** -126:
+            assert h == 0.0 and l == 0.0 and math.copysign(1, h) == math.copysign(1, x)
+            continue
+        a = abs(x)
+        th = trunc_bits(a, 24)
+        assert abs(h) == th and math.copysign(1, h) == math.copysign(1, x)
+        rem = a - th  # exact in FP64 (the low bits of a)
+        tl = trunc_bits(rem, 24) if rem >= 2.0 ** -126 else 0.0
+        assert abs(l) == tl and (l == 0.0 or math.copysign(1, l) == math.copysign(1, x))
+        if a >= 2.0 ** -73:  # the remainder, however small, in FP32's normal range
+            assert abs(a - th - tl) < 2.0 ** -47 * a
+
+
 def test_stage_sign_matrices_replay_the_flow_updates():
     """The FP32 descriptor kernel accumulates J on the tensor cores: per stage,
     Re J += Im G . B and Im J += Re G . (-B), G the stage's group sums in update
