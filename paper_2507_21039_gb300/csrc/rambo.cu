@@ -174,12 +174,13 @@ __device__ bool rambo_point(const Params& a, long long ev, int attempt, double (
     }
     double xi = (xf > 0.0f && xf <= 1.0f) ? (double)xf : sqrt(1.0 - r * r);
     bool ok = false;
+    double e[kMaxFinal];  // energies at the converged xi (the loop stops before updating it)
     for (int it = 0; it < 50; ++it) {
         double f = -a.sqrt_s, fp = 0.0;
         for (int j = 0; j < n; ++j) {
-            const double e = sqrt(a.m[j] * a.m[j] + xi * xi * P2[j]);
-            f += e;
-            fp += xi * P2[j] / e;
+            e[j] = sqrt(a.m[j] * a.m[j] + xi * xi * P2[j]);
+            f += e[j];
+            fp += xi * P2[j] / e[j];
         }
         if (fabs(f) <= 1e-14 * a.sqrt_s) {
             ok = true;
@@ -188,18 +189,22 @@ __device__ bool rambo_point(const Params& a, long long ev, int attempt, double (
         xi -= f / fp;
     }
     if (!ok) return false;
-    double wt2 = 1.0, wt3 = 0.0;
+    // weight factors; the energies of the converged solve are reused, |k_j| is xi
+    // times the massless energy, and xi^(2n-3) is a product (FP64 square roots,
+    // divisions and pow cost dozens of FP64-pipe instructions each on GB300)
+    double wt2 = 1.0, wt3 = 0.0, xin = 1.0;
     for (int j = 0; j < n; ++j) {
-        const double k0 = sqrt(a.m[j] * a.m[j] + xi * xi * P2[j]);
+        const double k0 = e[j];
+        const double kk = xi * k[j][0];
         k[j][1] *= xi;
         k[j][2] *= xi;
         k[j][3] *= xi;
         k[j][0] = k0;
-        const double kk = xi * sqrt(P2[j]);
         wt2 *= kk / k0;
         wt3 += kk * kk / k0;
     }
-    w *= pow(xi, 2 * n - 3) * wt2 * a.sqrt_s / wt3;
+    for (int j = 0; j < 2 * n - 3; ++j) xin *= xi;
+    w *= xin * wt2 * a.sqrt_s / wt3;
     return true;
 }
 
