@@ -401,7 +401,7 @@ int me_good_helicities(const me_handle* h, int* out, int cap, int* n)
 int me_flops_per_event(const me_handle* h, double* chain_flops, double* colour_flops)
 {
     if (!h) return ME_EINVAL;
-    if (chain_flops) *chain_flops = (double)h->ngood * (double)h->proc->flops_hel;
+    if (chain_flops) *chain_flops = (double)h->ngood * (double)h->proc->flops_hel + (double)h->proc->table_flops;
     if (colour_flops) *colour_flops = (double)h->ngood * (double)h->proc->colour_flops_hel;
     return ME_OK;
 }

@@ -281,10 +281,11 @@ __device__ __forceinline__ FSum fsum_add(FSum a, FSum b)
     const float z = t - a.s;
     return {t, a.c + b.c + ((a.s - (t - z)) + (b.s - z))};
 }
-__device__ __forceinline__ FSum fsum_warp(FSum v)
+// over aligned groups of W lanes (W a power of two <= 32; 32: the whole warp)
+template <int W = 32> __device__ __forceinline__ FSum fsum_warp(FSum v)
 {
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
+    for (int off = W / 2; off > 0; off >>= 1) {
         const FSum o{__shfl_xor_sync(0xffffffffu, v.s, off), __shfl_xor_sync(0xffffffffu, v.c, off)};
         v = fsum_add(v, o);
     }

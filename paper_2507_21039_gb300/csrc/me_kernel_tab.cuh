@@ -293,15 +293,17 @@ __global__ void __launch_bounds__(P::NT * tab_epc<P, T>(), is_fp64<T>() ? P::MIN
             }
             __syncthreads();
             if (live) {
-                for (int it = tid; it < NL + 2 * NPAR; it += NT) {
+                for (int it = tid; it < NL + P::NEXT; it += NT) {
                     if (it < NL) sln[it] = line_data_split<P>(spf, sgram, it, m2);
-                    else tab.st(it - NL, ext_wavefunction_split<P>(spf, it - NL, mtf, a.gauge_ext));
+                    else if (it < NL + 2 * NPAR) tab.st(it - NL, ext_wavefunction_split<P>(spf, it - NL, mtf, a.gauge_ext));
+                    else tab.st(2 * NPAR, ew_coefficients<T>(smom));  // Drell-Yan: entry 2 NPAR
                 }
             }
         } else if (live) {
-            for (int it = tid; it < 2 * NPAR + NL; it += NT) {
+            for (int it = tid; it < P::NEXT + NL; it += NT) {
                 if (it < 2 * NPAR) tab.st(it, ext_wavefunction<P, T>(smom, it, a.mt, a.gauge_ext));
-                else sln[it - 2 * NPAR] = line_data<P, T>(smom, it - 2 * NPAR, a.mt);
+                else if (it < P::NEXT) tab.st(2 * NPAR, ew_coefficients<T>(smom));  // Drell-Yan: entry 2 NPAR
+                else sln[it - P::NEXT] = line_data<P, T>(smom, it - P::NEXT, a.mt);
             }
         }
         __syncthreads();
@@ -366,8 +368,11 @@ __global__ void __launch_bounds__(P::NT * tab_epc<P, T>(), is_fp64<T>() ? P::MIN
                 if (a.hel_out) a.hel_out[e * a.nlist + i] = (double)v * a.norm;
             }
         }
-        if constexpr (F32) facc = fsum_warp(facc);
-        for (int off = 16; off > 0; off >>= 1) {
+        // (events of fewer than 32 threads share a warp: reduce within each event's lanes)
+        constexpr int W = NT < 32 ? NT : 32;
+        static_assert((W & (W - 1)) == 0, "threads per event: a power of two below 32, or whole warps");
+        if constexpr (F32) facc = fsum_warp<W>(facc);
+        for (int off = W / 2; off > 0; off >>= 1) {
             if constexpr (!F32) acc += __shfl_xor_sync(0xffffffffu, acc, off);
             if constexpr (SDE) {
                 snum += __shfl_xor_sync(0xffffffffu, snum, off);

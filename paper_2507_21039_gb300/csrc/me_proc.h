@@ -35,8 +35,9 @@ struct ProcDesc {
     double iden;               // initial spin x colour average x final identical-particle factor
     int cden;                  // colour-matrix denominator (C = num / cden)
     const int* cnum;           // colour numerators [ncol][ncol] (host)
-    long long flops_hel;       // chain flops per helicity (generator count)
+    long long flops_hel;       // chain flops per evaluated helicity (generator count)
     long long colour_flops_hel;
+    long long table_flops;     // per event, helicity-independent (the helicity-recycled tables)
     int coupling_power;        // |M|^2 proportional to (4 pi alpha)^coupling_power
     cudaError_t (*launch)(int precision, const LaunchArgs&);
     const int* diag_lines;     // [ndiag][4] internal-line masks of each diagram (host), 0-padded

@@ -27,7 +27,13 @@ EXT_KINDS = {"VIN": 0, "VOUT": 1, "FO_U": 2, "FO_V": 3, "FI_U": 4, "FI_V": 5}
 # bit 3 = (descriptor kernel) each stage's table work runs beside the previous
 # stage's amplitudes (measured on GB300 over stage sizes, events per CTA and
 # fence intervals)
-TAB_PROCESSES = {"gg_ttxg": (32, 1, 1, 1, 0, 1, 4), "gg_ttxgg": (64, 2, 2, 5, 60, 7, 4)}
+TAB_PROCESSES = {"gg_ttxg": (32, 1, 1, 1, 0, 1, 4), "gg_ttxgg": (64, 2, 2, 5, 60, 7, 4),
+                 # Drell-Yan u u~ -> e+ e- + 2, 3 g (16 and 32 kept helicities; resident tables).
+                 # Measured FP32 |M|^2 kernel (2^20 / 2^18 events): n = 2 at 16 threads x 8 events,
+                 # fence 4: 2.75 ms (4 events 2.76, 16 events with fence 2 3.27, 32 threads 5.05; the
+                 # straight-line kernel 3.86); n = 3 at 32 x 2, fence 24: 3.21 ms (fence 4 3.63, 7 3.48,
+                 # 12 3.30, 60 3.40; 4 events 3.73; straight-line 5.15)
+                 "uux_epemgg": (16, 8, 4, 0, 0, 4, 4), "uux_epemggg": (32, 2, 2, 0, 0, 24, 4)}
 # processes evaluated with the staged descriptor kernel (me_kernel_interp.cuh)
 # process -> (threads per event, amplitudes per stage and schedule mode (as
 #             above) in FP32 / mixed, the same in FP64).  FP32 keeps J in shared
@@ -319,11 +325,15 @@ def emit_process(process: str) -> tuple[str, dict]:
     kernel_struct_d = "ProcInterpD" if IP else kernel_struct
     launch_fn = "launch_tab" if TP else ("launch_interp" if IP else "launch_scalar")
     nhel_all = 1 << npar
+    # chain flops per evaluated helicity, and the helicity-independent table
+    # flops per event (the table kernels compute every variant of every object
+    # once per event, however many helicities are kept)
+    table_flops_ev = 0
     if TP:
-        flops_hel = tab_amp_flops + -(-tab_flops // nhel_all)
+        flops_hel, table_flops_ev = tab_amp_flops, tab_flops
     elif IP:
-        flops_hel = IP.tab.amplitude_flops_per_helicity(not INTERP_PROCESSES[process][2] & 2) + \
-            -(-IP.table_flops // nhel_all)
+        flops_hel = IP.tab.amplitude_flops_per_helicity(not INTERP_PROCESSES[process][2] & 2)
+        table_flops_ev = IP.table_flops
     else:
         flops_hel = P.flops_per_helicity()
     tc_members, tc_array = "", ""
@@ -455,7 +465,7 @@ const ProcDesc* procdesc_{process}()
 {{
     static const ProcDesc d = {{"{process}", {npar}, {1 << npar}, {ncol}, {P.ndiagrams}, {len(P.amps)}, {k}, {nlines},
                                {threads}, {iden!r}, {den}, {ns}::h_cnum, {flops_hel}LL,
-                               {P.colour_flops_per_helicity()}LL, {cpow}, &{ns}::launch, {ns}::h_diag_lines,
+                               {P.colour_flops_per_helicity()}LL, {table_flops_ev}LL, {cpow}, &{ns}::launch, {ns}::h_diag_lines,
                                {ns}::h_diag_nlines, &{ns}::jscratch_per_cta, &{ns}::jscratch_ctas, {family}}};
     return &d;
 }}
@@ -470,6 +480,7 @@ const ProcDesc* procdesc_{process}()
         "ncol": ncol,
         "nlines": nlines,
         "flops_per_helicity": flops_hel,
+        "table_flops_per_event": table_flops_ev,
         "flops_per_helicity_unrecycled": P.flops_per_helicity(),
         "table_entries": TP.size if TP else 0,
         "colour_flops_per_helicity": P.colour_flops_per_helicity(),
@@ -498,6 +509,12 @@ def _table_call(kind, k="k"):
         c = f"VVV1A<{kind[-1]}, T>(tab.ld({k}.in0), tab.ld({k}.in1), ln[{k}.la].p, ln[{k}.lb].p, o);"
     elif kind in ("VVVV1A", "VVVV3A", "VVVV4A"):
         c = f"{kind}<T>(tab.ld({k}.in0), tab.ld({k}.in1), tab.ld({k}.in2), o);"
+    elif kind in ("ext_lepL", "ext_lepR"):  # Drell-Yan lepton pair: (ubar(e-), v(e+), coefficients)
+        other = "oR" if kind == "ext_lepL" else "oL"
+        outs = "o, oR" if kind == "ext_lepL" else "oL, o"
+        c = f"Wf<T> {other}; LEPLR<T>(tab.ld({k}.in0), tab.ld({k}.in1), tab.ld({k}.in2), {outs});"
+    elif kind in ("FFVLR_2", "FFVLR_1"):
+        c = f"{kind}<T>(tab.ld({k}.in0), tab.ld({k}.in1), tab.ld({k}.in2), ln[{k}.lo], o);"
     else:
         raise ValueError(kind)
     return f"Wf<T> o; {c} tab.st({k}.out, o);"

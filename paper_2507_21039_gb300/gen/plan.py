@@ -46,7 +46,8 @@ FLOPS = {
     "DOTV": 30, "DOTF": 30,
     # Drell-Yan insertion (massless quark line): the FFV1 routines with a second
     # 2x2 block and no mass terms; the lepton-pair objects of both chiralities
-    "FFVLR_0": 80, "FFVLR_2": 116, "FFVLR_1": 116, "ext_lepL": 176,
+    # (one call forms both: ext_lepR costs nothing beside ext_lepL in the chain)
+    "FFVLR_0": 80, "FFVLR_2": 116, "FFVLR_1": 116, "ext_lepL": 176, "ext_lepR": 0,
 }
 V4NAMES = ("VVVV1", "VVVV3", "VVVV4")
 

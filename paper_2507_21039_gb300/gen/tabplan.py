@@ -26,7 +26,15 @@ from __future__ import annotations
 
 from dataclasses import dataclass, field
 
-from .plan import FLOPS, Plan, amputate, build_plan, colour_groups
+from .plan import FLOPS, Plan, amputate, build_plan, build_plan_dy, colour_groups
+
+# Drell-Yan lepton-pair objects (both chiralities of the electroweak insertion):
+# functions of the e+ (particle 2) and e- (particle 3) states and the event's
+# electroweak coefficients, which sit at table entry 2 npar
+LEPTON_KINDS = ("ext_lepL", "ext_lepR")
+LEPTON_SUPPORT = (3, 2)
+# flops of one table task: a lepton-pair task forms both chiralities and stores one
+TASK_FLOPS = dict(FLOPS, ext_lepR=FLOPS["ext_lepL"])
 
 
 @dataclass
@@ -54,7 +62,7 @@ class TabPlan:
     amp_supports: list       # distinct supports of amplitude operands
 
     def table_flops(self) -> int:
-        return sum(FLOPS[r.kind] * len(r.tasks) for r in self.rounds)
+        return sum(TASK_FLOPS[r.kind] * len(r.tasks) for r in self.rounds)
 
     def amplitude_flops_per_helicity(self, grouped: bool = True) -> int:
         """amplitudes plus their accumulation into J; grouped: amplitudes with
@@ -77,7 +85,9 @@ def _support(P: Plan, i: int, memo: dict):
     if i in memo:
         return memo[i]
     op = P.ops[i]
-    if op.kind.startswith("ext_"):
+    if op.kind in LEPTON_KINDS:
+        s = LEPTON_SUPPORT
+    elif op.kind.startswith("ext_"):
         s = (op.ext,)
     else:
         acc = set()
@@ -93,40 +103,54 @@ def compress(full_bits: dict, support) -> int:
     return sum(full_bits[p] << j for j, p in enumerate(support))
 
 
+def _plan_of(process: str) -> Plan:
+    from .emit import DY_PROCESSES  # the Drell-Yan process names and their gluon counts
+
+    return build_plan_dy(DY_PROCESSES[process]) if process in DY_PROCESSES else build_plan(process)
+
+
 def build_tabplan(process: str, amputated: bool = False) -> TabPlan:
     """amputated: every amplitude becomes a contraction of two table objects
-    (plan.amputate), the vertex objects joining the table."""
-    P = build_plan(process)
+    (plan.amputate), the vertex objects joining the table.  Drell-Yan: the
+    lepton-pair objects are table objects of support {e+, e-} (level 1), the
+    electroweak coefficients table entry 2 npar."""
+    P = _plan_of(process)
     memo = {}
     sup = {i: _support(P, i, memo) for i in range(len(P.ops))}
     if amputated:
         P = amputate(P, sup)
         memo = {}
         sup = {i: _support(P, i, memo) for i in range(len(P.ops))}
+    external = lambda op: op.kind.startswith("ext_") and op.kind not in LEPTON_KINDS
+    dy = any(op.kind in LEPTON_KINDS for op in P.ops)
     base = {}
     for i, op in enumerate(P.ops):
-        if op.kind.startswith("ext_"):
+        if external(op):
             base[i] = 2 * op.ext
-    nxt = 2 * P.npar
+    ew = 2 * P.npar  # Drell-Yan: the electroweak coefficients' entry
+    nxt = 2 * P.npar + (1 if dy else 0)
     level = {}
     for i, op in enumerate(P.ops):
-        if op.kind.startswith("ext_"):
+        if external(op):
             level[i] = 0
         else:
-            level[i] = 1 + max(level[a] for a in op.args)
-        if op.out != "A" and not op.kind.startswith("ext_"):
+            level[i] = 1 + max([level[a] for a in op.args] or [0])
+        if op.out != "A" and not external(op):
             base[i] = nxt
             nxt += 1 << len(sup[i])
     rounds = {}
     for i, op in enumerate(P.ops):
-        if op.out == "A" or op.kind.startswith("ext_"):
+        if op.out == "A" or external(op):
             continue
         key = (level[i], op.kind)
         r = rounds.setdefault(key, Round(level[i], op.kind))
         S = sup[i]
         for v in range(1 << len(S)):
             bits = {p: (v >> j) & 1 for j, p in enumerate(S)}
-            ins = tuple(base[a] + compress(bits, sup[a]) for a in op.args)
+            if op.kind in LEPTON_KINDS:  # (ubar(e-), v(e+), coefficients), as the straight-line chain passes them
+                ins = (2 * 3 + bits[3], 2 * 2 + bits[2], ew)
+            else:
+                ins = tuple(base[a] + compress(bits, sup[a]) for a in op.args)
             if op.kind == "VVV1P0_1" or op.kind.startswith("VVV1A"):
                 ln = (op.mom[0], op.mom[1], op.line)
             else:
