@@ -400,6 +400,47 @@ int main(int argc, char** argv) {
             assert abs(a - th - tl) < 2.0 ** -47 * a
 
 
+@pytest.mark.parametrize("process", ["uux_epemgg", "uux_epemggg"])
+def test_drell_yan_table_plan_layout(process):
+    """Drell-Yan on the helicity-recycled table kernel: the lepton-pair objects
+    have support {e+, e-} and read the e- and e+ states of their variant and the
+    electroweak coefficients at entry 2 npar, which no object overwrites; every
+    task's inputs are externals, that entry or objects of an earlier level;
+    every index (tasks and amplitude operands) lies inside the table."""
+    from paper_2507_21039_gb300.gen.tabplan import LEPTON_KINDS, build_tabplan
+
+    T = build_tabplan(process)
+    P = T.plan
+    npar, size = P.npar, T.size
+    ew = 2 * npar
+    level_of = {}
+    for r in T.rounds:
+        for t in r.tasks:
+            assert ew < t.out < size and t.out not in level_of
+            level_of[t.out] = r.level
+    for r in T.rounds:
+        for v, t in enumerate(sorted(r.tasks, key=lambda x: x.out)):
+            if r.kind in LEPTON_KINDS:
+                assert r.level == 1 and len(t.ins) == 3 and t.ins[2] == ew
+                assert t.ins[0] in (6, 7) and t.ins[1] in (4, 5)  # ubar(e-), v(e+) entries 2e + b
+            for x in t.ins:
+                assert 0 <= x < size
+                if x > ew:
+                    assert level_of[x] < r.level
+    for i, op in enumerate(P.ops):
+        if op.kind in LEPTON_KINDS:
+            # variant v = b(e-) + 2 b(e+) (support particles in descending order)
+            assert T.support[i] == (3, 2)
+            lo = T.base[i]
+            tasks = {t.out: t.ins for r in T.rounds if r.kind == op.kind for t in r.tasks}
+            assert set(tasks) == set(range(lo, lo + 4))
+            for v in range(4):
+                assert tasks[lo + v] == (6 + (v & 1), 4 + (v >> 1), ew)
+    for ai, _ in P.amps:
+        for a in P.ops[ai].args:
+            assert 0 <= T.base[a] and T.base[a] + (1 << len(T.support[a])) <= size
+
+
 def test_stage_sign_matrices_replay_the_flow_updates():
     """The FP32 descriptor kernel accumulates J on the tensor cores: per stage,
     Re J += Im G . B and Im J += Re G . (-B), G the stage's group sums in update
