@@ -52,6 +52,13 @@
 #ifndef ME_INTERP_HPAIR
 #define ME_INTERP_HPAIR 1
 #endif
+// Build option ME_INTERP_HPAIR64: the FP64 kernel (J in a global scratch) also
+// runs two threads per helicity, each with its own copy of J, summed in the
+// colour form (1), or one thread per helicity (0, default: measured on GB300
+// for gg -> t t~ g g g, 20.0 k against 19.4 k events/s, for twice the scratch)
+#ifndef ME_INTERP_HPAIR64
+#define ME_INTERP_HPAIR64 0
+#endif
 // Build option ME_INTERP_A_MMAJOR: the group-sum operands A in the M-major
 // layout (1, default: a warp's 32 rows of one column on distinct banks) or
 // K-major (0: the four row groups of a warp on the same banks, 4-way conflicts)
@@ -81,7 +88,10 @@ struct __align__(16) IStage {
     unsigned short amp_mid, slot_mid;
     // 1: the stage's table rounds run beside the previous stage's amplitudes
     // (their slots are not read there); 0: in a phase of their own
-    unsigned short ahead, pad;
+    unsigned short ahead;
+    // colour terms of the groups before amp_mid (J updated flow by flow: the
+    // second thread's first term is stage_term_begin + term_mid)
+    unsigned short term_mid;
 };
 struct __align__(16) IAmp {
     unsigned short op[4];
@@ -116,7 +126,8 @@ template <class P, class T> struct InterpLayout {
     // threads per CTA: one per helicity, or two with J in tensor memory (the
     // second takes the later colour groups of each stage); register budget for
     // two resident CTAs when J is in tensor memory
-    static constexpr int NTH = (J_MMA && ME_INTERP_HPAIR) ? 2 * P::NT : P::NT;
+    static constexpr bool J_GLOBAL = !J_MMA && !J_IN_SMEM;
+    static constexpr int NTH = ((J_MMA && ME_INTERP_HPAIR) || (J_GLOBAL && ME_INTERP_HPAIR64)) ? 2 * P::NT : P::NT;
     static constexpr int MIN_CTAS = J_MMA ? 2 : 1;
     // J_MMA operands: six A matrices (BF16 hi / mid / lo of Im G and Re G, 128 x 16
     // each, ABYTES apart) and the stage's sign matrix B (128 flows x 16, 4096 bytes)
@@ -190,7 +201,8 @@ __global__ void __launch_bounds__(InterpLayout<P, T>::NTH, InterpLayout<P, T>::M
     // memory), or TMEM columns c (Re) and 128 + c (Im) of its lane from tj
     cx<T>* jp = nullptr;
     if constexpr (L::J_IN_SMEM) jp = reinterpret_cast<cx<T>*>(smem + L::jsm) + threadIdx.x;
-    else if constexpr (!L::J_MMA) jp = jglobal + (size_t)blockIdx.x * NCOL * NT + threadIdx.x;
+    else if constexpr (!L::J_MMA)  // one copy per helicity thread (two copies per CTA with helicity pairs)
+        jp = jglobal + ((size_t)blockIdx.x * (NTH / NT) + threadIdx.x / NT) * NCOL * NT + (threadIdx.x & (NT - 1));
     __shared__ double red[NTH / 32];
     __shared__ FSum fred[NTH / 32];
     __shared__ double red_sde[SDE ? 2 : 1][NTH / 32];
@@ -314,6 +326,7 @@ __global__ void __launch_bounds__(InterpLayout<P, T>::NTH, InterpLayout<P, T>::M
                 } else {
                     amp_lo = st.amp_mid;
                     slot = st.slot_mid;
+                    term += st.term_mid;
                 }
             }
             if constexpr (L::J_MMA) {
@@ -564,6 +577,25 @@ __global__ void __launch_bounds__(InterpLayout<P, T>::NTH, InterpLayout<P, T>::M
         } else if constexpr (TC) {
             v = colour_tc_smem<NCOL, NT, P::NSPLIT>(reinterpret_cast<const cx<float>*>(smem + L::jsm), P::bfrag(),
                                                     rowv, tid);
+        } else if constexpr (NTH > NT) {
+            // J of a helicity is the sum of its two threads' copies (half 1's copy
+            // follows half 0's): the first thread forms the colour sum
+            __syncthreads();
+            if (!half) {
+                const cx<T>* j1 = jp + (size_t)NCOL * NT;
+                C w = C(0);
+                for (int i = 0; i < NCOL; ++i) {
+                    const cx<T> ji = {jp[i * NT].re + j1[i * NT].re, jp[i * NT].im + j1[i * NT].im};
+                    C zr = C(0), zi = C(0);
+                    for (int j = i; j < NCOL; ++j) {
+                        const C n = (C)P::cnum2(i, j);
+                        zr = fma(n, (C)(jp[j * NT].re + j1[j * NT].re), zr);
+                        zi = fma(n, (C)(jp[j * NT].im + j1[j * NT].im), zi);
+                    }
+                    w = fma((C)ji.re, zr, fma((C)ji.im, zi, w));
+                }
+                v = (T)w;
+            }
         } else {
             v = colour_scalar(jp, NT);
         }
@@ -634,7 +666,7 @@ __global__ void __launch_bounds__(InterpLayout<P, T>::NTH, InterpLayout<P, T>::M
 template <class P, class T> constexpr size_t interp_jscratch_per_cta()
 {
     using L = InterpLayout<P, T>;
-    return (!L::J_IN_SMEM && !L::J_MMA) ? sizeof(cx<T>) * (size_t)P::NCOL * P::NT : 0;
+    return L::J_GLOBAL ? sizeof(cx<T>) * (size_t)P::NCOL * P::NT * (L::NTH / P::NT) : 0;
 }
 
 // One-time kernel attributes and the number of resident CTAs per SM of the

@@ -886,7 +886,8 @@ def emit_interp_struct(process: str, nt: int, stage_amps: int, num, mode: int = 
                 assert col < 128
                 img[umma_k16_offset(col, k) // 2] = 0x3F80 if c == (0, -1) else 0xBF80
         bmat += [img[i] | (img[i + 1] << 16) for i in range(0, 2048, 2)]
-        stages.append((r0, len(rounds), a0, len(amps), a0 + st.mid, st.slot_mid, int(st.ahead)))
+        term_mid = sum(len(I.flush[ai]) for ai in st.amps[:st.mid] if ai in I.flush)
+        stages.append((r0, len(rounds), a0, len(amps), a0 + st.mid, st.slot_mid, int(st.ahead), term_mid))
     masks = []
     for S in I.supports:
         m = 0
@@ -915,7 +916,7 @@ def emit_interp_struct(process: str, nt: int, stage_amps: int, num, mode: int = 
     src = ""
     src += arr("c_itasks", "TabTask", tasks, lambda t: "{%d, %d, %d, %d, %d, %d, %d, 0, 0}" % t, 4)
     src += arr("c_rounds", "IRound", rounds, lambda r: "{%du, %d, %d, %d}" % r, 8)
-    src += arr("c_stages", "IStage", stages, lambda r: "{%d, %d, %d, %d, %d, %d, %d, 0}" % r, 4)
+    src += arr("c_stages", "IStage", stages, lambda r: "{%d, %d, %d, %d, %d, %d, %d, %d}" % r, 4)
     src += arr("c_amps", "IAmp", amps, lambda a: "{{%d, %d, %d, %d}, {%d, %d, %d, %d}, %d, %d, %d, %d}" % (
         *a[0], *a[1], a[2], a[3], a[4], a[5]), 3)
     src += arr("c_terms", "unsigned short", terms, lambda x: "%d" % x, 16)

@@ -226,7 +226,7 @@ def test_stage_split_between_the_threads_of_a_helicity():
     amplitudes are shared out at a colour-group boundary.  Every stage closes
     all its groups (no group sum stays open across a stage), the split point
     lies on a group boundary, the second thread's first update slot counts the
-    groups before it, the halves are balanced to within the largest group, and
+    groups before it and its first colour term their terms, the halves are balanced to within the largest group, and
     the emitted stage descriptors carry the split."""
     from paper_2507_21039_gb300.gen.emit import INTERP_PROCESSES, emit_interp_struct
     from paper_2507_21039_gb300.gen.interp import FLOPS, FLUSH_COST
@@ -235,7 +235,8 @@ def test_stage_split_between_the_threads_of_a_helicity():
     src, I = emit_interp_struct("gg_ttxggg", nt, sf, colour_matrix(5)[0], mf)
     P = I.tab.plan
     body = re.search(r"c_stages\[\d+\] = \{(.*?)\n\};", src, re.S).group(1)
-    rows = [tuple(int(x) for x in r) for r in re.findall(r"\{(\d+), (\d+), (\d+), (\d+), (\d+), (\d+), \d+, 0\}", body)]
+    rows = [tuple(int(x) for x in r)
+            for r in re.findall(r"\{(\d+), (\d+), (\d+), (\d+), (\d+), (\d+), \d+, (\d+)\}", body)]
     assert len(rows) == len(I.stages)
     a0 = 0
     for st, row in zip(I.stages, rows):
@@ -243,7 +244,9 @@ def test_stage_split_between_the_threads_of_a_helicity():
         assert 0 < len(amps) <= sf and amps[-1] in I.flush
         assert st.mid == 0 or amps[st.mid - 1] in I.flush
         assert st.slot_mid == sum(1 for a in amps[:st.mid] if a in I.flush)
-        assert row[2:] == (a0, a0 + len(amps), a0 + st.mid, st.slot_mid)
+        # the second thread's first colour term (J updated flow by flow in FP64)
+        term_mid = sum(len(I.flush[a]) for a in amps[:st.mid] if a in I.flush)
+        assert row[2:] == (a0, a0 + len(amps), a0 + st.mid, st.slot_mid, term_mid)
         cost = [FLOPS[P.ops[P.amps[a][0]].kind] + (FLUSH_COST if a in I.flush else 0) for a in amps]
         ends = [i + 1 for i, a in enumerate(amps) if a in I.flush]
         best = min(max(sum(cost[:m]), sum(cost[m:])) for m in ends)
@@ -268,7 +271,7 @@ def test_table_work_ahead_never_overwrites_live_entries():
     assert I.table_size <= _interp_table_cap("gg_ttxggg", nt)
     assert sum(st.ahead for st in I.stages) > 0.9 * len(I.stages) and not I.stages[0].ahead
     body = re.search(r"c_stages\[\d+\] = \{(.*?)\n\};", src, re.S).group(1)
-    flags = [int(f) for f in re.findall(r"\{\d+, \d+, \d+, \d+, \d+, \d+, (\d+), 0\}", body)]
+    flags = [int(f) for f in re.findall(r"\{\d+, \d+, \d+, \d+, \d+, \d+, (\d+), \d+\}", body)]
     assert flags == [int(st.ahead) for st in I.stages]
 
     def obj_range(x):
