@@ -34,7 +34,7 @@ KERNELS = {"ee_mumu": "me_kernel_scalar<ee_mumu, float>", "gg_ttx": "me_kernel_s
            "gg_ttxg": "me_kernel_tab<gg_ttxg, float>", "gg_ttxgg": "me_kernel_tab<gg_ttxgg, float>",
            "gg_ttxggg": "me_kernel_interp<gg_ttxggg, float>",
            "uux_epem": "me_kernel_scalar<uux_epem, float>", "uux_epemg": "me_kernel_scalar<uux_epemg, float>",
-           "uux_epemgg": "me_kernel_scalar<uux_epemgg, float>", "uux_epemggg": "me_kernel_scalar<uux_epemggg, float>"}
+           "uux_epemgg": "me_kernel_tab<uux_epemgg, float>", "uux_epemggg": "me_kernel_tab<uux_epemggg, float>"}
 PROCESS_LABEL = {"ee_mumu": "e+ e- -> mu+ mu-", "gg_ttx": "g g -> t t~", "gg_ttxg": "g g -> t t~ g",
                  "gg_ttxgg": "g g -> t t~ g g", "gg_ttxggg": "g g -> t t~ g g g",
                  "uux_epem": "u u~ -> e+ e-", "uux_epemg": "u u~ -> e+ e- g", "uux_epemgg": "u u~ -> e+ e- g g",

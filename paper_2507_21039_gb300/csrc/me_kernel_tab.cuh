@@ -358,6 +358,7 @@ __global__ void __launch_bounds__(P::NT * tab_epc<P, T>(), is_fp64<T>() ? P::MIN
             } else {
                 v = colour_as<P, T, C>(J);
             }
+            if (!P::hel_allowed(h)) v = T(0);  // vanishes exactly; its table variants were not computed
             if (act) {
                 if constexpr (F32) facc = fsum_add(facc, FSum{(float)v, 0.0f});
                 else acc += (double)v;

@@ -650,6 +650,14 @@ def _variant_code(npar, supports):
     return bits + sups
 
 
+def _allowed_expr(TP):
+    """C expression of the helicity index h: every pair of TP.opposite_pairs has
+    different helicity bits (particle p's bit is bit npar - 1 - p of h)"""
+    n = TP.plan.npar
+    terms = [f"(((h >> {n - 1 - a}) ^ (h >> {n - 1 - b})) & 1)" for a, b in TP.opposite_pairs]
+    return " && ".join(terms) if terms else "true"
+
+
 def emit_tab_struct(process: str, nt: int, epc_f: int, epc_d: int, amputated: int, stage: int,
                     fence_f: int, fence_d: int, ncol: int, nlines: int, colour_body: list):
     """ProcTab: task table, table rounds and per-helicity amplitudes.
@@ -776,6 +784,9 @@ struct ProcTab : Proc {{
     static constexpr long long TABLE_FLOPS = {table_flops}LL, AMP_FLOPS = {amp_flops}LL;
     // warp fence every n amplitudes (FP32, FP64)
     static constexpr int FENCE_F = {fence_f}, FENCE_D = {fence_d};
+    // helicities that can be non-zero; the others are exactly 0 and the table
+    // variants only they would read are not computed
+    __device__ static __forceinline__ bool hel_allowed(int h) {{ (void)h; return {_allowed_expr(TP)}; }}
 {body}
 }};
 """

@@ -33,6 +33,13 @@ from .plan import FLOPS, Plan, amputate, build_plan, build_plan_dy, colour_group
 # electroweak coefficients, which sit at table entry 2 npar
 LEPTON_KINDS = ("ext_lepL", "ext_lepR")
 LEPTON_SUPPORT = (3, 2)
+# Drell-Yan with massless fermions: helicity conservation along the quark line
+# (u, u~ = particles 0, 1) and the lepton pair (2, 3) makes every configuration
+# with equal helicity bits in either pair vanish exactly.  Variants of an object
+# whose support holds both members of a pair with equal bits are never read by
+# a non-vanishing helicity; they are not computed (the kernel returns 0 for
+# the vanishing helicities, ProcTab::hel_allowed)
+DY_OPPOSITE_PAIRS = ((0, 1), (2, 3))
 # flops of one table task: a lepton-pair task forms both chiralities and stores one
 TASK_FLOPS = dict(FLOPS, ext_lepR=FLOPS["ext_lepL"])
 
@@ -60,6 +67,7 @@ class TabPlan:
     rounds: list             # Round, in dependency order
     nlevels: int
     amp_supports: list       # distinct supports of amplitude operands
+    opposite_pairs: tuple = ()  # particle pairs whose helicity bits must differ (else |M_h|^2 = 0)
 
     def table_flops(self) -> int:
         return sum(TASK_FLOPS[r.kind] * len(r.tasks) for r in self.rounds)
@@ -138,6 +146,7 @@ def build_tabplan(process: str, amputated: bool = False) -> TabPlan:
         if op.out != "A" and not external(op):
             base[i] = nxt
             nxt += 1 << len(sup[i])
+    pairs = DY_OPPOSITE_PAIRS if dy else ()
     rounds = {}
     for i, op in enumerate(P.ops):
         if op.out == "A" or external(op):
@@ -147,6 +156,8 @@ def build_tabplan(process: str, amputated: bool = False) -> TabPlan:
         S = sup[i]
         for v in range(1 << len(S)):
             bits = {p: (v >> j) & 1 for j, p in enumerate(S)}
+            if any(a in bits and b in bits and bits[a] == bits[b] for a, b in pairs):
+                continue  # read only by vanishing helicities
             if op.kind in LEPTON_KINDS:  # (ubar(e-), v(e+), coefficients), as the straight-line chain passes them
                 ins = (2 * 3 + bits[3], 2 * 2 + bits[2], ew)
             else:
@@ -158,4 +169,5 @@ def build_tabplan(process: str, amputated: bool = False) -> TabPlan:
             r.tasks.append(Task(base[i] + v, ins, ln))
     order = sorted(rounds, key=lambda k: (k[0], k[1]))
     amp_sup = sorted({sup[a] for ai, _ in P.amps for a in P.ops[ai].args}, key=lambda s: (len(s), s))
-    return TabPlan(P, sup, base, nxt, [rounds[k] for k in order], max(k[0] for k in order) if order else 0, amp_sup)
+    return TabPlan(P, sup, base, nxt, [rounds[k] for k in order], max(k[0] for k in order) if order else 0, amp_sup,
+                   pairs)

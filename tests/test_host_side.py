@@ -408,8 +408,10 @@ def test_drell_yan_table_plan_layout(process):
     """Drell-Yan on the helicity-recycled table kernel: the lepton-pair objects
     have support {e+, e-} and read the e- and e+ states of their variant and the
     electroweak coefficients at entry 2 npar, which no object overwrites; every
-    task's inputs are externals, that entry or objects of an earlier level;
-    every index (tasks and amplitude operands) lies inside the table."""
+    task's inputs are externals, that entry or computed variants of objects of
+    an earlier level; every index (tasks and amplitude operands) lies inside the
+    table; every variant that a non-vanishing helicity (opposite u, u~ and
+    opposite e+, e- bits) reads is computed."""
     from paper_2507_21039_gb300.gen.tabplan import LEPTON_KINDS, build_tabplan
 
     T = build_tabplan(process)
@@ -435,13 +437,26 @@ def test_drell_yan_table_plan_layout(process):
             # variant v = b(e-) + 2 b(e+) (support particles in descending order)
             assert T.support[i] == (3, 2)
             lo = T.base[i]
+            # only the opposite-helicity variants (v = 1, 2) are computed: equal e+, e-
+            # helicities give exactly zero
             tasks = {t.out: t.ins for r in T.rounds if r.kind == op.kind for t in r.tasks}
-            assert set(tasks) == set(range(lo, lo + 4))
-            for v in range(4):
+            assert set(tasks) == {lo + 1, lo + 2}
+            for v in (1, 2):
                 assert tasks[lo + v] == (6 + (v & 1), 4 + (v >> 1), ew)
     for ai, _ in P.amps:
         for a in P.ops[ai].args:
             assert 0 <= T.base[a] and T.base[a] + (1 << len(T.support[a])) <= size
+    from paper_2507_21039_gb300.gen.tabplan import compress
+
+    computed = set(level_of)
+    for h in range(1 << npar):
+        bits = {p: (h >> (npar - 1 - p)) & 1 for p in range(npar)}
+        if bits[0] == bits[1] or bits[2] == bits[3]:
+            continue
+        for ai, _ in P.amps:
+            for a in P.ops[ai].args:
+                if T.base[a] > ew:
+                    assert T.base[a] + compress(bits, T.support[a]) in computed
 
 
 def test_stage_sign_matrices_replay_the_flow_updates():
