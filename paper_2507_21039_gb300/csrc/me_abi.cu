@@ -10,6 +10,7 @@
 #include <new>
 
 #include "me.h"
+#include "me_pool.h"
 #include "me_proc.h"
 
 using me::LaunchArgs;
@@ -240,7 +241,7 @@ int check_finite(const double* d_mom, int64_t n, cudaStream_t st)
 {
     unsigned long long* d_bad = nullptr;
     unsigned long long bad = 0;
-    if (cudaMallocAsync(&d_bad, sizeof(unsigned long long), st) != cudaSuccess) return ME_ENOMEM;
+    if (me::staging_alloc(&d_bad, sizeof(unsigned long long), st) != cudaSuccess) return ME_ENOMEM;
     int rc = ME_OK;
     if (cudaMemsetAsync(d_bad, 0, sizeof(unsigned long long), st) != cudaSuccess) rc = ME_ECUDA;
     if (rc == ME_OK) {
@@ -452,9 +453,9 @@ static int sigmakin_host_pipelined(me_handle* h, const double* momenta, int64_t 
     }
     const int64_t per = 4 * (int64_t)h->proc->npar;  // doubles per event
     double *d_mom = nullptr, *d_me2 = nullptr;
-    if (cudaMallocAsync(&d_mom, sizeof(double) * per * nevt, st) != cudaSuccess) return ME_ENOMEM;
+    if (me::staging_alloc(&d_mom, sizeof(double) * per * nevt, st) != cudaSuccess) return ME_ENOMEM;
     int rc = ME_OK;
-    if (cudaMallocAsync(&d_me2, sizeof(double) * nevt, st) != cudaSuccess) rc = ME_ENOMEM;
+    if (me::staging_alloc(&d_me2, sizeof(double) * nevt, st) != cudaSuccess) rc = ME_ENOMEM;
     if (rc == ME_OK && cudaEventRecord(h->fork, st) != cudaSuccess) rc = ME_ECUDA;
     for (int i = 0; i < 2 && rc == ME_OK; ++i)
         if (cudaStreamWaitEvent(h->pipe[i], h->fork, 0) != cudaSuccess) rc = ME_ECUDA;
@@ -512,10 +513,10 @@ static int sigmakin_impl(me_handle* h, const double* momenta, int64_t nevt, doub
     double *d_mom = nullptr, *d_me2 = nullptr;
     int rc = ME_OK;
     if (!dm) {
-        if (cudaMallocAsync(&d_mom, mbytes, st) != cudaSuccess) return ME_ENOMEM;
+        if (me::staging_alloc(&d_mom, mbytes, st) != cudaSuccess) return ME_ENOMEM;
         if (cudaMemcpyAsync(d_mom, momenta, mbytes, cudaMemcpyHostToDevice, st) != cudaSuccess) rc = ME_ECUDA;
     }
-    if (rc == ME_OK && !dr && cudaMallocAsync(&d_me2, sizeof(double) * nevt, st) != cudaSuccess) rc = ME_ENOMEM;
+    if (rc == ME_OK && !dr && me::staging_alloc(&d_me2, sizeof(double) * nevt, st) != cudaSuccess) rc = ME_ENOMEM;
     const double* mom_use = dm ? momenta : d_mom;
     double* me2_use = dr ? me2 : d_me2;
     if (rc == ME_OK && h->check_finite) rc = check_finite(mom_use, (int64_t)(mbytes / sizeof(double)), st);
@@ -584,9 +585,9 @@ int me_sigmakin_hsample(me_handle* h, const double* momenta, int64_t nevt, const
     }
     short* d_hel_ev = nullptr;
     double* d_w_ev = nullptr;
-    if (cudaMallocAsync(&d_hel_ev, sizeof(short) * nevt, st) != cudaSuccess) return ME_ENOMEM;
+    if (me::staging_alloc(&d_hel_ev, sizeof(short) * nevt, st) != cudaSuccess) return ME_ENOMEM;
     int rc = ME_OK;
-    if (cudaMallocAsync(&d_w_ev, sizeof(double) * nevt, st) != cudaSuccess) rc = ME_ENOMEM;
+    if (me::staging_alloc(&d_w_ev, sizeof(double) * nevt, st) != cudaSuccess) rc = ME_ENOMEM;
     if (rc == ME_OK) {
         hsample_select<<<(unsigned)((nevt + 255) / 256), 256, 0, st>>>(u, nevt, h->d_hs, h->ngood, h->d_hel, d_hel_ev,
                                                                        d_w_ev, hel);

@@ -38,6 +38,7 @@
 #include <algorithm>
 
 #include "me_kernel_tab.cuh"
+#include "me_pool.h"
 #include "me_tmem.cuh"
 
 // Build option ME_INTERP_J_MMA: FP32 colour-flow vector accumulated by the
@@ -734,7 +735,7 @@ template <class P, class T, bool TC = false, class C = T, bool SDE = false> cuda
             if (grid > fit) grid = fit;
             jg = static_cast<cx<T>*>(a.jscratch);
         } else {
-            e = cudaMallocAsync(&jg, per * (size_t)grid, a.stream);
+            e = staging_alloc(&jg, per * (size_t)grid, a.stream);
             if (e != cudaSuccess) return e;
             own = true;
         }

@@ -11,6 +11,7 @@
 #include <cstdint>
 
 #include "me.h"
+#include "me_pool.h"
 
 namespace {
 
@@ -329,11 +330,11 @@ extern "C" int rambo_sample(uint64_t seed, int64_t ev0, int64_t nevt, double sqr
     double *d_m = nullptr, *d_w = nullptr;
     unsigned long long* d_fail = nullptr;
     int rc = ME_OK;
-    if (!dev_m && cudaMallocAsync(&d_m, mbytes, st) != cudaSuccess) return ME_ENOMEM;
-    if (weights_out && !dev_w && cudaMallocAsync(&d_w, sizeof(double) * nevt, st) != cudaSuccess) rc = ME_ENOMEM;
+    if (!dev_m && me::staging_alloc(&d_m, mbytes, st) != cudaSuccess) return ME_ENOMEM;
+    if (weights_out && !dev_w && me::staging_alloc(&d_w, sizeof(double) * nevt, st) != cudaSuccess) rc = ME_ENOMEM;
     const bool want_fail = nfail_out != nullptr || !dev_m || !dev_w;
     if (rc == ME_OK && want_fail) {
-        if (cudaMallocAsync(&d_fail, sizeof(unsigned long long), st) != cudaSuccess) rc = ME_ENOMEM;
+        if (me::staging_alloc(&d_fail, sizeof(unsigned long long), st) != cudaSuccess) rc = ME_ENOMEM;
         else if (cudaMemsetAsync(d_fail, 0, sizeof(unsigned long long), st) != cudaSuccess) rc = ME_ECUDA;
     }
     a.mom = dev_m ? momenta_out : d_m;
