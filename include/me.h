@@ -30,11 +30,18 @@
  *     results are in the caller's buffer.
  *   - the caller owns every buffer it passes; the library never keeps a
  *     pointer to it after the call.  The handle owns its device state.
+ *   - temporary device buffers (the staging of host buffers, per-launch
+ *     scratch) are stream-ordered allocations from a pool per device that the
+ *     library creates on first use and keeps until the process exits; freed
+ *     memory stays reserved in it for later calls (at most the largest set of
+ *     buffers in flight at once, e.g. about 400 MB after a host-buffer call on
+ *     2^20 gg -> t t~ g g events).  While a stream is captured into a graph
+ *     they come from the default pool instead.
  *   - every call returns 0 on success or a negative ME_E* code; nothing
  *     throws across the ABI.  nevt == 0 is a no-op returning 0.
  *   - handles are independent; one handle must not be used from two host
- *     threads at the same time.  The only global mutable state is the fixed
- *     scratch array of me_filter_helicities_noalloc.
+ *     threads at the same time.  The global mutable state is the fixed
+ *     scratch array of me_filter_helicities_noalloc and that pool.
  */
 #ifndef LIBME_ME_H
 #define LIBME_ME_H
