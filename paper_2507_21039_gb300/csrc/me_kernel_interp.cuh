@@ -192,7 +192,9 @@ __global__ void __launch_bounds__(InterpLayout<P, T>::NTH, InterpLayout<P, T>::M
 {
     using L = InterpLayout<P, T>;
     constexpr int NTH = L::NTH;
-    extern __shared__ __align__(1024) unsigned char smem[];
+    // (the operand offsets inside are multiples of 1024 from the base; the
+    // unswizzled tensor-core operands need 16-byte alignment only)
+    extern __shared__ __align__(16) unsigned char smem[];
     constexpr int NPAR = P::NPAR, NL = P::NLINES, NT = P::NT, NCOL = P::NCOL;
     double* smom = reinterpret_cast<double*>(smem + L::mom);
     Ln<T>* sln = reinterpret_cast<Ln<T>*>(smem + L::lines);

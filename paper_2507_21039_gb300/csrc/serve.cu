@@ -87,16 +87,6 @@ int npar_of(const char* process)
     return pd && pd->npar <= kMaxPar ? pd->npar : 0;
 }
 
-bool is_pinned(const void* p)
-{
-    cudaPointerAttributes at;
-    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
-        cudaGetLastError();
-        return false;
-    }
-    return at.type == cudaMemoryTypeHost;
-}
-
 }  // namespace
 
 struct srv_server {
