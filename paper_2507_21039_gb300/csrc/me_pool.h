@@ -1,7 +1,7 @@
 // Temporary device buffers of the library (host-buffer staging, per-launch
 // scratch) come from a private stream-ordered memory pool per device whose
 // release threshold is unlimited: freed memory stays reserved for the next
-// call instead of going back to the driver at every synchronisation, which the
+// call instead of going back to the CUDA driver at every synchronisation, which the
 // default pool (threshold 0) does, so that a repeated call maps no memory
 // again.  The pool holds at most the largest set of buffers that were in
 // flight at once; it lives until the process exits.
