@@ -80,6 +80,37 @@ def test_dy_full_size_sampled(orc):
     assert np.all(np.isfinite(got)) and np.all(got > 0)
 
 
+def test_dy_full_size_sampled_gg(orc):
+    """The 2^20-event u u~ -> e+ e- gg batch of the benchmark workload in one
+    launch (table kernel, FP32): sampled events against the oracle one by one."""
+    name = "uux_epemgg"
+    w = DY_WORKLOADS[name]
+    mom = oracle_events(orc, name, w.nevt)
+    got = gpu_me2(name, "fp32", mom)
+    idx = np.unique(np.r_[0, w.nevt - 1, np.random.default_rng(4).integers(0, w.nevt, 60)])
+    ref = orc.dy_me2(2, mom[idx], alpha_s=ALPHA_S)
+    rel = np.abs(got[idx] / ref - 1)
+    assert np.median(rel) <= LOW_MEDIAN and rel.max() <= LOW_MAX
+    assert np.all(np.isfinite(got)) and np.all(got > 0)
+
+
+@pytest.mark.parametrize("name", list(NGLUON))
+def test_dy_kept_helicities_conserve_helicity(orc, name):
+    """The FP64 helicity filter keeps exactly the configurations with opposite
+    u, u~ and opposite e+, e- helicity bits (massless fermions: the others vanish
+    exactly), 2 x 2 x 2^n of them; the table kernels compute only the table
+    variants these read."""
+    npar = DY_WORKLOADS[name].npar
+    mom = oracle_events(orc, name, 64)
+    h = me.workload_handle(name, "fp64")
+    me.me_filter_helicities(h, torch.from_numpy(mom).cuda())
+    good = me.me_good_helicities(h)
+    h.close()
+    bit = lambda hh, p: (hh >> (npar - 1 - p)) & 1
+    expect = [hh for hh in range(1 << npar) if bit(hh, 0) != bit(hh, 1) and bit(hh, 2) != bit(hh, 3)]
+    assert list(good) == expect and len(expect) == 4 << NGLUON[name]
+
+
 @pytest.mark.parametrize("name", ["uux_epemg", "uux_epemgg", "uux_epemggg"])
 def test_dy_gauge_invariance_on_gpu(orc, name):
     """A gluon's polarisation replaced by its momentum: every helicity
